@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 BPMF Gibbs sampler: latent rows sampled per second.
+
+One step = one full Gibbs sweep of Alg. 1 (hyper(V), every movie, hyper(U),
+every user, test predictions + RMSE) over the 480,000 x 18,000 rating matrix
+with 1e8 ratings at K = 64 (synthetic, seeded; ``workloads.config3``).
+value = (M + N) x sweeps / device time, max over ranks, summed over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun (N > 1) every rank runs an independent chain (replicas: the
+sweep itself is not sharded across GPUs here), so scaling is weak.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores (rank 0 only) and prints the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "latent rows sampled/s (Gibbs sweep, K=64)"
+UNIT = "rows/s"
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (host only)
+# ----------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def dist_init(world, backend):
+    if world <= 1:
+        return
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+
+
+def barrier(world, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
+
+
+def reduce_over_ranks(x, world, op="max", device=None):
+    """Max (or sum) of a float over all ranks; identity for one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64,
+                     device=device if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def aggregate_rows_per_s(rows_per_rank, sweeps, max_ms):
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    return rows_per_rank * sweeps / (max_ms / 1e3)
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = str(index)
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.index, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 8:
+                    continue
+                try:
+                    sm.append(float(f[0]))
+                    mx.append(float(f[1]))
+                except ValueError:
+                    continue
+                for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                    "sw_power_cap"), f[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# algorithmic work per phase (stated in the design doc)
+# ----------------------------------------------------------------------------
+def row_phase_flops(nnz, rows, K):
+    """Per rating: symmetric Gram K(K+1) + right-hand side 2K flops.
+    Per row: Cholesky K^3/3 + two triangular solves 2K^2 each + prior terms 2K^2."""
+    return nnz * (K * (K + 1) + 2 * K) + rows * (K**3 / 3.0 + 6.0 * K * K)
+
+
+def row_phase_bytes(nnz, rows, K):
+    """Compulsory bytes: index + value per rating, gathered factor row (4K) per rating,
+    row pointer (8) + factor row written (4K) per row."""
+    return nnz * (8 + 4 * K) + rows * (8 + 4 * K)
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (baseline and reference arm)
+# ----------------------------------------------------------------------------
+def oracle_sample_rate(prob, frac, seed=0, nthreads=None):
+    """Time the FP64 oracle on a uniform sample of `frac` of the rows of each side
+    (row updates + row statistics), extrapolate to a full sweep, return rows/s."""
+    import oracle
+    nthreads = nthreads or os.cpu_count() or 1
+    orc = oracle.Oracle(prob, nthreads=nthreads)
+    rng = np.random.default_rng(seed)
+    t_sweep = 0.0
+    desc = []
+    for side, n in ((oracle.MOVIE, prob.N), (oracle.USER, prob.M)):
+        k = max(1, int(round(frac * n)))
+        rows = np.sort(rng.choice(n, size=k, replace=False))
+        X = orc.get_factors(side)[rows]
+        t0 = time.perf_counter()
+        oracle.row_stats(X)
+        orc.rows_subset(side, rows)
+        t1 = time.perf_counter()
+        t_sweep += (t1 - t0) * (n / k)
+        desc.append("%d/%d %s" % (k, n, "movies" if side == oracle.MOVIE else "users"))
+    return (prob.M + prob.N) / t_sweep, nthreads, ", ".join(desc)
+
+
+# ----------------------------------------------------------------------------
+# arms
+# ----------------------------------------------------------------------------
+def make_problem(args, rank):
+    import workloads
+    gen = workloads.CONFIGS[args.config]
+    kw = {"seed": {1: 0, 2: 1, 3: 2}[args.config] + 1000 * rank}
+    if args.config != 1:
+        kw["scale"] = args.scale
+    return gen(**kw)
+
+
+def run_native(args):
+    import torch
+
+    import paper_1705_10633_gb300 as bp
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+    prob = make_problem(args, rank)
+    K = prob.K
+    flags = bp.BPMF_BF16_GRAM if args.bf16 else 0
+    stream = torch.cuda.Stream(device=dev)
+    params = bp.bpmf_default_params(alpha=prob.alpha, seed=prob.seed, burn_in=prob.burn_in,
+                                    flags=flags)
+    h = bp.bpmf_create(prob.M, prob.N, K, prob.csr_ptr, prob.csr_col, prob.csr_val,
+                       test_i=prob.test_i, test_j=prob.test_j, test_r=prob.test_r, params=params,
+                       stream=stream.cuda_stream)
+    phases = [bp.BPMF_PHASE_HYPER_MOVIE, bp.BPMF_PHASE_ROWS_MOVIE, bp.BPMF_PHASE_HYPER_USER,
+              bp.BPMF_PHASE_ROWS_USER, bp.BPMF_PHASE_PREDICT, bp.BPMF_PHASE_ADVANCE]
+    names = ["hyper_movie", "rows_movie", "hyper_user", "rows_user", "predict", "advance"]
+    try:
+        for _ in range(args.warmup):
+            bp.bpmf_sweep(h, 1, want_rmse=False)
+        torch.cuda.synchronize(dev)
+        barrier(world, local)
+        torch.cuda.synchronize(dev)
+        n0 = bp.bpmf_launch_count(h)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(phases) + 1)]
+              for _ in range(args.steps)]
+        clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+        clocks.start()
+        with torch.cuda.stream(stream):
+            for s in range(args.steps):
+                for p, ph in enumerate(phases):
+                    ev[s][p].record(stream)
+                    bp.bpmf_step(h, ph)
+                ev[s][-1].record(stream)
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop()
+        barrier(world, local)
+        torch.cuda.synchronize(dev)
+        launches = bp.bpmf_launch_count(h) - n0
+        status = bp.bpmf_status(h)
+        if status != 0:
+            raise bp.BpmfError(status, "timed sweeps")
+        rs, ra = bp.bpmf_sweep(h, 0)
+        total_ms = ev[0][0].elapsed_time(ev[-1][-1])
+        phase_ms = {n: sum(ev[s][p].elapsed_time(ev[s][p + 1]) for s in range(args.steps))
+                    / args.steps for p, n in enumerate(names)}
+        info_u = bp.bpmf_info(h, 0)
+        info_v = bp.bpmf_info(h, 1)
+    finally:
+        bp.bpmf_destroy(h)
+
+    max_ms = reduce_over_ranks(total_ms, world, "max", dev)
+    value = aggregate_rows_per_s((prob.M + prob.N) * world, args.steps, max_ms)
+    ms_per_step = max_ms / args.steps
+
+    # dominant kernel: the slower row-update phase (one kernel launch per bin)
+    nnz = prob.nnz
+    dom = max(("rows_movie", "rows_user"), key=lambda n: phase_ms[n])
+    dom_rows = prob.N if dom == "rows_movie" else prob.M
+    flops = row_phase_flops(nnz, dom_rows, K)
+    achieved = flops / (phase_ms[dom] / 1e3) / 1e12
+    peaks = load_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
+    roofline = {"bound": "alu", "kernel": "rows_warp_kernel<64> (%s)" % dom,
+                "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / fp32_peak, 4), "traffic": None,
+                "peak_source": "FP32 CUDA-core peak from %d SMs x 128 lanes x 2 x %.0f MHz" % (n_sm, sm_max),
+                "algorithmic_tflop_per_launch": round(flops / 1e12, 4),
+                "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()}}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, prob, bp, torch, dev, stream, world, local)
+
+    out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "bf16-gram/f32" if args.bf16 else "f32", "data": "synthetic",
+           "config": {"workload": prob.name, "M": prob.M, "N": prob.N, "K": K, "nnz": nnz,
+                      "test": prob.T, "sweeps_per_s": round(1e3 / ms_per_step, 3),
+                      "l2": "inputs larger than L2 (ratings CSR+CSC %.2f GB)" % (nnz * 16 / 1e9),
+                      "bins": {"users": [info_u["n_short"], info_u["n_long"]],
+                               "movies": [info_v["n_short"], info_v["n_long"]]},
+                      "parallelism": "replicas x%d" % world, "rmse_sample": rs, "rmse_avg": ra},
+           "roofline": roofline, "clocks": clk, "gpu_launches": int(launches), "e2e": e2e}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, desc = oracle_sample_rate(prob, args.cpu_frac)
+        out["cpu_baseline"] = {"value": round(rate, 2), "unit": UNIT, "cores": cores,
+                               "kind": "oracle", "sample": "FP64 oracle row updates + row "
+                               "statistics on uniform row samples (%s), extrapolated to one sweep"
+                               % desc}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_e2e(args, prob, bp, torch, dev, stream, world, local):
+    """Whole job through the public C ABI from host buffers: create (host -> device
+    copies of the ratings and test set, column view, bins, initial draw), then
+    `steps` sweeps each returning its RMSE to the host."""
+    h2d = (prob.csr_ptr.nbytes + prob.csr_col.nbytes + prob.csr_val.nbytes + prob.test_i.nbytes
+           + prob.test_j.nbytes + prob.test_r.nbytes)
+    barrier(world, local)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    params = bp.bpmf_default_params(alpha=prob.alpha, seed=prob.seed, burn_in=prob.burn_in,
+                                    flags=bp.BPMF_BF16_GRAM if args.bf16 else 0)
+    h = bp.bpmf_create(prob.M, prob.N, prob.K, prob.csr_ptr, prob.csr_col, prob.csr_val,
+                       test_i=prob.test_i, test_j=prob.test_j, test_r=prob.test_r, params=params,
+                       stream=stream.cuda_stream)
+    try:
+        for _ in range(args.steps):
+            bp.bpmf_sweep(h, 1)  # RMSE of the step read back to the host
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+    finally:
+        bp.bpmf_destroy(h)
+    ms = reduce_over_ranks((t1 - t0) * 1e3, world, "max", dev)
+    return {"value": round(aggregate_rows_per_s((prob.M + prob.N) * world, args.steps, ms), 1),
+            "unit": UNIT, "h2d_bytes_per_step": int(h2d / args.steps),
+            "d2h_bytes_per_step": 16,
+            "note": "wall clock of bpmf_create from host arrays + %d x bpmf_sweep with RMSE "
+                    "read back" % args.steps}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    prob = make_problem(args, 0)
+    import oracle  # noqa: F401  (built by __graft_entry__.build())
+    times = []
+    rates = []
+    desc = cores = None
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        rate, cores, desc = oracle_sample_rate(prob, args.ref_frac, seed=s)
+        t1 = time.perf_counter()
+        if s >= args.warmup:
+            rates.append(rate)
+            times.append(t1 - t0)
+    value = float(np.mean(rates))
+    out = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * (prob.M + prob.N) / value, 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": prob.name, "M": prob.M, "N": prob.N, "K": prob.K,
+                      "nnz": prob.nnz},
+           "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": cores,
+                            "kind": "oracle", "sample": desc + " per step"},
+           "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--config", type=int, choices=[1, 2, 3], default=3)
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--bf16", action="store_true", help="BF16-input tensor-core Gram for long rows")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-frac", type=float, default=0.1)
+    ap.add_argument("--ref-frac", type=float, default=0.01)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

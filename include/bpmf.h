@@ -1,0 +1,177 @@
+/*
+ * bpmf.h -- C ABI of the GB300 BPMF Gibbs sampler (one chain on one GPU).
+ *
+ * The method is Bayesian Probabilistic Matrix Factorization by Gibbs sampling
+ * as laid out in Alg. 1 of arXiv:1705.10633 (Sec. 2): per sweep, sample the
+ * movie hyper-parameters from V, update every movie, sample the user
+ * hyper-parameters from U, update every user, then predict the test points and
+ * compute the RMSE.  The per-item update (Sec. 2; Sec. 3.1) forms the K x K
+ * precision from the other side's vectors of the item's ratings, factors it by
+ * Cholesky instead of inverting it, and draws the item's new vector.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: BPMF_OK (0) or a negative BPMF_E* code; bpmf_strerror()
+ *     names it.  No entry point aborts the process.
+ *   - Pointers named host_* or documented as host memory are read (or written)
+ *     only during the call; the caller keeps ownership.  Device memory the
+ *     library needs is owned by the handle and released by bpmf_destroy().
+ *   - A handle is not thread-safe.  Work is ordered on the CUDA stream given to
+ *     bpmf_create(); calls that return host values synchronise that stream.
+ *   - Matrices are row-major.  U is M x K (users = rows of R), V is N x K
+ *     (movies = columns of R); K <= 64.
+ *   - Ratings: CSR (users) with int64 row pointers, int32 column indices and
+ *     FP32 values.  Columns inside a row may be in any order.
+ */
+#ifndef BPMF_H
+#define BPMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------- */
+#define BPMF_OK 0
+#define BPMF_EINVAL -1   /* bad argument: dims, K > 64, malformed CSR/CSC, ... */
+#define BPMF_ENOMEM -2   /* device or host allocation failed                  */
+#define BPMF_ECUDA -3    /* a CUDA runtime call failed                        */
+#define BPMF_ENOTPD -4   /* a precision matrix had a non-positive pivot       */
+#define BPMF_ETIMEOUT -5 /* a bounded device wait gave up                     */
+#define BPMF_ENAN -6     /* a NaN/Inf was produced                            */
+#define BPMF_EGAMMA -7   /* the gamma sampler exhausted its attempts          */
+
+/* ---- flags (bpmf_params.flags) ----------------------------------------- */
+#define BPMF_BF16_GRAM 0x1u   /* long rows: BF16 inputs, FP32 accumulation on tensor cores */
+#define BPMF_CLIP 0x2u        /* clip predictions to [clip_lo, clip_hi]                   */
+#define BPMF_DEBUG_MEANS 0x4u /* keep each row's conditional mean (bpmf_debug_means)      */
+#define BPMF_NO_CENTER 0x8u   /* do not subtract the training mean from the ratings       */
+#define BPMF_CUDA_CORE_GRAM 0x10u /* every row on the CUDA-core (FP32 FMA) kernel         */
+
+/* ---- sides and phases --------------------------------------------------- */
+#define BPMF_USER 0  /* rows of R, factors U, CSR */
+#define BPMF_MOVIE 1 /* columns of R, factors V, CSC */
+
+#define BPMF_PHASE_HYPER_USER 0  /* statistics of U, Normal-Wishart draw of (mu_U, Lambda_U) */
+#define BPMF_PHASE_HYPER_MOVIE 1 /* same for V                                              */
+#define BPMF_PHASE_ROWS_USER 2   /* every user row given V                                  */
+#define BPMF_PHASE_ROWS_MOVIE 3  /* every movie column given U                              */
+#define BPMF_PHASE_PREDICT 4     /* test predictions, running averages, RMSE                */
+#define BPMF_PHASE_ADVANCE 5     /* sweep counter += 1                                      */
+
+typedef struct bpmf_ctx* bpmf_handle;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc
+ * returns device memory of at least `bytes` bytes usable on `stream`, or NULL. */
+typedef void* (*bpmf_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*bpmf_free_fn)(void* ptr, void* stream, void* ctx);
+
+typedef struct {
+    double alpha;       /* rating precision (BPMF observation noise precision)         */
+    double beta0;       /* Normal-Wishart prior: mean precision scale                   */
+    double nu0;         /* Normal-Wishart prior: degrees of freedom, must be >= K       */
+    const double* mu0;  /* K prior mean, NULL = zeros (host, copied)                    */
+    const double* W0;   /* K x K SPD prior scale, NULL = identity (host, copied)        */
+    uint64_t seed;      /* Philox key                                                   */
+    uint32_t job_id;    /* goes into the Philox counter (tag | job_id << 8)             */
+    int32_t burn_in;    /* sweeps before predictions enter the running average          */
+    int32_t order;      /* 0 = movies first (Alg. 1), 1 = users first                   */
+    uint32_t flags;     /* BPMF_* flags                                                  */
+    double clip_lo, clip_hi;
+    int32_t long_min_degree; /* rows with at least this many ratings use the tensor-core
+                                kernel; <= 0 = library default                          */
+    bpmf_alloc_fn alloc; /* NULL = cudaMalloc / cudaFree */
+    bpmf_free_fn free;
+    void* alloc_ctx;
+} bpmf_params;
+
+/* Fill *p with the defaults: alpha 2, beta0 2, nu0 = K (set at create when 0),
+ * mu0 0, W0 I, seed 0, burn_in 0, order 0, no flags, clip [1, 5]. */
+int bpmf_default_params(bpmf_params* p);
+
+/*
+ * Create a chain: copy the ratings (host arrays) to the device, build the
+ * column view, bin the rows by degree, and draw the initial factors
+ * U, V ~ N(0, 1) from the Philox init streams.
+ *   csr_*        : M + 1 row pointers (csr_ptr[0] = 0), nnz column indices in
+ *                  [0, N), nnz values.  Host memory.
+ *   csc_*        : the same ratings by column, or all three NULL to have the
+ *                  library build them.  Host memory.
+ *   test_*       : T held-out points (row, column, value), T may be 0.  Host.
+ *   cuda_stream  : cudaStream_t for all work of this handle (NULL = default).
+ * Errors: BPMF_EINVAL for bad sizes, K outside [1, 64], nu0 < K, pointers out
+ * of order or indices out of range; BPMF_ENOMEM; BPMF_ECUDA.
+ */
+int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t* csr_ptr,
+                const int32_t* csr_col, const float* csr_val, const int64_t* csc_ptr,
+                const int32_t* csc_row, const float* csc_val, int64_t T, const int32_t* test_i,
+                const int32_t* test_j, const float* test_r, const bpmf_params* p,
+                void* cuda_stream);
+
+/*
+ * Run n_sweeps full Gibbs sweeps (Alg. 1): hyper(V), movies, hyper(U), users,
+ * predict (order 0; order 1 swaps the sides).  If either RMSE pointer is
+ * non-NULL, the call waits for the sweeps and writes the RMSE of the last
+ * sweep's sample and of the running-average prediction (NaN before burn-in;
+ * both NaN when T = 0).  Host pointers.  A sticky device error from any
+ * kernel is returned as its code.
+ */
+int bpmf_sweep(bpmf_handle h, int32_t n_sweeps, double* rmse_sample, double* rmse_avg);
+
+/* Run one BPMF_PHASE_* step of a sweep (for checking the steps one by one). */
+int bpmf_step(bpmf_handle h, int32_t phase);
+
+/*
+ * Predictions r_bar + u_i . v_j of the current sample for n points (clipped
+ * under BPMF_CLIP).  where = 0: i, j, out are host arrays; where = 1: device
+ * arrays valid on the handle's stream.  BPMF_EINVAL for indices out of range.
+ */
+int bpmf_predict(bpmf_handle h, int64_t n, const int32_t* i, const int32_t* j, float* out,
+                 int32_t where);
+
+/*
+ * Chain state, host buffers: U (M x K), V (N x K) FP32, hyper FP64 laid out as
+ * [mu_U (K), Lambda_U (K x K), mu_V (K), Lambda_V (K x K)], sweep = number of
+ * completed sweeps.  Any pointer may be NULL to skip that part.  Because every
+ * random number is a function of (seed, sweep, row), restoring a state and
+ * continuing reproduces an uninterrupted chain.
+ */
+int bpmf_get_state(bpmf_handle h, float* U, float* V, double* hyper, uint64_t* sweep);
+int bpmf_set_state(bpmf_handle h, const float* U, const float* V, const double* hyper,
+                   uint64_t sweep);
+
+/* Running prediction sums (T doubles) and the number of sweeps they hold. */
+int bpmf_get_accum(bpmf_handle h, double* psum, int64_t* n_avg);
+int bpmf_set_accum(bpmf_handle h, const double* psum, int64_t n_avg);
+
+/* Statistics of the last hyper step of `side`: row count, mean (K) and scatter
+ * S = (1/n) sum (x - mean)(x - mean)^T (K x K), FP64 host buffers. */
+int bpmf_get_stats(bpmf_handle h, int32_t side, int64_t* n, double* mean, double* S);
+
+/* Conditional means of the last row update of `side` (rows x K FP32, host);
+ * needs BPMF_DEBUG_MEANS at create, else BPMF_EINVAL. */
+int bpmf_debug_means(bpmf_handle h, int32_t side, float* out);
+
+/* Sticky device status: BPMF_OK, BPMF_ENOTPD, BPMF_ENAN or BPMF_EGAMMA.  Syncs. */
+int bpmf_status(bpmf_handle h);
+
+/* Diagnostics: number of rows of `side` on the CUDA-core kernel and on the
+ * tensor-core kernel, the centring mean, and device bytes held. */
+int bpmf_info(bpmf_handle h, int32_t side, int64_t* n_short, int64_t* n_long, double* rbar,
+              int64_t* device_bytes);
+
+/* Number of kernels this handle has launched so far (all phases, all sweeps). */
+int bpmf_launch_count(bpmf_handle h, int64_t* launches);
+
+/* Human-readable name of a return code (static string). */
+const char* bpmf_strerror(int code);
+
+/* Release everything the handle owns.  NULL-safe. */
+int bpmf_destroy(bpmf_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BPMF_H */

@@ -1,0 +1,699 @@
+// bpmf_api.cu -- the C ABI of include/bpmf.h: handle lifetime, host-side
+// validation and preprocessing (column view, degree bins), and the order of
+// the device phases of one Gibbs sweep (Alg. 1).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "bpmf.h"
+#include "bpmf_internal.cuh"
+#include "philox.cuh"
+
+using namespace bpmf;
+
+namespace {
+
+constexpr int kDefaultLongMinDegree = 64;
+
+struct DevSide {
+    int64_t rows = 0;
+    int64_t* ptr = nullptr;
+    int32_t* idx = nullptr;
+    float* val = nullptr;
+    float* X = nullptr;
+    float* means = nullptr;
+    int32_t* bin_rows = nullptr;  // short bin first, then long bin, each longest first
+    int64_t n_short = 0, n_long = 0;
+    double* mu64 = nullptr;
+    double* lam64 = nullptr;
+    float* lam32 = nullptr;
+    float* lammu32 = nullptr;
+    double* partials = nullptr;
+    int red_blocks = 1;
+    double* sums = nullptr;
+    double* stats = nullptr;
+    uint32_t tag_init = 0, tag_row = 0, tag_hyper = 0, tag_gamma = 0;
+};
+
+}  // namespace
+
+struct bpmf_ctx {
+    int device = 0;
+    int num_sms = 1;
+    cudaStream_t stream = nullptr;
+    int64_t M = 0, N = 0, nnz = 0, T = 0;
+    int K = 0, kp = 0;
+    bpmf_params p{};
+    std::vector<double> mu0, W0;
+    double rbar = 0.0;
+    DevSide side[2];
+    double* mu0_d = nullptr;
+    double* W0inv_d = nullptr;
+    int32_t* ti = nullptr;
+    int32_t* tj = nullptr;
+    float* tr = nullptr;
+    double* psum = nullptr;
+    double* pred_partials = nullptr;
+    int pred_blocks = 1;
+    Control* ctl = nullptr;
+    std::vector<void*> allocs;
+    int64_t bytes = 0;
+    int64_t launches = 0;  // kernels launched by the phases
+};
+
+namespace {
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? BPMF_OK : BPMF_ECUDA; }
+
+void* dalloc(bpmf_ctx* h, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (h->p.alloc) {
+        p = h->p.alloc(bytes, (void*)h->stream, h->p.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        h->allocs.push_back(p);
+        h->bytes += (int64_t)bytes;
+    }
+    return p;
+}
+
+template <class T>
+bool alloc_n(bpmf_ctx* h, T** out, size_t n)
+{
+    *out = static_cast<T*>(dalloc(h, sizeof(T) * n));
+    return *out != nullptr;
+}
+
+// Host FP64 Cholesky (lower) used to validate W0 and to invert it.
+bool host_cholesky(int K, const double* A, std::vector<double>& L)
+{
+    L.assign((size_t)K * K, 0.0);
+    for (int j = 0; j < K; ++j) {
+        double d = A[j * K + j];
+        for (int k = 0; k < j; ++k) d -= L[j * K + k] * L[j * K + k];
+        if (!(d > 0.0)) return false;
+        L[j * K + j] = sqrt(d);
+        for (int i = j + 1; i < K; ++i) {
+            double s = A[i * K + j];
+            for (int k = 0; k < j; ++k) s -= L[i * K + k] * L[j * K + k];
+            L[i * K + j] = s / L[j * K + j];
+        }
+    }
+    return true;
+}
+
+bool host_spd_inverse(int K, const double* A, std::vector<double>& inv)
+{
+    std::vector<double> L;
+    if (!host_cholesky(K, A, L)) return false;
+    inv.assign((size_t)K * K, 0.0);
+    std::vector<double> y(K), x(K);
+    for (int c = 0; c < K; ++c) {
+        for (int i = 0; i < K; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) s -= L[i * K + k] * y[k];
+            y[i] = s / L[i * K + i];
+        }
+        for (int i = K - 1; i >= 0; --i) {
+            double s = y[i];
+            for (int k = i + 1; k < K; ++k) s -= L[k * K + i] * x[k];
+            x[i] = s / L[i * K + i];
+        }
+        for (int i = 0; i < K; ++i) inv[i * K + c] = x[i];
+    }
+    return true;
+}
+
+bool valid_csr(int64_t rows, int64_t cols, const int64_t* ptr, const int32_t* idx)
+{
+    if (ptr[0] != 0) return false;
+    for (int64_t r = 0; r < rows; ++r)
+        if (ptr[r + 1] < ptr[r]) return false;
+    const int64_t nnz = ptr[rows];
+    for (int64_t t = 0; t < nnz; ++t)
+        if (idx[t] < 0 || (int64_t)idx[t] >= cols) return false;
+    return true;
+}
+
+// Column view by counting sort; rows ascend inside each column.
+void build_csc(int64_t M, int64_t N, const int64_t* rp, const int32_t* ci, const float* v,
+               std::vector<int64_t>& cp, std::vector<int32_t>& ri, std::vector<float>& cv)
+{
+    const int64_t nnz = rp[M];
+    cp.assign((size_t)N + 1, 0);
+    for (int64_t t = 0; t < nnz; ++t) cp[(size_t)ci[t] + 1] += 1;
+    for (int64_t j = 0; j < N; ++j) cp[j + 1] += cp[j];
+    std::vector<int64_t> fill(cp.begin(), cp.end() - 1);
+    ri.resize((size_t)nnz);
+    cv.resize((size_t)nnz);
+    for (int64_t i = 0; i < M; ++i)
+        for (int64_t t = rp[i]; t < rp[i + 1]; ++t) {
+            const int64_t q = fill[ci[t]]++;
+            ri[q] = (int32_t)i;
+            cv[q] = v[t];
+        }
+}
+
+// Degree bins: rows below `long_min` (short bin) then the rest (long bin), each
+// ordered by decreasing degree so that a grid-stride loop hands the longest
+// rows out first (the per-item cost model of Sec. 4.2: fixed + per-rating cost).
+void bin_rows(int64_t rows, const int64_t* ptr, int64_t long_min, std::vector<int32_t>& order,
+              int64_t* n_short, int64_t* n_long)
+{
+    order.resize((size_t)rows);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        const int64_t da = ptr[a + 1] - ptr[a], db = ptr[b + 1] - ptr[b];
+        const bool la = da >= long_min, lb = db >= long_min;
+        if (la != lb) return lb;  // short bin first
+        return da > db;
+    });
+    int64_t ns = 0;
+    for (int64_t r = 0; r < rows; ++r)
+        if (ptr[r + 1] - ptr[r] < long_min) ++ns;
+    *n_short = ns;
+    *n_long = rows - ns;
+}
+
+int sync_status(bpmf_ctx* h)
+{
+    Control c;
+    cudaError_t e = cudaMemcpyAsync(&c, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return BPMF_ECUDA;
+    if (c.status & kStatusNotPD) return BPMF_ENOTPD;
+    if (c.status & kStatusNaN) return BPMF_ENAN;
+    if (c.status & kStatusGamma) return BPMF_EGAMMA;
+    return BPMF_OK;
+}
+
+int phase_hyper(bpmf_ctx* h, int s)
+{
+    DevSide& d = h->side[s];
+    cudaError_t e = launch_hyper_reduce(d.X, d.rows, h->kp, d.mu64, d.partials, d.red_blocks,
+                                        h->stream);
+    if (e == cudaSuccess) e = launch_hyper_combine(d.partials, d.red_blocks, h->kp, d.sums, h->stream);
+    if (e != cudaSuccess) return BPMF_ECUDA;
+    NWArgs a;
+    a.sums = d.sums;
+    a.shift64 = d.mu64;
+    a.n = d.rows;
+    a.K = h->K;
+    a.kp = h->kp;
+    a.beta0 = h->p.beta0;
+    a.nu0 = h->p.nu0;
+    a.mu0 = h->mu0_d;
+    a.W0inv = h->W0inv_d;
+    a.seed = h->p.seed;
+    a.c3_normal = d.tag_hyper;
+    a.c3_gamma = d.tag_gamma;
+    a.ctl = h->ctl;
+    a.stats = d.stats;
+    a.mu64 = d.mu64;
+    a.lam64 = d.lam64;
+    a.lam32 = d.lam32;
+    a.lammu32 = d.lammu32;
+    h->launches += 3;
+    return cuda_rc(launch_nw_sample(a, h->stream));
+}
+
+int phase_rows(bpmf_ctx* h, int s)
+{
+    DevSide& d = h->side[s];
+    const DevSide& o = h->side[1 - s];
+    RowArgs a;
+    a.ptr = d.ptr;
+    a.idx = d.idx;
+    a.val = d.val;
+    a.Y = o.X;
+    a.ldy = h->kp;
+    a.X = d.X;
+    a.ldx = h->kp;
+    a.means = d.means;
+    a.lam = d.lam32;
+    a.lammu = d.lammu32;
+    a.ctl = h->ctl;
+    a.seed = h->p.seed;
+    a.c3 = d.tag_row;
+    a.K = h->K;
+    a.alpha = (float)h->p.alpha;
+    // every bin runs on the CUDA-core kernel in this build; the long bin is
+    // ordered separately so a dedicated long-row kernel can take it over
+    a.rows = d.bin_rows;
+    a.nrows = d.n_short + d.n_long;
+    if (a.nrows > 0) h->launches += 1;
+    return cuda_rc(launch_rows_warp(a, h->kp, h->num_sms, h->stream));
+}
+
+int phase_predict(bpmf_ctx* h)
+{
+    const DevSide& u = h->side[BPMF_USER];
+    const DevSide& v = h->side[BPMF_MOVIE];
+    cudaError_t e = cudaSuccess;
+    if (h->T > 0)
+        e = launch_predict(h->ti, h->tj, h->tr, h->T, u.X, v.X, h->kp, h->kp, h->rbar,
+                           (h->p.flags & BPMF_CLIP) ? 1 : 0, h->p.clip_lo, h->p.clip_hi,
+                           h->p.burn_in, h->psum, h->ctl, h->pred_partials, h->pred_blocks,
+                           h->stream);
+    if (e == cudaSuccess)
+        e = launch_predict_finish(h->pred_partials, h->T > 0 ? h->pred_blocks : 0, h->T,
+                                  h->p.burn_in, h->ctl, h->stream);
+    h->launches += h->T > 0 ? 2 : 1;
+    return cuda_rc(e);
+}
+
+int run_phase(bpmf_ctx* h, int phase)
+{
+    switch (phase) {
+    case BPMF_PHASE_HYPER_USER: return phase_hyper(h, BPMF_USER);
+    case BPMF_PHASE_HYPER_MOVIE: return phase_hyper(h, BPMF_MOVIE);
+    case BPMF_PHASE_ROWS_USER: return phase_rows(h, BPMF_USER);
+    case BPMF_PHASE_ROWS_MOVIE: return phase_rows(h, BPMF_MOVIE);
+    case BPMF_PHASE_PREDICT: return phase_predict(h);
+    case BPMF_PHASE_ADVANCE: h->launches += 1; return cuda_rc(launch_advance(h->ctl, h->stream));
+    default: return BPMF_EINVAL;
+    }
+}
+
+int copy_packed_d2h(const float* dev, int64_t rows, int K, int ld, float* host, cudaStream_t s)
+{
+    if (rows == 0) return BPMF_OK;
+    return cuda_rc(cudaMemcpy2DAsync(host, sizeof(float) * K, dev, sizeof(float) * ld,
+                                     sizeof(float) * K, (size_t)rows, cudaMemcpyDeviceToHost, s));
+}
+
+}  // namespace
+
+extern "C" {
+
+int bpmf_default_params(bpmf_params* p)
+{
+    if (!p) return BPMF_EINVAL;
+    memset(p, 0, sizeof(*p));
+    p->alpha = 2.0;
+    p->beta0 = 2.0;
+    p->nu0 = 0.0;  // 0 = K
+    p->clip_lo = 1.0;
+    p->clip_hi = 5.0;
+    return BPMF_OK;
+}
+
+const char* bpmf_strerror(int code)
+{
+    switch (code) {
+    case BPMF_OK: return "ok";
+    case BPMF_EINVAL: return "invalid argument";
+    case BPMF_ENOMEM: return "out of memory";
+    case BPMF_ECUDA: return "CUDA runtime error";
+    case BPMF_ENOTPD: return "precision matrix not positive definite";
+    case BPMF_ETIMEOUT: return "device wait timed out";
+    case BPMF_ENAN: return "NaN or Inf produced";
+    case BPMF_EGAMMA: return "gamma sampler exhausted its attempts";
+    default: return "unknown error";
+    }
+}
+
+int bpmf_destroy(bpmf_handle h)
+{
+    if (!h) return BPMF_OK;
+    cudaStreamSynchronize(h->stream);
+    for (void* ptr : h->allocs) {
+        if (h->p.free) h->p.free(ptr, (void*)h->stream, h->p.alloc_ctx);
+        else cudaFree(ptr);
+    }
+    delete h;
+    return BPMF_OK;
+}
+
+int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t* csr_ptr,
+                const int32_t* csr_col, const float* csr_val, const int64_t* csc_ptr,
+                const int32_t* csc_row, const float* csc_val, int64_t T, const int32_t* test_i,
+                const int32_t* test_j, const float* test_r, const bpmf_params* p,
+                void* cuda_stream)
+{
+    if (!out) return BPMF_EINVAL;
+    *out = nullptr;
+    if (M <= 0 || N <= 0 || M > INT32_MAX || N > INT32_MAX || K < 1 || K > kMaxK || T < 0)
+        return BPMF_EINVAL;
+    if (!csr_ptr || (!csr_col && csr_ptr[M] > 0) || (!csr_val && csr_ptr[M] > 0)) return BPMF_EINVAL;
+    if (T > 0 && (!test_i || !test_j || !test_r)) return BPMF_EINVAL;
+    const bool have_csc = csc_ptr || csc_row || csc_val;
+    if (have_csc && !(csc_ptr && (csc_ptr[N] == 0 || (csc_row && csc_val)))) return BPMF_EINVAL;
+    bpmf_params prm;
+    if (p) prm = *p;
+    else bpmf_default_params(&prm);
+    if (prm.nu0 == 0.0) prm.nu0 = (double)K;
+    if (!(prm.alpha > 0.0) || !(prm.beta0 > 0.0) || !(prm.nu0 >= (double)K)) return BPMF_EINVAL;
+    if (prm.order != 0 && prm.order != 1) return BPMF_EINVAL;
+    if (!valid_csr(M, N, csr_ptr, csr_col)) return BPMF_EINVAL;
+    if (have_csc) {
+        if (!valid_csr(N, M, csc_ptr, csc_row) || csc_ptr[N] != csr_ptr[M]) return BPMF_EINVAL;
+    }
+    for (int64_t t = 0; t < T; ++t)
+        if (test_i[t] < 0 || test_i[t] >= M || test_j[t] < 0 || test_j[t] >= N) return BPMF_EINVAL;
+
+    bpmf_ctx* h = new (std::nothrow) bpmf_ctx();
+    if (!h) return BPMF_ENOMEM;
+    h->p = prm;
+    h->M = M;
+    h->N = N;
+    h->K = K;
+    h->kp = (K + 15) / 16 * 16;
+    h->T = T;
+    h->nnz = csr_ptr[M];
+    h->stream = (cudaStream_t)cuda_stream;
+    h->mu0.assign(K, 0.0);
+    h->W0.assign((size_t)K * K, 0.0);
+    for (int k = 0; k < K; ++k) h->mu0[k] = prm.mu0 ? prm.mu0[k] : 0.0;
+    for (int i = 0; i < K * K; ++i) h->W0[i] = prm.W0 ? prm.W0[i] : (i / K == i % K ? 1.0 : 0.0);
+    h->p.mu0 = nullptr;
+    h->p.W0 = nullptr;
+    std::vector<double> W0inv;
+    if (!host_spd_inverse(K, h->W0.data(), W0inv)) {
+        delete h;
+        return BPMF_EINVAL;
+    }
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return BPMF_ECUDA;
+    }
+    // training mean in index order (FP64)
+    double total = 0.0;
+    for (int64_t t = 0; t < h->nnz; ++t) total += (double)csr_val[t];
+    h->rbar = ((prm.flags & BPMF_NO_CENTER) || h->nnz == 0) ? 0.0 : total / (double)h->nnz;
+
+    std::vector<int64_t> cp;
+    std::vector<int32_t> ri;
+    std::vector<float> cv;
+    if (!have_csc) {
+        build_csc(M, N, csr_ptr, csr_col, csr_val, cp, ri, cv);
+        csc_ptr = cp.data();
+        csc_row = ri.data();
+        csc_val = cv.data();
+    }
+    const int64_t long_min = prm.long_min_degree > 0 ? prm.long_min_degree : kDefaultLongMinDegree;
+    const int64_t* hp[2] = {csr_ptr, csc_ptr};
+    const int32_t* hi[2] = {csr_col, csc_row};
+    const float* hv[2] = {csr_val, csc_val};
+    const int64_t rows[2] = {M, N};
+    int rc = BPMF_OK;
+    const int kp = h->kp;
+    cudaStream_t st = h->stream;
+    std::vector<int32_t> order;
+    for (int s = 0; s < 2 && rc == BPMF_OK; ++s) {
+        DevSide& d = h->side[s];
+        d.rows = rows[s];
+        d.tag_init = tag_word(s == 0 ? kTagInitU : kTagInitV, prm.job_id);
+        d.tag_row = tag_word(s == 0 ? kTagRowU : kTagRowV, prm.job_id);
+        d.tag_hyper = tag_word(s == 0 ? kTagHyperU : kTagHyperV, prm.job_id);
+        d.tag_gamma = tag_word(s == 0 ? kTagGammaU : kTagGammaV, prm.job_id);
+        d.red_blocks = hyper_reduce_blocks(d.rows, h->num_sms);
+        bool ok = alloc_n(h, &d.ptr, d.rows + 1) && alloc_n(h, &d.idx, h->nnz) &&
+                  alloc_n(h, &d.val, h->nnz) && alloc_n(h, &d.X, (size_t)d.rows * kp) &&
+                  alloc_n(h, &d.bin_rows, d.rows) && alloc_n(h, &d.mu64, K) &&
+                  alloc_n(h, &d.lam64, (size_t)K * K) && alloc_n(h, &d.lam32, (size_t)kp * kp) &&
+                  alloc_n(h, &d.lammu32, kp) &&
+                  alloc_n(h, &d.partials, (size_t)d.red_blocks * hyper_partial_doubles(kp)) &&
+                  alloc_n(h, &d.sums, hyper_partial_doubles(kp)) &&
+                  alloc_n(h, &d.stats, (size_t)K + (size_t)K * K);
+        if (ok && (prm.flags & BPMF_DEBUG_MEANS)) ok = alloc_n(h, &d.means, (size_t)d.rows * kp);
+        if (!ok) {
+            rc = BPMF_ENOMEM;
+            break;
+        }
+        bin_rows(d.rows, hp[s], long_min, order, &d.n_short, &d.n_long);
+        cudaError_t e = cudaMemcpyAsync(d.ptr, hp[s], sizeof(int64_t) * (d.rows + 1),
+                                        cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && h->nnz)
+            e = cudaMemcpyAsync(d.idx, hi[s], sizeof(int32_t) * h->nnz, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && h->nnz)
+            e = cudaMemcpyAsync(d.val, hv[s], sizeof(float) * h->nnz, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d.bin_rows, order.data(), sizeof(int32_t) * d.rows,
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = launch_center_values(d.val, h->nnz, h->rbar, st);
+        if (e == cudaSuccess) e = launch_init_factors(d.X, d.rows, K, kp, prm.seed, d.tag_init, st);
+        if (e == cudaSuccess && d.means) e = cudaMemsetAsync(d.means, 0, sizeof(float) * d.rows * kp, st);
+        // initial hyper state: mu = 0, Lambda = I
+        std::vector<double> I((size_t)K * K, 0.0);
+        for (int k = 0; k < K; ++k) I[(size_t)k * K + k] = 1.0;
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.mu64, 0, sizeof(double) * K, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d.lam64, I.data(), sizeof(double) * K * K, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = launch_hyper_refresh(d.mu64, d.lam64, K, kp, d.lam32, d.lammu32, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors go out of scope
+        if (e != cudaSuccess) rc = BPMF_ECUDA;
+    }
+    if (rc == BPMF_OK) {
+        h->pred_blocks = predict_blocks(T, h->num_sms);
+        bool ok = alloc_n(h, &h->mu0_d, K) && alloc_n(h, &h->W0inv_d, (size_t)K * K) &&
+                  alloc_n(h, &h->ti, T) && alloc_n(h, &h->tj, T) && alloc_n(h, &h->tr, T) &&
+                  alloc_n(h, &h->psum, T) && alloc_n(h, &h->pred_partials, 2 * (size_t)h->pred_blocks) &&
+                  alloc_n(h, &h->ctl, 1);
+        if (!ok) rc = BPMF_ENOMEM;
+    }
+    if (rc == BPMF_OK) {
+        cudaError_t e = cudaMemcpyAsync(h->mu0_d, h->mu0.data(), sizeof(double) * K,
+                                        cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->W0inv_d, W0inv.data(), sizeof(double) * K * K,
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && T) e = cudaMemcpyAsync(h->ti, test_i, 4 * T, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && T) e = cudaMemcpyAsync(h->tj, test_j, 4 * T, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && T) e = cudaMemcpyAsync(h->tr, test_r, 4 * T, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && T) e = cudaMemsetAsync(h->psum, 0, sizeof(double) * T, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->ctl, 0, sizeof(Control), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = BPMF_ECUDA;
+    }
+    if (rc != BPMF_OK) {
+        cudaGetLastError();
+        bpmf_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return BPMF_OK;
+}
+
+int bpmf_step(bpmf_handle h, int32_t phase)
+{
+    if (!h) return BPMF_EINVAL;
+    return run_phase(h, phase);
+}
+
+int bpmf_sweep(bpmf_handle h, int32_t n_sweeps, double* rmse_sample, double* rmse_avg)
+{
+    if (!h || n_sweeps < 0) return BPMF_EINVAL;
+    const int first = h->p.order == 0 ? BPMF_MOVIE : BPMF_USER;
+    const int second = 1 - first;
+    const int hyp[2] = {BPMF_PHASE_HYPER_USER, BPMF_PHASE_HYPER_MOVIE};
+    const int rowp[2] = {BPMF_PHASE_ROWS_USER, BPMF_PHASE_ROWS_MOVIE};
+    for (int it = 0; it < n_sweeps; ++it) {
+        const int seq[6] = {hyp[first], rowp[first], hyp[second], rowp[second], BPMF_PHASE_PREDICT,
+                            BPMF_PHASE_ADVANCE};
+        for (int ph : seq) {
+            const int rc = run_phase(h, ph);
+            if (rc) return rc;
+        }
+    }
+    if (rmse_sample || rmse_avg) {
+        Control c;
+        cudaError_t e = cudaMemcpyAsync(&c, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return BPMF_ECUDA;
+        if (rmse_sample) *rmse_sample = c.rmse_sample;
+        if (rmse_avg) *rmse_avg = c.rmse_avg;
+        if (c.status & kStatusNotPD) return BPMF_ENOTPD;
+        if (c.status & kStatusNaN) return BPMF_ENAN;
+        if (c.status & kStatusGamma) return BPMF_EGAMMA;
+    }
+    return BPMF_OK;
+}
+
+int bpmf_predict(bpmf_handle h, int64_t n, const int32_t* i, const int32_t* j, float* out,
+                 int32_t where)
+{
+    if (!h || n < 0 || (n > 0 && (!i || !j || !out)) || (where != 0 && where != 1)) return BPMF_EINVAL;
+    if (n == 0) return BPMF_OK;
+    const int clip = (h->p.flags & BPMF_CLIP) ? 1 : 0;
+    const DevSide& u = h->side[BPMF_USER];
+    const DevSide& v = h->side[BPMF_MOVIE];
+    if (where == 1)
+        return cuda_rc(launch_predict_points(i, j, n, u.X, v.X, h->kp, h->kp, h->rbar, clip,
+                                             h->p.clip_lo, h->p.clip_hi, out, h->stream));
+    for (int64_t t = 0; t < n; ++t)
+        if (i[t] < 0 || i[t] >= h->M || j[t] < 0 || j[t] >= h->N) return BPMF_EINVAL;
+    int32_t *di = nullptr, *dj = nullptr;
+    float* dout = nullptr;
+    cudaError_t e = cudaMallocAsync(&di, 4 * n, h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dj, 4 * n, h->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dout, 4 * n, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(di, i, 4 * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dj, j, 4 * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = launch_predict_points(di, dj, n, u.X, v.X, h->kp, h->kp, h->rbar, clip, h->p.clip_lo,
+                                  h->p.clip_hi, dout, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, 4 * n, cudaMemcpyDeviceToHost, h->stream);
+    if (di) cudaFreeAsync(di, h->stream);
+    if (dj) cudaFreeAsync(dj, h->stream);
+    if (dout) cudaFreeAsync(dout, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return BPMF_ECUDA;
+    }
+    return BPMF_OK;
+}
+
+int bpmf_get_state(bpmf_handle h, float* U, float* V, double* hyper, uint64_t* sweep)
+{
+    if (!h) return BPMF_EINVAL;
+    const int K = h->K;
+    int rc = BPMF_OK;
+    if (U) rc = copy_packed_d2h(h->side[0].X, h->M, K, h->kp, U, h->stream);
+    if (!rc && V) rc = copy_packed_d2h(h->side[1].X, h->N, K, h->kp, V, h->stream);
+    if (!rc && hyper) {
+        double* o = hyper;
+        for (int s = 0; s < 2 && !rc; ++s) {
+            rc = cuda_rc(cudaMemcpyAsync(o, h->side[s].mu64, sizeof(double) * K,
+                                         cudaMemcpyDeviceToHost, h->stream));
+            if (!rc)
+                rc = cuda_rc(cudaMemcpyAsync(o + K, h->side[s].lam64, sizeof(double) * K * K,
+                                             cudaMemcpyDeviceToHost, h->stream));
+            o += K + K * K;
+        }
+    }
+    Control c;
+    if (!rc) rc = cuda_rc(cudaMemcpyAsync(&c, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, h->stream));
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(h->stream));
+    if (!rc && sweep) *sweep = c.sweep;
+    return rc;
+}
+
+int bpmf_set_state(bpmf_handle h, const float* U, const float* V, const double* hyper,
+                   uint64_t sweep)
+{
+    if (!h) return BPMF_EINVAL;
+    const int K = h->K, kp = h->kp;
+    cudaStream_t st = h->stream;
+    const float* src[2] = {U, V};
+    int rc = BPMF_OK;
+    for (int s = 0; s < 2 && !rc; ++s) {
+        if (!src[s]) continue;
+        DevSide& d = h->side[s];
+        rc = cuda_rc(cudaMemsetAsync(d.X, 0, sizeof(float) * d.rows * kp, st));
+        if (!rc)
+            rc = cuda_rc(cudaMemcpy2DAsync(d.X, sizeof(float) * kp, src[s], sizeof(float) * K,
+                                           sizeof(float) * K, (size_t)d.rows,
+                                           cudaMemcpyHostToDevice, st));
+    }
+    if (!rc && hyper) {
+        const double* in = hyper;
+        for (int s = 0; s < 2 && !rc; ++s) {
+            DevSide& d = h->side[s];
+            rc = cuda_rc(cudaMemcpyAsync(d.mu64, in, sizeof(double) * K, cudaMemcpyHostToDevice, st));
+            if (!rc)
+                rc = cuda_rc(cudaMemcpyAsync(d.lam64, in + K, sizeof(double) * K * K,
+                                             cudaMemcpyHostToDevice, st));
+            if (!rc) rc = cuda_rc(launch_hyper_refresh(d.mu64, d.lam64, K, kp, d.lam32, d.lammu32, st));
+            in += K + K * K;
+        }
+    }
+    if (!rc) {
+        unsigned long long sw = sweep;
+        rc = cuda_rc(cudaMemcpyAsync(&h->ctl->sweep, &sw, sizeof(sw), cudaMemcpyHostToDevice, st));
+    }
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(st));
+    return rc;
+}
+
+int bpmf_get_accum(bpmf_handle h, double* psum, int64_t* n_avg)
+{
+    if (!h) return BPMF_EINVAL;
+    int rc = BPMF_OK;
+    if (psum && h->T)
+        rc = cuda_rc(cudaMemcpyAsync(psum, h->psum, sizeof(double) * h->T, cudaMemcpyDeviceToHost,
+                                     h->stream));
+    Control c;
+    if (!rc) rc = cuda_rc(cudaMemcpyAsync(&c, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, h->stream));
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(h->stream));
+    if (!rc && n_avg) *n_avg = c.n_avg;
+    return rc;
+}
+
+int bpmf_set_accum(bpmf_handle h, const double* psum, int64_t n_avg)
+{
+    if (!h || n_avg < 0) return BPMF_EINVAL;
+    int rc = BPMF_OK;
+    if (psum && h->T)
+        rc = cuda_rc(cudaMemcpyAsync(h->psum, psum, sizeof(double) * h->T, cudaMemcpyHostToDevice,
+                                     h->stream));
+    long long na = n_avg;
+    if (!rc)
+        rc = cuda_rc(cudaMemcpyAsync(&h->ctl->n_avg, &na, sizeof(na), cudaMemcpyHostToDevice, h->stream));
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(h->stream));
+    return rc;
+}
+
+int bpmf_get_stats(bpmf_handle h, int32_t side, int64_t* n, double* mean, double* S)
+{
+    if (!h || (side != 0 && side != 1)) return BPMF_EINVAL;
+    const int K = h->K;
+    const DevSide& d = h->side[side];
+    int rc = BPMF_OK;
+    if (mean) rc = cuda_rc(cudaMemcpyAsync(mean, d.stats, sizeof(double) * K, cudaMemcpyDeviceToHost, h->stream));
+    if (!rc && S)
+        rc = cuda_rc(cudaMemcpyAsync(S, d.stats + K, sizeof(double) * K * K, cudaMemcpyDeviceToHost,
+                                     h->stream));
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(h->stream));
+    if (!rc && n) *n = d.rows;
+    return rc;
+}
+
+int bpmf_debug_means(bpmf_handle h, int32_t side, float* out)
+{
+    if (!h || (side != 0 && side != 1) || !out) return BPMF_EINVAL;
+    const DevSide& d = h->side[side];
+    if (!d.means) return BPMF_EINVAL;
+    int rc = copy_packed_d2h(d.means, d.rows, h->K, h->kp, out, h->stream);
+    if (!rc) rc = cuda_rc(cudaStreamSynchronize(h->stream));
+    return rc;
+}
+
+int bpmf_status(bpmf_handle h)
+{
+    if (!h) return BPMF_EINVAL;
+    return sync_status(h);
+}
+
+int bpmf_launch_count(bpmf_handle h, int64_t* launches)
+{
+    if (!h || !launches) return BPMF_EINVAL;
+    *launches = h->launches;
+    return BPMF_OK;
+}
+
+int bpmf_info(bpmf_handle h, int32_t side, int64_t* n_short, int64_t* n_long, double* rbar,
+              int64_t* device_bytes)
+{
+    if (!h || (side != 0 && side != 1)) return BPMF_EINVAL;
+    if (n_short) *n_short = h->side[side].n_short;
+    if (n_long) *n_long = h->side[side].n_long;
+    if (rbar) *rbar = h->rbar;
+    if (device_bytes) *device_bytes = h->bytes;
+    return BPMF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// bpmf_internal.cuh -- device-side structures and kernel launchers shared by the
+// translation units of the GB300 BPMF library.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bpmf {
+
+constexpr int kMaxK = 64;
+
+// Per-handle scalars that live on the device so that a whole sweep can be
+// replayed (CUDA graph) without host involvement.
+struct Control {
+    unsigned long long sweep;  // completed sweeps (Philox counter field c2)
+    long long n_avg;           // sweeps held in the running prediction sums
+    unsigned int status;       // sticky error bits (kStatus*)
+    unsigned int pad;
+    double rmse_sample;
+    double rmse_avg;
+};
+
+enum : unsigned int { kStatusNotPD = 1u, kStatusNaN = 2u, kStatusGamma = 4u };
+
+// Arguments of one row-update launch (one side, one degree bin).
+struct RowArgs {
+    const int64_t* ptr;    // rows + 1 offsets into idx/val
+    const int32_t* idx;    // other-side index of each rating
+    const float* val;      // centred rating
+    const float* Y;        // other side's factors, ldy floats per row
+    float* X;              // this side's factors (written), ldx floats per row
+    float* means;          // conditional means (ldx per row) or nullptr
+    const int32_t* rows;   // rows of this bin, longest first
+    int64_t nrows;
+    const float* lam;      // prior precision, kp x kp, identity beyond K
+    const float* lammu;    // prior precision times prior mean, kp (zero beyond K)
+    Control* ctl;
+    uint64_t seed;
+    uint32_t c3;           // Philox tag word of this side's row noise
+    int ldx, ldy;
+    int K;
+    float alpha;
+};
+
+// ---- launchers (each returns the launch error) ----------------------------
+cudaError_t launch_init_factors(float* X, int64_t rows, int K, int ld, uint64_t seed, uint32_t c3,
+                                cudaStream_t s);
+cudaError_t launch_center_values(float* val, int64_t n, double rbar, cudaStream_t s);
+
+// Hyper step, part 1: per-block partial sums of (x - shift) and (x - shift)(x - shift)^T.
+int hyper_reduce_blocks(int64_t rows, int num_sms);
+__host__ __device__ inline size_t hyper_partial_doubles(int kp)
+{
+    return (size_t)kp + (size_t)kp * kp;
+}
+cudaError_t launch_hyper_reduce(const float* X, int64_t rows, int kp, const double* shift64,
+                                double* partials, int nblocks, cudaStream_t s);
+// part 2: fixed-order sum of the partials -> sums[kp + kp*kp]
+cudaError_t launch_hyper_combine(const double* partials, int nblocks, int kp, double* sums,
+                                 cudaStream_t s);
+
+struct NWArgs {
+    const double* sums;     // kp + kp*kp raw sums from the reduction
+    const double* shift64;  // kp, shift used by the reduction (= previous mu)
+    int64_t n;              // rows of this side
+    int K, kp;
+    double beta0, nu0;
+    const double* mu0;      // K
+    const double* W0inv;    // K x K
+    uint64_t seed;
+    uint32_t c3_normal, c3_gamma;
+    Control* ctl;
+    double* stats;          // out: mean (K), S (K x K)
+    double* mu64;           // out: K    (also the next shift)
+    double* lam64;          // out: K x K
+    float* lam32;           // out: kp x kp, identity beyond K
+    float* lammu32;         // out: kp
+};
+cudaError_t launch_nw_sample(const NWArgs& a, cudaStream_t s);
+// FP32 copies of a hyper state given in FP64 (after bpmf_set_state).
+cudaError_t launch_hyper_refresh(const double* mu64, const double* lam64, int K, int kp,
+                                 float* lam32, float* lammu32, cudaStream_t s);
+
+// Row updates on CUDA cores: one warp per row (any degree).
+cudaError_t launch_rows_warp(const RowArgs& a, int kp, int num_sms, cudaStream_t s);
+
+// Test predictions.
+int predict_blocks(int64_t T, int num_sms);
+cudaError_t launch_predict(const int32_t* ti, const int32_t* tj, const float* tr, int64_t T,
+                           const float* U, const float* V, int ld, int kp, double rbar, int clip,
+                           double lo, double hi, int burn_in, double* psum, Control* ctl,
+                           double* partials, int nblocks, cudaStream_t s);
+cudaError_t launch_predict_finish(const double* partials, int nblocks, int64_t T, int burn_in,
+                                  Control* ctl, cudaStream_t s);
+cudaError_t launch_predict_points(const int32_t* i, const int32_t* j, int64_t n, const float* U,
+                                  const float* V, int ld, int kp, double rbar, int clip, double lo,
+                                  double hi, float* out, cudaStream_t s);
+cudaError_t launch_advance(Control* ctl, cudaStream_t s);
+
+}  // namespace bpmf

@@ -1,0 +1,208 @@
+// k_misc.cu -- initial factors, rating centring, test-set prediction and RMSE
+// (Alg. 1, last inner loop: "for all test points: predict rating and compute
+// RMSE"), and the sweep counter.
+#include <math.h>
+
+#include "bpmf_internal.cuh"
+#include "philox.cuh"
+
+namespace bpmf {
+
+// U or V ~ N(0, 1): row r takes normals 0..K-1 of its init stream (c1 = r,
+// c2 = 0); one thread per Philox call (four normals); padding columns are 0.
+__global__ void init_factors_kernel(float* X, int64_t rows, int K, int ld, uint64_t seed, uint32_t c3)
+{
+    const int calls = ld / 4;
+    const int64_t n = rows * calls;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / calls;
+        const int c = (int)(e % calls);
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (4 * c < K) z = normals4_f32(seed, (uint32_t)c, (uint32_t)r, 0u, c3);
+        const int k = 4 * c;
+        if (k + 0 >= K) z.x = 0.f;
+        if (k + 1 >= K) z.y = 0.f;
+        if (k + 2 >= K) z.z = 0.f;
+        if (k + 3 >= K) z.w = 0.f;
+        reinterpret_cast<float4*>(X + r * ld)[c] = z;
+    }
+}
+
+cudaError_t launch_init_factors(float* X, int64_t rows, int K, int ld, uint64_t seed, uint32_t c3,
+                                cudaStream_t s)
+{
+    const int64_t n = rows * (ld / 4);
+    const int blocks = (int)((n + 255) / 256 < 65535 * 8 ? (n + 255) / 256 : 65535 * 8);
+    if (blocks < 1) return cudaSuccess;
+    init_factors_kernel<<<blocks, 256, 0, s>>>(X, rows, K, ld, seed, c3);
+    return cudaGetLastError();
+}
+
+__global__ void center_values_kernel(float* val, int64_t n, double rbar)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        val[e] = (float)((double)val[e] - rbar);
+}
+
+cudaError_t launch_center_values(float* val, int64_t n, double rbar, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t want = (n + 255) / 256;
+    const int blocks = (int)(want < 4096 ? want : 4096);
+    center_values_kernel<<<blocks, 256, 0, s>>>(val, n, rbar);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// prediction / RMSE
+// ---------------------------------------------------------------------------
+constexpr int kPredThreads = 256;
+
+int predict_blocks(int64_t T, int num_sms)
+{
+    int64_t want = (T + kPredThreads - 1) / kPredThreads;
+    int64_t cap = (int64_t)num_sms * 4;
+    if (want > cap) want = cap;
+    if (want < 1) want = 1;
+    return (int)want;
+}
+
+__device__ __forceinline__ float dot_row(const float* __restrict__ u, const float* __restrict__ v,
+                                         int kp)
+{
+    float s = 0.f;
+    for (int k = 0; k < kp; k += 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(u + k));
+        const float4 b = __ldg(reinterpret_cast<const float4*>(v + k));
+        s = fmaf(a.x, b.x, s);
+        s = fmaf(a.y, b.y, s);
+        s = fmaf(a.z, b.z, s);
+        s = fmaf(a.w, b.w, s);
+    }
+    return s;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    return s;
+}
+
+__global__ void __launch_bounds__(kPredThreads) predict_kernel(
+    const int32_t* __restrict__ ti, const int32_t* __restrict__ tj, const float* __restrict__ tr,
+    int64_t T, const float* __restrict__ U, const float* __restrict__ V, int ld, int kp,
+    double rbar, int clip, double lo, double hi, int burn_in, double* __restrict__ psum,
+    const Control* __restrict__ ctl, double* __restrict__ partials)
+{
+    __shared__ double red[kPredThreads / 32];
+    const int acc = (long long)ctl->sweep >= (long long)burn_in ? 1 : 0;
+    const long long n_new = ctl->n_avg + acc;
+    double se = 0.0, sa = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = ti[t], j = tj[t];
+        double p = rbar + (double)dot_row(U + (int64_t)i * ld, V + (int64_t)j * ld, kp);
+        if (clip) p = fmin(fmax(p, lo), hi);
+        const double r = (double)tr[t];
+        se += (p - r) * (p - r);
+        double ps = psum[t];
+        if (acc) {
+            ps += p;
+            psum[t] = ps;
+        }
+        if (n_new > 0) {
+            const double pa = ps / (double)n_new;
+            sa += (pa - r) * (pa - r);
+        }
+    }
+    const double bse = block_sum(se, red);
+    const double bsa = block_sum(sa, red);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = bse;
+        partials[2 * blockIdx.x + 1] = bsa;
+    }
+}
+
+cudaError_t launch_predict(const int32_t* ti, const int32_t* tj, const float* tr, int64_t T,
+                           const float* U, const float* V, int ld, int kp, double rbar, int clip,
+                           double lo, double hi, int burn_in, double* psum, Control* ctl,
+                           double* partials, int nblocks, cudaStream_t s)
+{
+    predict_kernel<<<nblocks, kPredThreads, 0, s>>>(ti, tj, tr, T, U, V, ld, kp, rbar, clip, lo,
+                                                    hi, burn_in, psum, ctl, partials);
+    return cudaGetLastError();
+}
+
+__global__ void predict_finish_kernel(const double* partials, int nblocks, int64_t T, int burn_in,
+                                      Control* ctl)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int acc = (long long)ctl->sweep >= (long long)burn_in ? 1 : 0;
+    const long long n_new = ctl->n_avg + acc;
+    double se = 0.0, sa = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        se += partials[2 * b];
+        sa += partials[2 * b + 1];
+    }
+    ctl->n_avg = n_new;
+    if (T > 0) {
+        ctl->rmse_sample = sqrt(se / (double)T);
+        ctl->rmse_avg = n_new > 0 ? sqrt(sa / (double)T) : (double)NAN;
+    } else {
+        ctl->rmse_sample = (double)NAN;
+        ctl->rmse_avg = (double)NAN;
+    }
+}
+
+cudaError_t launch_predict_finish(const double* partials, int nblocks, int64_t T, int burn_in,
+                                  Control* ctl, cudaStream_t s)
+{
+    predict_finish_kernel<<<1, 32, 0, s>>>(partials, nblocks, T, burn_in, ctl);
+    return cudaGetLastError();
+}
+
+__global__ void predict_points_kernel(const int32_t* __restrict__ pi, const int32_t* __restrict__ pj,
+                                      int64_t n, const float* __restrict__ U,
+                                      const float* __restrict__ V, int ld, int kp, double rbar,
+                                      int clip, double lo, double hi, float* __restrict__ out)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        double p = rbar + (double)dot_row(U + (int64_t)pi[t] * ld, V + (int64_t)pj[t] * ld, kp);
+        if (clip) p = fmin(fmax(p, lo), hi);
+        out[t] = (float)p;
+    }
+}
+
+cudaError_t launch_predict_points(const int32_t* i, const int32_t* j, int64_t n, const float* U,
+                                  const float* V, int ld, int kp, double rbar, int clip, double lo,
+                                  double hi, float* out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t want = (n + 255) / 256;
+    const int blocks = (int)(want < 4096 ? want : 4096);
+    predict_points_kernel<<<blocks, 256, 0, s>>>(i, j, n, U, V, ld, kp, rbar, clip, lo, hi, out);
+    return cudaGetLastError();
+}
+
+__global__ void advance_kernel(Control* ctl)
+{
+    if (threadIdx.x == 0) ctl->sweep += 1ull;
+}
+
+cudaError_t launch_advance(Control* ctl, cudaStream_t s)
+{
+    advance_kernel<<<1, 32, 0, s>>>(ctl);
+    return cudaGetLastError();
+}
+
+}  // namespace bpmf

@@ -1,0 +1,291 @@
+// k_rows_warp.cu -- per-row conditional update on CUDA cores, one warp per row.
+//
+// For row i of one side (Alg. 1 inner loops; Sec. 2 and Sec. 3.1):
+//   Lambda_i = Lambda_X + alpha sum_c y_c y_c^T      (Gram of gathered rows)
+//   b_i      = alpha sum_c r_c y_c + Lambda_X mu_X
+//   L L^T = Lambda_i (Cholesky instead of an inverse, Sec. 3.1)
+//   x_i = L^{-T} (L^{-1} b_i + z),  z ~ N(0, I) from the row's Philox stream
+// which equals mean + L^{-T} z with mean = Lambda_i^{-1} b_i.
+//
+// Layout inside the warp (KT = K rounded up to 16, K <= 64):
+//   gather : 32 ratings per chunk, each lane loads float4 pieces of the
+//            gathered rows into a shared-memory stage (coalesced 16-B loads);
+//   Gram   : lane owns rows i1 = lane and i2 = 63 - lane of Lambda_i (65
+//            lower-triangle entries for KT = 64, balanced) and adds
+//            y[i] * y[0..KT) per rating, y read as shared-memory broadcasts;
+//   Cholesky: on the same registers; column k of L is published through
+//            shared memory each step and every lane updates its own rows.
+//   solves : forward substitution with the pivot broadcast by shuffle, back
+//            substitution reading L from shared memory.
+#include "bpmf_internal.cuh"
+#include "philox.cuh"
+
+namespace bpmf {
+
+constexpr int kWarpsPerCta = 4;
+constexpr int kChunk = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int KT>
+struct WarpLayout {
+    static constexpr int NR1 = KT < 32 ? KT : 32;  // rows owned as i1 = lane
+    static constexpr bool TWO = KT > 32;           // rows owned as i2 = 63 - lane
+    static constexpr int LD = KT + 1;              // row stride of the square buffer
+    static constexpr int F4 = KT / 4;              // float4 per gathered row
+    static constexpr int RPI = 32 / F4;            // gathered rows per warp load
+    static constexpr int STAGE = kChunk * KT;
+    static constexpr int SQ = KT * LD;
+    static constexpr int PER_WARP = STAGE + SQ + 2 * KT + KT + KT + kChunk;  // floats
+    static constexpr int PER_WARP_ALIGNED = (PER_WARP + 3) & ~3;
+};
+
+template <int KT>
+__global__ void __launch_bounds__(kWarpsPerCta * 32) rows_warp_kernel(RowArgs a)
+{
+    using W = WarpLayout<KT>;
+    extern __shared__ float4 dyn_smem4[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    float* sm = reinterpret_cast<float*>(dyn_smem4) + wib * W::PER_WARP_ALIGNED;
+    float* stage = sm;
+    float* sq = stage + W::STAGE;
+    float* colbuf = sq + W::SQ;
+    float* dinv = colbuf + 2 * KT;
+    float* zb = dinv + KT;
+    float* rb = zb + KT;
+
+    const uint32_t sweep = (uint32_t)a.ctl->sweep;
+    const int i1 = lane;
+    const int i2 = 63 - lane;
+    const bool v1 = i1 < KT;
+    const bool v2 = W::TWO && i2 < KT;
+    const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerCta;
+    bool bad = false;
+
+    for (int64_t q = (int64_t)blockIdx.x * kWarpsPerCta + wib; q < a.nrows; q += nwarps) {
+        const int row = a.rows[q];
+        const int64_t p0 = a.ptr[row], p1 = a.ptr[row + 1];
+
+        // Gram rows i1, i2 accumulate in the registers the Cholesky works on
+        float a1[W::NR1];
+        float a2[W::TWO ? KT : 1];
+#pragma unroll
+        for (int j = 0; j < W::NR1; ++j) a1[j] = 0.f;
+#pragma unroll
+        for (int j = 0; j < (W::TWO ? KT : 1); ++j) a2[j] = 0.f;
+        float rhs1 = 0.f, rhs2 = 0.f;
+
+        for (int64_t base = p0; base < p1; base += kChunk) {
+            const int cnt = (int)min((int64_t)kChunk, p1 - base);
+            int c = 0;
+            float r = 0.f;
+            if (lane < cnt) {
+                c = __ldg(a.idx + base + lane);
+                r = __ldg(a.val + base + lane);
+            }
+            rb[lane] = r;
+            // gather the chunk's rows of Y into the stage (rows >= cnt are zero)
+            const int f = lane % W::F4, sub = lane / W::F4;
+#pragma unroll 4
+            for (int it = 0; it < kChunk / W::RPI; ++it) {
+                const int qq = it * W::RPI + sub;
+                const int cq = __shfl_sync(kFull, c, qq & 31);
+                if (sub < W::RPI) {
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (qq < cnt)
+                        v = __ldg(reinterpret_cast<const float4*>(a.Y + (int64_t)cq * a.ldy) + f);
+                    reinterpret_cast<float4*>(stage + qq * KT)[f] = v;
+                }
+            }
+            __syncwarp();
+            // one rating at a time: row i of the Gram += y[i] * y (lower part used)
+#pragma unroll 2
+            for (int qq = 0; qq < cnt; ++qq) {
+                const float* srow = stage + qq * KT;
+                const float rq = rb[qq];
+                const float x1 = v1 ? srow[i1] : 0.f;
+                const float x2 = v2 ? srow[i2] : 0.f;
+                rhs1 = fmaf(rq, x1, rhs1);
+                rhs2 = fmaf(rq, x2, rhs2);
+#pragma unroll
+                for (int j4 = 0; j4 < KT; j4 += 4) {
+                    const float4 y4 = *reinterpret_cast<const float4*>(srow + j4);
+                    const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = j4 + u;
+                        if (j < W::NR1) a1[j < W::NR1 ? j : 0] = fmaf(x1, yv[u], a1[j < W::NR1 ? j : 0]);
+                        if (W::TWO) a2[W::TWO ? j : 0] = fmaf(x2, yv[u], a2[W::TWO ? j : 0]);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        // Lambda_i rows = Lambda_X rows + alpha * Gram rows; b = alpha * rhs + Lambda_X mu_X
+#pragma unroll
+        for (int j = 0; j < W::NR1; ++j)
+            a1[j] = v1 ? fmaf(a.alpha, a1[j], __ldg(a.lam + i1 * KT + j)) : (j == 0 ? 1.f : 0.f);
+        if (W::TWO) {
+#pragma unroll
+            for (int j = 0; j < KT; ++j)
+                a2[W::TWO ? j : 0] = v2 ? fmaf(a.alpha, a2[W::TWO ? j : 0], __ldg(a.lam + i2 * KT + j))
+                                        : 0.f;
+        }
+        float b1 = v1 ? fmaf(a.alpha, rhs1, __ldg(a.lammu + i1)) : 0.f;
+        float b2 = v2 ? fmaf(a.alpha, rhs2, __ldg(a.lammu + i2)) : 0.f;
+
+        // ---- Cholesky, right-looking, column k published through shared memory
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            float* cb = colbuf + (k & 1) * KT;
+            const int owner = k < 32 ? k : 63 - k;
+            float pv;
+            if (k < W::NR1) pv = a1[k];
+            else pv = a2[W::TWO ? k : 0];
+            float piv = __shfl_sync(kFull, pv, owner);
+            if (!(piv > 0.f && piv < INFINITY)) {  // also catches NaN
+                bad = true;
+                piv = 1.f;
+            }
+            const float rinv = rsqrtf(piv);
+            if (lane == 0) dinv[k] = rinv;
+            float l1 = 0.f, l2 = 0.f;
+            if (k < W::NR1) {
+                if (i1 > k) a1[k] *= rinv;
+                else if (i1 == k) a1[k] = piv * rinv;
+                l1 = a1[k];
+                if (i1 > k && v1) cb[i1] = l1;
+            }
+            if (W::TWO) {
+                const int kk = W::TWO ? k : 0;
+                if (i2 > k) a2[kk] *= rinv;
+                else if (i2 == k) a2[kk] = piv * rinv;
+                l2 = a2[kk];
+                if (i2 > k && v2) cb[i2] = l2;
+            }
+            __syncwarp();
+            // trailing update a[j] -= L[i][k] L[j][k] for j > k
+#pragma unroll
+            for (int j4 = ((k + 1) / 4) * 4; j4 < KT; j4 += 4) {
+                const float4 cv = *reinterpret_cast<const float4*>(cb + j4);
+                const float cj[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j4 + u;
+                    if (j > k) {
+                        if (j < W::NR1) a1[j < W::NR1 ? j : 0] = fmaf(-l1, cj[u], a1[j < W::NR1 ? j : 0]);
+                        if (W::TWO) a2[W::TWO ? j : 0] = fmaf(-l2, cj[u], a2[W::TWO ? j : 0]);
+                    }
+                }
+            }
+        }
+
+        // ---- forward substitution y = L^{-1} b (in place in b1, b2)
+#pragma unroll
+        for (int k = 0; k < KT; ++k) {
+            const int owner = k < 32 ? k : 63 - k;
+            const float bk = __shfl_sync(kFull, k < 32 ? b1 : b2, owner);
+            const float yk = bk * dinv[k];
+            if (k < W::NR1) {
+                if (i1 == k) b1 = yk;
+                else if (i1 > k) b1 = fmaf(-a1[k < W::NR1 ? k : 0], yk, b1);
+            }
+            if (W::TWO) {
+                if (i2 == k) b2 = yk;
+                else if (i2 > k) b2 = fmaf(-a2[W::TWO ? k : 0], yk, b2);
+            }
+        }
+        // ---- noise z (zero beyond K) and L to shared memory for the back solve
+        if (lane < KT / 4) {
+            const float4 z4 = normals4_f32(a.seed, (uint32_t)lane, (uint32_t)row, sweep, a.c3);
+            const int kk = 4 * lane;
+            zb[kk + 0] = kk + 0 < a.K ? z4.x : 0.f;
+            zb[kk + 1] = kk + 1 < a.K ? z4.y : 0.f;
+            zb[kk + 2] = kk + 2 < a.K ? z4.z : 0.f;
+            zb[kk + 3] = kk + 3 < a.K ? z4.w : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < W::NR1; ++j)
+            if (v1 && j <= i1) sq[i1 * W::LD + j] = a1[j];
+        if (W::TWO) {
+#pragma unroll
+            for (int j = 0; j < KT; ++j)
+                if (v2 && j <= i2) sq[i2 * W::LD + j] = a2[W::TWO ? j : 0];
+        }
+        __syncwarp();
+        float t1 = b1 + (v1 ? zb[i1] : 0.f);
+        float t2 = b2 + (v2 ? zb[i2] : 0.f);
+        float m1 = b1, m2 = b2;
+        const bool want_means = a.means != nullptr;
+
+        // ---- back substitution x = L^{-T} t
+#pragma unroll
+        for (int i = KT - 1; i >= 0; --i) {
+            const int owner = i < 32 ? i : 63 - i;
+            const float di = dinv[i];
+            const float ui = __shfl_sync(kFull, i < 32 ? t1 : t2, owner) * di;
+            float mi = 0.f;
+            if (want_means) mi = __shfl_sync(kFull, i < 32 ? m1 : m2, owner) * di;
+            const float* Lrow = sq + i * W::LD;
+            if (i1 == i) { t1 = ui; m1 = mi; }
+            else if (i1 < i && v1) {
+                const float l = Lrow[i1];
+                t1 = fmaf(-l, ui, t1);
+                m1 = fmaf(-l, mi, m1);
+            }
+            if (W::TWO) {
+                if (i2 == i) { t2 = ui; m2 = mi; }
+                else if (i2 < i && v2) {
+                    const float l = Lrow[i2];
+                    t2 = fmaf(-l, ui, t2);
+                    m2 = fmaf(-l, mi, m2);
+                }
+            }
+        }
+        float* xr = a.X + (int64_t)row * a.ldx;
+        if (v1) xr[i1] = t1;
+        if (v2) xr[i2] = t2;
+        if (want_means) {
+            float* mr = a.means + (int64_t)row * a.ldx;
+            if (v1) mr[i1] = m1;
+            if (v2) mr[i2] = m2;
+        }
+        __syncwarp();
+    }
+    if (bad && lane == 0) atomicOr(&a.ctl->status, kStatusNotPD);
+}
+
+template <int KT>
+static cudaError_t launch_kt(const RowArgs& a, int num_sms, cudaStream_t s)
+{
+    using W = WarpLayout<KT>;
+    const size_t smem = sizeof(float) * (size_t)W::PER_WARP_ALIGNED * kWarpsPerCta;
+    cudaError_t e = cudaFuncSetAttribute(rows_warp_kernel<KT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_warp_kernel<KT>,
+                                                      kWarpsPerCta * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int64_t need = (a.nrows + kWarpsPerCta - 1) / kWarpsPerCta;
+    int64_t grid = (int64_t)num_sms * per_sm;
+    if (need < grid) grid = need;
+    if (grid < 1) return cudaSuccess;
+    rows_warp_kernel<KT><<<(unsigned)grid, kWarpsPerCta * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_warp(const RowArgs& a, int kp, int num_sms, cudaStream_t s)
+{
+    if (a.nrows <= 0) return cudaSuccess;
+    switch (kp) {
+    case 16: return launch_kt<16>(a, num_sms, s);
+    case 32: return launch_kt<32>(a, num_sms, s);
+    case 48: return launch_kt<48>(a, num_sms, s);
+    case 64: return launch_kt<64>(a, num_sms, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace bpmf

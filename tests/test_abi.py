@@ -1,0 +1,114 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point of
+include/bpmf.h; argument validation happens on the host before any CUDA call.
+No kernel runs here (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bpmf.h")
+
+
+@pytest.fixture(scope="module")
+def bp():
+    from paper_1705_10633_gb300 import _build
+    _build.build()
+    import paper_1705_10633_gb300 as bp
+    bp.lib()
+    return bp
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(bpmf_\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("bpmf_create", "bpmf_sweep", "bpmf_predict", "bpmf_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(bp):
+    L = C.CDLL(bp.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_binding_has_the_same_names(bp):
+    for name in declared_functions():
+        assert hasattr(bp, name), name
+
+
+def test_strerror(bp):
+    assert bp.bpmf_strerror(0) == "ok"
+    assert "invalid" in bp.bpmf_strerror(-1)
+    assert bp.bpmf_strerror(12345) == "unknown error"
+
+
+def test_destroy_null_is_ok(bp):
+    assert bp.lib().bpmf_destroy(None) == 0
+
+
+def _tiny():
+    ptr = np.array([0, 2, 3], dtype=np.int64)
+    col = np.array([0, 2, 1], dtype=np.int32)
+    val = np.array([1.0, 2.0, 3.0], dtype=np.float32)
+    return ptr, col, val
+
+
+@pytest.mark.parametrize("case", ["bad_ptr0", "decreasing", "col_range", "neg_col", "K0", "K65",
+                                  "nu0", "alpha", "W0", "test_range", "order"])
+def test_create_rejects_malformed_input(bp, case):
+    ptr, col, val = _tiny()
+    M, N, K = 2, 3, 4
+    kw = {}
+    ti = tj = tr = None
+    if case == "bad_ptr0":
+        ptr = np.array([1, 2, 3], dtype=np.int64)
+    elif case == "decreasing":
+        ptr = np.array([0, 3, 2], dtype=np.int64)
+    elif case == "col_range":
+        col = np.array([0, 3, 1], dtype=np.int32)
+    elif case == "neg_col":
+        col = np.array([0, -1, 1], dtype=np.int32)
+    elif case == "K0":
+        K = 0
+    elif case == "K65":
+        K = 65
+    elif case == "nu0":
+        kw["nu0"] = K - 0.5
+    elif case == "alpha":
+        kw["alpha"] = 0.0
+    elif case == "W0":
+        kw["W0"] = -np.eye(K)
+    elif case == "order":
+        kw["order"] = 2
+    elif case == "test_range":
+        ti, tj, tr = np.array([5], np.int32), np.array([0], np.int32), np.array([1.0], np.float32)
+    p = bp.bpmf_default_params(**kw)
+    with pytest.raises(bp.BpmfError) as ei:
+        bp.bpmf_create(M, N, K, ptr, col, val, test_i=ti, test_j=tj, test_r=tr, params=p)
+    assert ei.value.code == bp.BPMF_EINVAL
+
+
+def test_create_without_gpu_reports_cuda_error(bp):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    ptr, col, val = _tiny()
+    with pytest.raises(bp.BpmfError) as ei:
+        bp.bpmf_create(2, 3, 4, ptr, col, val)
+    assert ei.value.code == bp.BPMF_ECUDA
+
+
+def test_product_code_never_touches_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1705_10633_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in text.lower(), f
