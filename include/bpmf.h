@@ -164,6 +164,32 @@ int bpmf_info(bpmf_handle h, int32_t side, int64_t* n_short, int64_t* n_long, do
 /* Number of kernels this handle has launched so far (all phases, all sweeps). */
 int bpmf_launch_count(bpmf_handle h, int64_t* launches);
 
+/*
+ * Row statistics of a device matrix, computed without allocating any memory.
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory when they need the reduction (for example a
+ * serving process whose pool has already reserved the whole GPU, or a
+ * latency-critical loop where cudaMalloc/cudaFree would synchronise the
+ * device).  It runs the same reduction as the hyper step of a handle and
+ * writes the same quantities bpmf_get_stats returns:
+ *   mean = (1/rows) sum_r x_r,  S = (1/rows) sum_r (x_r - mean)(x_r - mean)^T.
+ *   X      : device, rows x ld FP32 with ld = K rounded up to a multiple of 16
+ *            (16, 32, 48 or 64); columns K..ld-1 are ignored.
+ *   shift  : device, K doubles subtracted before summing for accuracy (any
+ *            value near the mean; the handle uses its current mu), or NULL.
+ *   mean   : device, K doubles (written).   S : device, K x K doubles (written).
+ *   stream : cudaStream_t; the call only enqueues work and returns.
+ * Scratch lives in a fixed file-scope device array (about 5.4 MB, held on every
+ * GPU that loads the library until the process exits); K > 64 or rows outside
+ * [1, 2^31 - 1] is rejected with BPMF_EINVAL.  The first call on each device
+ * looks up the array's device address (with that device current), so make
+ * that first call before any stream capture.  All calls share the one array:
+ * calls that overlap on the GPU (other streams, other threads) race and must
+ * be serialised by the caller.  Nothing in the array needs to start at zero.
+ */
+int bpmf_row_stats_noalloc(const float* X, int64_t rows, int32_t K, const double* shift,
+                           double* mean, double* S, void* stream);
+
 /* Human-readable name of a return code (static string). */
 const char* bpmf_strerror(int code);
 

@@ -80,6 +80,7 @@ def lib():
     L.bpmf_status.argtypes = [vp]
     L.bpmf_info.argtypes = [vp, i32, P(i64), P(i64), P(C.c_double), P(i64)]
     L.bpmf_launch_count.argtypes = [vp, P(i64)]
+    L.bpmf_row_stats_noalloc.argtypes = [vp, i64, i32, vp, vp, vp, vp]
     L.bpmf_strerror.argtypes = [C.c_int]
     L.bpmf_strerror.restype = C.c_char_p
     L.bpmf_destroy.argtypes = [vp]
@@ -259,6 +260,13 @@ def bpmf_launch_count(h):
     return n.value
 
 
+def bpmf_row_stats_noalloc(X_ptr, rows, K, shift_ptr, mean_ptr, S_ptr, stream=None):
+    """Device pointers in and out (see include/bpmf.h); allocates nothing."""
+    _check(lib().bpmf_row_stats_noalloc(X_ptr, int(rows), int(K), shift_ptr, mean_ptr, S_ptr,
+                                        None if stream is None else C.c_void_p(int(stream))),
+           "bpmf_row_stats_noalloc")
+
+
 def bpmf_destroy(h):
     if h:
         _check(lib().bpmf_destroy(h), "bpmf_destroy")
@@ -278,5 +286,6 @@ def create_from_problem(prob, flags=0, seed=None, burn_in=None, params=None, str
 EXPORTED = ["bpmf_default_params", "bpmf_create", "bpmf_sweep", "bpmf_step", "bpmf_predict",
             "bpmf_get_state", "bpmf_set_state", "bpmf_get_accum", "bpmf_set_accum",
             "bpmf_get_stats", "bpmf_debug_means", "bpmf_status", "bpmf_info", "bpmf_launch_count",
+            "bpmf_row_stats_noalloc",
             "bpmf_strerror",
             "bpmf_destroy"]
