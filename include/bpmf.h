@@ -48,6 +48,9 @@ extern "C" {
 #define BPMF_DEBUG_MEANS 0x4u /* keep each row's conditional mean (bpmf_debug_means)      */
 #define BPMF_NO_CENTER 0x8u   /* do not subtract the training mean from the ratings       */
 #define BPMF_CUDA_CORE_GRAM 0x10u /* every row on the CUDA-core (FP32 FMA) kernel         */
+#define BPMF_TEST_STALL 0x100u /* test only: the tensor-core kernel's gather producers never
+                                  signal, so its bounded waits run out and the sweep reports
+                                  BPMF_ETIMEOUT (exercises failure detection without a fault) */
 
 /* ---- sides and phases --------------------------------------------------- */
 #define BPMF_USER 0  /* rows of R, factors U, CSR */
@@ -80,7 +83,8 @@ typedef struct {
     uint32_t flags;     /* BPMF_* flags                                                  */
     double clip_lo, clip_hi;
     int32_t long_min_degree; /* rows with at least this many ratings use the tensor-core
-                                kernel; <= 0 = library default                          */
+                                kernel (K in 49..64); <= 0 = library default (48)      */
+    int32_t wait_timeout_ms; /* limit of every device-side wait, <= 0 = 2000 ms         */
     bpmf_alloc_fn alloc; /* NULL = cudaMalloc / cudaFree */
     bpmf_free_fn free;
     void* alloc_ctx;
@@ -153,7 +157,8 @@ int bpmf_get_stats(bpmf_handle h, int32_t side, int64_t* n, double* mean, double
  * needs BPMF_DEBUG_MEANS at create, else BPMF_EINVAL. */
 int bpmf_debug_means(bpmf_handle h, int32_t side, float* out);
 
-/* Sticky device status: BPMF_OK, BPMF_ENOTPD, BPMF_ENAN or BPMF_EGAMMA.  Syncs. */
+/* Sticky device status: BPMF_OK, BPMF_ENOTPD, BPMF_ENAN, BPMF_EGAMMA or
+ * BPMF_ETIMEOUT.  Syncs the handle's stream. */
 int bpmf_status(bpmf_handle h);
 
 /* Diagnostics: number of rows of `side` on the CUDA-core kernel and on the

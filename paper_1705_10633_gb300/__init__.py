@@ -27,6 +27,7 @@ BPMF_CLIP = 0x2
 BPMF_DEBUG_MEANS = 0x4
 BPMF_NO_CENTER = 0x8
 BPMF_CUDA_CORE_GRAM = 0x10
+BPMF_TEST_STALL = 0x100
 
 BPMF_USER, BPMF_MOVIE = 0, 1
 (BPMF_PHASE_HYPER_USER, BPMF_PHASE_HYPER_MOVIE, BPMF_PHASE_ROWS_USER, BPMF_PHASE_ROWS_MOVIE,
@@ -42,6 +43,7 @@ class bpmf_params(C.Structure):
                 ("seed", C.c_uint64), ("job_id", C.c_uint32), ("burn_in", C.c_int32),
                 ("order", C.c_int32), ("flags", C.c_uint32), ("clip_lo", C.c_double),
                 ("clip_hi", C.c_double), ("long_min_degree", C.c_int32),
+                ("wait_timeout_ms", C.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 

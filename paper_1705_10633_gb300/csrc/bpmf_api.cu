@@ -17,7 +17,8 @@ using namespace bpmf;
 
 namespace {
 
-constexpr int kDefaultLongMinDegree = 64;
+constexpr int kDefaultLongMinDegree = 48;
+constexpr int kDefaultWaitTimeoutMs = 2000;
 
 struct DevSide {
     int64_t rows = 0;
@@ -25,6 +26,8 @@ struct DevSide {
     int32_t* idx = nullptr;
     float* val = nullptr;
     float* X = nullptr;
+    __half* Xh = nullptr;  // FP16 split of X, kept when the tensor-core kernel is on
+    __half* Xl = nullptr;
     float* means = nullptr;
     int32_t* bin_rows = nullptr;  // short bin first, then long bin, each longest first
     int64_t n_short = 0, n_long = 0;
@@ -47,6 +50,7 @@ struct bpmf_ctx {
     cudaStream_t stream = nullptr;
     int64_t M = 0, N = 0, nnz = 0, T = 0;
     int K = 0, kp = 0;
+    bool tc = false;  // long rows on the tensor-core kernel
     bpmf_params p{};
     std::vector<double> mu0, W0;
     double rbar = 0.0;
@@ -194,6 +198,7 @@ int sync_status(bpmf_ctx* h)
     if (c.status & kStatusNotPD) return BPMF_ENOTPD;
     if (c.status & kStatusNaN) return BPMF_ENAN;
     if (c.status & kStatusGamma) return BPMF_EGAMMA;
+    if (c.status & kStatusTimeout) return BPMF_ETIMEOUT;
     return BPMF_OK;
 }
 
@@ -232,12 +237,17 @@ int phase_rows(bpmf_ctx* h, int s)
     DevSide& d = h->side[s];
     const DevSide& o = h->side[1 - s];
     RowArgs a;
+    memset(&a, 0, sizeof(a));
     a.ptr = d.ptr;
     a.idx = d.idx;
     a.val = d.val;
     a.Y = o.X;
     a.ldy = h->kp;
     a.X = d.X;
+    a.Xh = d.Xh;
+    a.Xl = d.Xl;
+    a.Yh = o.Xh;
+    a.Yl = o.Xl;
     a.ldx = h->kp;
     a.means = d.means;
     a.lam = d.lam32;
@@ -247,12 +257,30 @@ int phase_rows(bpmf_ctx* h, int s)
     a.c3 = d.tag_row;
     a.K = h->K;
     a.alpha = (float)h->p.alpha;
-    // every bin runs on the CUDA-core kernel in this build; the long bin is
-    // ordered separately so a dedicated long-row kernel can take it over
+    a.timeout_ns = (int64_t)(h->p.wait_timeout_ms > 0 ? h->p.wait_timeout_ms : kDefaultWaitTimeoutMs) *
+                   1000000LL;
+    a.test_stall = (h->p.flags & BPMF_TEST_STALL) ? 1 : 0;
+    cudaError_t e = cudaSuccess;
+    if (!h->tc) {
+        // every row on the CUDA-core kernel
+        a.rows = d.bin_rows;
+        a.nrows = d.n_short + d.n_long;
+        if (a.nrows > 0) h->launches += 1;
+        return cuda_rc(launch_rows_warp(a, h->kp, h->num_sms, h->stream));
+    }
     a.rows = d.bin_rows;
-    a.nrows = d.n_short + d.n_long;
-    if (a.nrows > 0) h->launches += 1;
-    return cuda_rc(launch_rows_warp(a, h->kp, h->num_sms, h->stream));
+    a.nrows = d.n_short;
+    if (a.nrows > 0) {
+        h->launches += 1;
+        e = launch_rows_warp(a, h->kp, h->num_sms, h->stream);
+    }
+    a.rows = d.bin_rows + d.n_short;
+    a.nrows = d.n_long;
+    if (e == cudaSuccess && a.nrows > 0) {
+        h->launches += 1;
+        e = launch_rows_tc(a, h->num_sms, h->stream);
+    }
+    return cuda_rc(e);
 }
 
 int phase_predict(bpmf_ctx* h)
@@ -369,6 +397,7 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
     h->N = N;
     h->K = K;
     h->kp = (K + 15) / 16 * 16;
+    h->tc = h->kp == 64 && !(prm.flags & BPMF_CUDA_CORE_GRAM);
     h->T = T;
     h->nnz = csr_ptr[M];
     h->stream = (cudaStream_t)cuda_stream;
@@ -429,6 +458,8 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
                   alloc_n(h, &d.sums, hyper_partial_doubles(kp)) &&
                   alloc_n(h, &d.stats, (size_t)K + (size_t)K * K);
         if (ok && (prm.flags & BPMF_DEBUG_MEANS)) ok = alloc_n(h, &d.means, (size_t)d.rows * kp);
+        if (ok && h->tc)
+            ok = alloc_n(h, &d.Xh, (size_t)d.rows * kp) && alloc_n(h, &d.Xl, (size_t)d.rows * kp);
         if (!ok) {
             rc = BPMF_ENOMEM;
             break;
@@ -445,6 +476,7 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
                                 cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = launch_center_values(d.val, h->nnz, h->rbar, st);
         if (e == cudaSuccess) e = launch_init_factors(d.X, d.rows, K, kp, prm.seed, d.tag_init, st);
+        if (e == cudaSuccess && d.Xh) e = launch_split_factors(d.X, d.rows, kp, d.Xh, d.Xl, st);
         if (e == cudaSuccess && d.means) e = cudaMemsetAsync(d.means, 0, sizeof(float) * d.rows * kp, st);
         // initial hyper state: mu = 0, Lambda = I
         std::vector<double> I((size_t)K * K, 0.0);
@@ -518,6 +550,7 @@ int bpmf_sweep(bpmf_handle h, int32_t n_sweeps, double* rmse_sample, double* rms
         if (c.status & kStatusNotPD) return BPMF_ENOTPD;
         if (c.status & kStatusNaN) return BPMF_ENAN;
         if (c.status & kStatusGamma) return BPMF_EGAMMA;
+        if (c.status & kStatusTimeout) return BPMF_ETIMEOUT;
     }
     return BPMF_OK;
 }
@@ -598,6 +631,7 @@ int bpmf_set_state(bpmf_handle h, const float* U, const float* V, const double* 
             rc = cuda_rc(cudaMemcpy2DAsync(d.X, sizeof(float) * kp, src[s], sizeof(float) * K,
                                            sizeof(float) * K, (size_t)d.rows,
                                            cudaMemcpyHostToDevice, st));
+        if (!rc && d.Xh) rc = cuda_rc(launch_split_factors(d.X, d.rows, kp, d.Xh, d.Xl, st));
     }
     if (!rc && hyper) {
         const double* in = hyper;

@@ -1,6 +1,7 @@
 // bpmf_internal.cuh -- device-side structures and kernel launchers shared by the
 // translation units of the GB300 BPMF library.  Not part of the public ABI.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,6 +30,10 @@ struct RowArgs {
     const float* Y;        // other side's factors, ldy floats per row
     float* X;              // this side's factors (written), ldx floats per row
     float* means;          // conditional means (ldx per row) or nullptr
+    __half* Xh;            // FP16 split of X (hi, lo), ldx per row, or nullptr
+    __half* Xl;
+    const __half* Yh;      // FP16 split of Y (tensor-core kernel only)
+    const __half* Yl;
     const int32_t* rows;   // rows of this bin, longest first
     int64_t nrows;
     const float* lam;      // prior precision, kp x kp, identity beyond K
@@ -36,6 +41,8 @@ struct RowArgs {
     Control* ctl;
     uint64_t seed;
     uint32_t c3;           // Philox tag word of this side's row noise
+    int64_t timeout_ns;    // bound on every device wait (tensor-core kernel)
+    int test_stall;        // test only: producers never signal (exercises the timeout path)
     int ldx, ldy;
     int K;
     float alpha;
@@ -82,6 +89,13 @@ cudaError_t launch_hyper_refresh(const double* mu64, const double* lam64, int K,
 
 // Row updates on CUDA cores: one warp per row (any degree).
 cudaError_t launch_rows_warp(const RowArgs& a, int kp, int num_sms, cudaStream_t s);
+// Row updates with the Gram on tensor cores (kp == 64, rows of the long bin).
+cudaError_t launch_rows_tc(const RowArgs& a, int num_sms, cudaStream_t s);
+// FP16 hi/lo split of a factor matrix (after init or set_state).
+cudaError_t launch_split_factors(const float* X, int64_t rows, int ld, __half* Xh, __half* Xl,
+                                 cudaStream_t s);
+
+enum : unsigned int { kStatusTimeout = 8u };
 
 // Test predictions.
 int predict_blocks(int64_t T, int num_sms);

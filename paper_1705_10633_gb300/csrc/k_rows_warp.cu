@@ -19,12 +19,12 @@
 //            substitution reading L from shared memory.
 #include "bpmf_internal.cuh"
 #include "philox.cuh"
+#include "rows_common.cuh"
 
 namespace bpmf {
 
 constexpr int kWarpsPerCta = 4;
 constexpr int kChunk = 32;
-constexpr unsigned kFull = 0xffffffffu;
 
 template <int KT>
 struct WarpLayout {
@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) rows_warp_kernel(RowArgs a)
         const int64_t p0 = a.ptr[row], p1 = a.ptr[row + 1];
 
         // Gram rows i1, i2 accumulate in the registers the Cholesky works on
-        float a1[W::NR1];
-        float a2[W::TWO ? KT : 1];
+        float a1[RowRegs<KT>::NR1];
+        float a2[RowRegs<KT>::NA2];
 #pragma unroll
         for (int j = 0; j < W::NR1; ++j) a1[j] = 0.f;
 #pragma unroll
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) rows_warp_kernel(RowArgs a)
 #pragma unroll 4
             for (int it = 0; it < kChunk / W::RPI; ++it) {
                 const int qq = it * W::RPI + sub;
-                const int cq = __shfl_sync(kFull, c, qq & 31);
+                const int cq = __shfl_sync(kFullMask, c, qq & 31);
                 if (sub < W::RPI) {
                     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (qq < cnt)
@@ -134,122 +134,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) rows_warp_kernel(RowArgs a)
         float b1 = v1 ? fmaf(a.alpha, rhs1, __ldg(a.lammu + i1)) : 0.f;
         float b2 = v2 ? fmaf(a.alpha, rhs2, __ldg(a.lammu + i2)) : 0.f;
 
-        // ---- Cholesky, right-looking, column k published through shared memory
-#pragma unroll
-        for (int k = 0; k < KT; ++k) {
-            float* cb = colbuf + (k & 1) * KT;
-            const int owner = k < 32 ? k : 63 - k;
-            float pv;
-            if (k < W::NR1) pv = a1[k];
-            else pv = a2[W::TWO ? k : 0];
-            float piv = __shfl_sync(kFull, pv, owner);
-            if (!(piv > 0.f && piv < INFINITY)) {  // also catches NaN
-                bad = true;
-                piv = 1.f;
-            }
-            const float rinv = rsqrtf(piv);
-            if (lane == 0) dinv[k] = rinv;
-            float l1 = 0.f, l2 = 0.f;
-            if (k < W::NR1) {
-                if (i1 > k) a1[k] *= rinv;
-                else if (i1 == k) a1[k] = piv * rinv;
-                l1 = a1[k];
-                if (i1 > k && v1) cb[i1] = l1;
-            }
-            if (W::TWO) {
-                const int kk = W::TWO ? k : 0;
-                if (i2 > k) a2[kk] *= rinv;
-                else if (i2 == k) a2[kk] = piv * rinv;
-                l2 = a2[kk];
-                if (i2 > k && v2) cb[i2] = l2;
-            }
-            __syncwarp();
-            // trailing update a[j] -= L[i][k] L[j][k] for j > k
-#pragma unroll
-            for (int j4 = ((k + 1) / 4) * 4; j4 < KT; j4 += 4) {
-                const float4 cv = *reinterpret_cast<const float4*>(cb + j4);
-                const float cj[4] = {cv.x, cv.y, cv.z, cv.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = j4 + u;
-                    if (j > k) {
-                        if (j < W::NR1) a1[j < W::NR1 ? j : 0] = fmaf(-l1, cj[u], a1[j < W::NR1 ? j : 0]);
-                        if (W::TWO) a2[W::TWO ? j : 0] = fmaf(-l2, cj[u], a2[W::TWO ? j : 0]);
-                    }
-                }
-            }
-        }
-
-        // ---- forward substitution y = L^{-1} b (in place in b1, b2)
-#pragma unroll
-        for (int k = 0; k < KT; ++k) {
-            const int owner = k < 32 ? k : 63 - k;
-            const float bk = __shfl_sync(kFull, k < 32 ? b1 : b2, owner);
-            const float yk = bk * dinv[k];
-            if (k < W::NR1) {
-                if (i1 == k) b1 = yk;
-                else if (i1 > k) b1 = fmaf(-a1[k < W::NR1 ? k : 0], yk, b1);
-            }
-            if (W::TWO) {
-                if (i2 == k) b2 = yk;
-                else if (i2 > k) b2 = fmaf(-a2[W::TWO ? k : 0], yk, b2);
-            }
-        }
-        // ---- noise z (zero beyond K) and L to shared memory for the back solve
-        if (lane < KT / 4) {
-            const float4 z4 = normals4_f32(a.seed, (uint32_t)lane, (uint32_t)row, sweep, a.c3);
-            const int kk = 4 * lane;
-            zb[kk + 0] = kk + 0 < a.K ? z4.x : 0.f;
-            zb[kk + 1] = kk + 1 < a.K ? z4.y : 0.f;
-            zb[kk + 2] = kk + 2 < a.K ? z4.z : 0.f;
-            zb[kk + 3] = kk + 3 < a.K ? z4.w : 0.f;
-        }
-#pragma unroll
-        for (int j = 0; j < W::NR1; ++j)
-            if (v1 && j <= i1) sq[i1 * W::LD + j] = a1[j];
-        if (W::TWO) {
-#pragma unroll
-            for (int j = 0; j < KT; ++j)
-                if (v2 && j <= i2) sq[i2 * W::LD + j] = a2[W::TWO ? j : 0];
-        }
-        __syncwarp();
-        float t1 = b1 + (v1 ? zb[i1] : 0.f);
-        float t2 = b2 + (v2 ? zb[i2] : 0.f);
-        float m1 = b1, m2 = b2;
-        const bool want_means = a.means != nullptr;
-
-        // ---- back substitution x = L^{-T} t
-#pragma unroll
-        for (int i = KT - 1; i >= 0; --i) {
-            const int owner = i < 32 ? i : 63 - i;
-            const float di = dinv[i];
-            const float ui = __shfl_sync(kFull, i < 32 ? t1 : t2, owner) * di;
-            float mi = 0.f;
-            if (want_means) mi = __shfl_sync(kFull, i < 32 ? m1 : m2, owner) * di;
-            const float* Lrow = sq + i * W::LD;
-            if (i1 == i) { t1 = ui; m1 = mi; }
-            else if (i1 < i && v1) {
-                const float l = Lrow[i1];
-                t1 = fmaf(-l, ui, t1);
-                m1 = fmaf(-l, mi, m1);
-            }
-            if (W::TWO) {
-                if (i2 == i) { t2 = ui; m2 = mi; }
-                else if (i2 < i && v2) {
-                    const float l = Lrow[i2];
-                    t2 = fmaf(-l, ui, t2);
-                    m2 = fmaf(-l, mi, m2);
-                }
-            }
-        }
-        float* xr = a.X + (int64_t)row * a.ldx;
-        if (v1) xr[i1] = t1;
-        if (v2) xr[i2] = t2;
-        if (want_means) {
-            float* mr = a.means + (int64_t)row * a.ldx;
-            if (v1) mr[i1] = m1;
-            if (v2) mr[i2] = m2;
-        }
+        float x1, x2, m1, m2;
+        factor_solve_sample<KT>(a1, a2, b1, b2, colbuf, dinv, zb, sq, lane, a.K, a.seed,
+                                (uint32_t)row, sweep, a.c3, a.means != nullptr, x1, x2, m1, m2, bad);
+        store_row<KT>(a, row, lane, x1, x2, m1, m2);
         __syncwarp();
     }
     if (bad && lane == 0) atomicOr(&a.ctl->status, kStatusNotPD);

@@ -1,0 +1,125 @@
+"""GPU parity of the tensor-core row kernel (K padded to 64, rows of the long bin).
+
+The Gram of long rows runs on tcgen05 with an FP16 hi/lo split of the gathered
+factors; the per-row tolerance stays the FP32 path's 1e-4 (norm-wise, against
+the FP64 oracle from the same state).  Also: the full-size 480k x 18k workload
+with 1e8 ratings in the launch configuration bench.py times, checked on
+sampled rows, and the bounded-wait timeout path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from test_gpu_parity import ROW_TOL, assert_worst, rowwise_rel, step_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bp():
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1705_10633_gb300 as bp
+    bp.lib()
+    return bp
+
+
+@pytest.mark.parametrize("K", [64, 50])
+def test_long_rows_tensor_core_parity(bp, K):
+    # degrees 60..400 on both sides: ragged against the 16-rating MMA step and the
+    # 64-rating stage; a few rows below the long threshold stay on the warp kernel
+    prob = workloads.random_small(600, 300, K, 60000, seed=200 + K, n_test=400, long_rows=6,
+                                  long_deg=290)
+    for side in (0, 1):
+        deg = np.diff(prob.csr_ptr) if side == 0 else prob.col_degrees()
+        assert (deg >= 48).sum() > 0.5 * len(deg)
+    assert_worst(step_parity(bp, prob, sweeps=2))
+
+
+def test_tensor_core_and_cuda_core_paths_agree(bp):
+    prob = workloads.random_small(500, 260, 64, 30000, seed=77, n_test=100)
+    K = prob.K
+    out = []
+    for flags in (0, bp.BPMF_CUDA_CORE_GRAM):
+        h = bp.create_from_problem(prob, flags=flags, stream=bp.torch_stream())
+        try:
+            assert (bp.bpmf_info(h, 1)["n_long"] > 0) or flags
+            bp.bpmf_sweep(h, 2)
+            out.append(bp.bpmf_get_state(h, prob.M, prob.N, K))
+        finally:
+            bp.bpmf_destroy(h)
+    for side in (0, 1):
+        assert rowwise_rel(out[0][side], out[1][side]).max() <= 3 * ROW_TOL
+
+
+def test_wait_timeout_reports_status_and_context_survives(bp):
+    prob = workloads.random_small(300, 200, 64, 20000, seed=5)
+    p = bp.bpmf_default_params(alpha=prob.alpha, seed=prob.seed, flags=bp.BPMF_TEST_STALL,
+                               wait_timeout_ms=100)
+    h = bp.create_from_problem(prob, params=p, stream=bp.torch_stream())
+    try:
+        assert bp.bpmf_info(h, 1)["n_long"] > 0
+        with pytest.raises(bp.BpmfError) as ei:
+            bp.bpmf_sweep(h, 1)
+        assert ei.value.code == bp.BPMF_ETIMEOUT
+        assert bp.bpmf_status(h) == bp.BPMF_ETIMEOUT
+    finally:
+        bp.bpmf_destroy(h)
+    h = bp.create_from_problem(prob, stream=bp.torch_stream())
+    try:
+        bp.bpmf_sweep(h, 1)
+        assert bp.bpmf_status(h) == 0
+    finally:
+        bp.bpmf_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def config3():
+    return workloads.config3()
+
+
+def test_full_size_config3_sampled_rows(bp, config3):
+    """One sweep of the 480,000 x 18,000, 1e8-rating, K = 64 workload (the bench
+    configuration), each half-sweep checked on sampled rows against the oracle."""
+    prob = config3
+    K = prob.K
+    h = bp.create_from_problem(prob, flags=bp.BPMF_DEBUG_MEANS, stream=bp.torch_stream())
+    rng = np.random.default_rng(0)
+    try:
+        bp.bpmf_sweep(h, 1)  # leave the initial state
+        U, V, hyper, s = bp.bpmf_get_state(h, prob.M, prob.N, K)
+        orc = oracle.Oracle(prob, nthreads=None)
+        orc.set_factors(0, U)
+        orc.set_factors(1, V)
+        orc.set_counters(s, 0)
+        for side, hp, rp, n in ((1, bp.BPMF_PHASE_HYPER_MOVIE, bp.BPMF_PHASE_ROWS_MOVIE, prob.N),
+                                (0, bp.BPMF_PHASE_HYPER_USER, bp.BPMF_PHASE_ROWS_USER, prob.M)):
+            bp.bpmf_step(h, hp)
+            nst, mean, S = bp.bpmf_get_stats(h, side, K)
+            m_ref, S_ref = oracle.row_stats(orc.get_factors(side))
+            assert np.linalg.norm(S - S_ref) <= 1e-5 * np.linalg.norm(S_ref)
+            _, _, hyper, _ = bp.bpmf_get_state(h, prob.M, prob.N, K)
+            off = 0 if side == 0 else K + K * K
+            mu_g, Lam_g = hyper[off:off + K], hyper[off + K:off + K + K * K].reshape(K, K)
+            Lam_ref, mu_ref = orc.nw_from_stats(side, nst, mean, S, s)
+            assert np.linalg.norm(Lam_g - Lam_ref) <= 1e-9 * np.linalg.norm(Lam_ref)
+            orc.set_hyper(side, mu_g, Lam_g)
+            bp.bpmf_step(h, rp)
+            deg = np.diff(prob.csr_ptr) if side == 0 else prob.col_degrees()
+            order = np.argsort(deg)
+            sample = np.unique(np.concatenate([rng.choice(n, 200, replace=False), order[-8:],
+                                               order[:8]]))
+            orc.rows_subset(side, sample)
+            Xg = bp.bpmf_get_state(h, prob.M, prob.N, K)[side]
+            Mg = bp.bpmf_debug_means(h, side, n, K)
+            ex = rowwise_rel(Xg[sample], orc.get_factors(side)[sample])
+            em = rowwise_rel(Mg[sample], orc.get_means(side)[sample])
+            worst = sorted(zip(ex, deg[sample]), reverse=True)[:5]
+            print("side %d worst (err, degree):" % side, [("%.2e" % e, int(d)) for e, d in worst])
+            assert ex.max() <= ROW_TOL, (side, worst)
+            assert em.max() <= ROW_TOL, (side, em.max(), deg[sample[np.argmax(em)]])
+            orc.set_factors(side, Xg)
+        assert bp.bpmf_status(h) == 0
+    finally:
+        bp.bpmf_destroy(h)
