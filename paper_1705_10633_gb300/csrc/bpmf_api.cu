@@ -17,7 +17,7 @@ using namespace bpmf;
 
 namespace {
 
-constexpr int kDefaultLongMinDegree = 48;
+constexpr int kDefaultLongMinDegree = 1;
 constexpr int kDefaultWaitTimeoutMs = 2000;
 
 struct DevSide {
@@ -251,6 +251,7 @@ int phase_rows(bpmf_ctx* h, int s)
     a.ldx = h->kp;
     a.means = d.means;
     a.lam = d.lam32;
+    a.lam_ct = d.lam32 + (size_t)h->kp * h->kp;
     a.lammu = d.lammu32;
     a.ctl = h->ctl;
     a.seed = h->p.seed;
@@ -452,7 +453,7 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
         bool ok = alloc_n(h, &d.ptr, d.rows + 1) && alloc_n(h, &d.idx, h->nnz) &&
                   alloc_n(h, &d.val, h->nnz) && alloc_n(h, &d.X, (size_t)d.rows * kp) &&
                   alloc_n(h, &d.bin_rows, d.rows) && alloc_n(h, &d.mu64, K) &&
-                  alloc_n(h, &d.lam64, (size_t)K * K) && alloc_n(h, &d.lam32, (size_t)kp * kp) &&
+                  alloc_n(h, &d.lam64, (size_t)K * K) && alloc_n(h, &d.lam32, (size_t)2 * kp * kp) &&
                   alloc_n(h, &d.lammu32, kp) &&
                   alloc_n(h, &d.partials, (size_t)d.red_blocks * hyper_partial_doubles(kp)) &&
                   alloc_n(h, &d.sums, hyper_partial_doubles(kp)) &&

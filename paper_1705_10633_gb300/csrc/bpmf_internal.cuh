@@ -37,6 +37,7 @@ struct RowArgs {
     const int32_t* rows;   // rows of this bin, longest first
     int64_t nrows;
     const float* lam;      // prior precision, kp x kp, identity beyond K
+    const float* lam_ct;   // the same, chunk-transposed: float4 (i, 4c..4c+3) at c * kp + i
     const float* lammu;    // prior precision times prior mean, kp (zero beyond K)
     Control* ctl;
     uint64_t seed;
@@ -79,10 +80,16 @@ struct NWArgs {
     double* stats;          // out: mean (K), S (K x K)
     double* mu64;           // out: K    (also the next shift)
     double* lam64;          // out: K x K
-    float* lam32;           // out: kp x kp, identity beyond K
+    float* lam32;           // out: kp x kp, identity beyond K, then its chunk-transposed copy
     float* lammu32;         // out: kp
 };
 cudaError_t launch_nw_sample(const NWArgs& a, cudaStream_t s);
+// Index of (i, j) in the chunk-transposed copy of a kp x kp matrix (kp a multiple
+// of 4): float4 (i, 4c .. 4c + 3) sits at float4 index c * kp + i.
+__host__ __device__ inline int chunk_t_index(int i, int j, int kp)
+{
+    return ((j >> 2) * kp + i) * 4 + (j & 3);
+}
 // FP32 copies of a hyper state given in FP64 (after bpmf_set_state).
 cudaError_t launch_hyper_refresh(const double* mu64, const double* lam64, int K, int kp,
                                  float* lam32, float* lammu32, cudaStream_t s);

@@ -301,7 +301,9 @@ __global__ void __launch_bounds__(kNWThreads) nw_sample_kernel(NWArgs a)
     const int kp = a.kp;
     for (int e = t; e < kp * kp; e += blockDim.x) {
         const int i = e / kp, j = e % kp;
-        a.lam32[e] = (i < K && j < K) ? (float)M1[i * K + j] : (i == j ? 1.f : 0.f);
+        const float v = (i < K && j < K) ? (float)M1[i * K + j] : (i == j ? 1.f : 0.f);
+        a.lam32[e] = v;
+        a.lam32[kp * kp + chunk_t_index(i, j, kp)] = v;
     }
     for (int i = t; i < kp; i += blockDim.x) {
         double s = 0.0;
@@ -337,7 +339,9 @@ __global__ void hyper_refresh_kernel(const double* mu64, const double* lam64, in
 {
     for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) {
         const int i = e / kp, j = e % kp;
-        lam32[e] = (i < K && j < K) ? (float)lam64[i * K + j] : (i == j ? 1.f : 0.f);
+        const float v = (i < K && j < K) ? (float)lam64[i * K + j] : (i == j ? 1.f : 0.f);
+        lam32[e] = v;
+        lam32[kp * kp + chunk_t_index(i, j, kp)] = v;
     }
     for (int i = threadIdx.x; i < kp; i += blockDim.x) {
         double s = 0.0;

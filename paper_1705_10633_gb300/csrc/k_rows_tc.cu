@@ -49,8 +49,9 @@ constexpr uint32_t kAccStride = 128;
 constexpr uint32_t kTileBytes = kStageRatings * 128;        // 64 ratings x 64 halves
 constexpr uint32_t kRBytes = 2048;                          // RHS operand, no swizzle
 constexpr uint32_t kStageBytes = 2 * kTileBytes + kRBytes;  // 18 KB (1 KB multiple)
-constexpr uint32_t kLamLd = 65;
-constexpr uint32_t kLamFloats = 64 * kLamLd;
+// A Lambda buffer: the lower triangle of the 64 x 64 precision in the XOR-swizzled
+// layout sw64 (row stride 64, 16-B chunks permuted by row & 7), then b (64 floats).
+constexpr uint32_t kLamFloats = 64 * 64 + 64;
 constexpr uint32_t kCholScratchFloats = 2 * 64 + 64 + 64;
 
 constexpr uint32_t kOffStages = 0;
@@ -337,10 +338,14 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
                             const uint32_t sH = sbase + kOffStages + s * kStageBytes;
                             const uint32_t sR = sH + 2 * kTileBytes;
                             for (int kb = 0; kb < (cnt + 15) / 16; ++kb) {
+                                // A = [H^T; L^T] (128 x 16); B = H, then B = L (16 x 64)
                                 const uint64_t adesc = sdesc(sH + kb * 2048, kTileBytes, 1024, 2);
+                                const uint64_t ldesc =
+                                    sdesc(sH + kTileBytes + kb * 2048, kTileBytes, 1024, 2);
                                 const uint64_t rdesc = sdesc(sR + kb * 256, 128, 1024, 0);
                                 const uint32_t acc = (base > c0 || kb > 0) ? 1u : 0u;
                                 tc_mma(dgram, adesc, adesc, kIdescGram, acc);
+                                tc_mma(dgram, adesc, ldesc, kIdescGram, 1u);
                                 tc_mma(drhs, adesc, rdesc, kIdescRhs, acc);
                             }
                             tc_commit(bar_stage_empty + 8 * s);
@@ -465,6 +470,7 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
         const int quarter = warp & 3;
         const int m = 32 * (quarter & 1) + lane;  // row of Lambda this thread serves
         const float alpha = a.alpha;
+        const float4* lam_ct4 = reinterpret_cast<const float4*>(a.lam_ct);
         uint32_t u = 0;  // accumulation chunks drained
         bool live = true;
         for (int64_t j = 0; j < nj && live; ++j) {
@@ -489,18 +495,6 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
                     live = false;
                     break;
                 }
-                tc_fence_after();
-                const uint32_t taddr = tmem_base + ((uint32_t)(32 * quarter) << 16) + slot * kAccStride;
-                uint32_t gr[64];
-                TMEM_LD16(taddr + 0, (gr + 0));
-                TMEM_LD16(taddr + 16, (gr + 16));
-                TMEM_LD16(taddr + 32, (gr + 32));
-                TMEM_LD16(taddr + 48, (gr + 48));
-                uint32_t r0, r1;
-                tmem_ld2(taddr + 64, r0, r1);
-                tmem_wait_ld();
-                tc_fence_before();
-                mbar_arrive(bar_acc_empty + 8 * slot);
                 if (first) {
                     ok = wait_bounded(bar_lam_empty + 8 * b, (uint32_t)((j / kNChol) & 1) ^ 1u, wc);
                     if (bar_any(1, 128, !ok)) {
@@ -509,31 +503,78 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
                         break;
                     }
                 }
-                rsum += __uint_as_float(r0) + __uint_as_float(r1);
-                // Lambda += alpha (H^T H + L^T H + (L^T H)^T) of this chunk; the first
-                // chunk starts from the prior precision
-                if (quarter < 2) {
+                tc_fence_after();
+                const uint32_t taddr = tmem_base + ((uint32_t)(32 * quarter) << 16) + slot * kAccStride;
+                uint32_t r0, r1;
+                tmem_ld2(taddr + 64, r0, r1);
+                // Lambda += alpha (H^T H + L^T H + (L^T H)^T) of this chunk, lower triangle
+                // (column <= row) only, 32 accumulator columns at a time; the first chunk
+                // starts from the prior precision
+                // The accumulator holds H^T (H + L) in its top 64 lanes and L^T (H + L) in
+                // its bottom 64; their sum is the chunk's Gram (H + L is the FP16 split of
+                // the other side's rows).  Bottom rows are stored first, then the top rows
+                // add theirs and, on a row's first chunk, the prior precision.  Only chunks
+                // on or below the diagonal are formed, 32 columns at a time.
+                uint32_t gr[32];
+                if (quarter >= 2) {
 #pragma unroll
-                    for (int c = 0; c < 64; ++c) {
-                        // Lambda_X is symmetric: read it by column so the lanes' loads coalesce
-                        const float base_v = first ? __ldg(a.lam + c * kKT + m) : L[m * kLamLd + c];
-                        L[m * kLamLd + c] = fmaf(alpha, __uint_as_float(gr[c]), base_v);
+                    for (int h = 0; h < 2; ++h) {
+                        TMEM_LD16(taddr + 32 * h, (gr + 0));
+                        TMEM_LD16(taddr + 32 * h + 16, (gr + 16));
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int cc = 8 * h + q;
+                            if (4 * cc <= m) {
+                                float4* p = chunk_ptr(L, m, cc);
+                                float4 v = make_float4(alpha * __uint_as_float(gr[4 * q + 0]),
+                                                       alpha * __uint_as_float(gr[4 * q + 1]),
+                                                       alpha * __uint_as_float(gr[4 * q + 2]),
+                                                       alpha * __uint_as_float(gr[4 * q + 3]));
+                                if (!first) {
+                                    const float4 o = *p;
+                                    v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+                                }
+                                *p = v;
+                            }
+                        }
                     }
                 }
                 named_bar(1, 128);
-                if (quarter >= 2) {
+                if (quarter < 2) {
 #pragma unroll
-                    for (int c = 0; c < 64; ++c) L[m * kLamLd + c] += alpha * __uint_as_float(gr[c]);
-                    named_bar(2, 64);
+                    for (int h = 0; h < 2; ++h) {
+                        TMEM_LD16(taddr + 32 * h, (gr + 0));
+                        TMEM_LD16(taddr + 32 * h + 16, (gr + 16));
+                        tmem_wait_ld();
 #pragma unroll
-                    for (int c = 0; c < 64; ++c) L[c * kLamLd + m] += alpha * __uint_as_float(gr[c]);
+                        for (int q = 0; q < 8; ++q) {
+                            const int cc = 8 * h + q;
+                            if (4 * cc <= m) {
+                                float4* p = chunk_ptr(L, m, cc);
+                                float4 o = *p;
+                                if (first) {  // chunk-transposed copy: the lanes' loads coalesce
+                                    const float4 x = __ldg(lam_ct4 + cc * 64 + m);
+                                    o.x += x.x; o.y += x.y; o.z += x.z; o.w += x.w;
+                                }
+                                o.x = fmaf(alpha, __uint_as_float(gr[4 * q + 0]), o.x);
+                                o.y = fmaf(alpha, __uint_as_float(gr[4 * q + 1]), o.y);
+                                o.z = fmaf(alpha, __uint_as_float(gr[4 * q + 2]), o.z);
+                                o.w = fmaf(alpha, __uint_as_float(gr[4 * q + 3]), o.w);
+                                *p = o;
+                            }
+                        }
+                    }
                 }
+                tc_fence_before();
+                mbar_arrive(bar_acc_empty + 8 * slot);
+                rsum += __uint_as_float(r0) + __uint_as_float(r1);
                 named_bar(1, 128);
             }
             if (!live) break;
             if (quarter >= 2) rtmp[m] = rsum;
             named_bar(1, 128);
-            if (quarter < 2) L[m * kLamLd + 64] = fmaf(alpha, rsum + rtmp[m], __ldg(a.lammu + m));
+            if (quarter < 2) L[4096 + m] = fmaf(alpha, rsum + rtmp[m], __ldg(a.lammu + m));
             mbar_arrive(bar_lam_full + 8 * b);
             named_bar(1, 128);  // rtmp is reused by the next row
         }
@@ -555,9 +596,9 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
             const int row = (int)row_ring[4 * rs + 0];
             float* L = lam_bufs + cw * kLamFloats;
             float x1, x2, m1, m2;
-            factor_solve_sample_smem<kKT>(L, colbuf, dinv, zb, lane, a.K, a.seed, (uint32_t)row,
-                                          sweep, a.c3, a.means != nullptr, x1, x2, m1, m2, bad);
-            store_row_panels<kKT>(a, row, lane, x1, x2, m1, m2);
+            factor_solve_sample_rl64(L, L + 4096, colbuf, dinv, zb, lane, a.K, a.seed, (uint32_t)row,
+                                     sweep, a.c3, a.means != nullptr, x1, x2, m1, m2, bad);
+            store_row_panels(a, row, lane, x1, x2, m1, m2);
             __syncwarp();
             mbar_arrive(bar_lam_empty + 8 * cw);
             if (lane == 0) mbar_arrive(bar_row_empty + 8 * rs);

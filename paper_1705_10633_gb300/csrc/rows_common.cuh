@@ -165,136 +165,125 @@ __device__ __forceinline__ void factor_solve_sample(float (&a1)[RowRegs<KT>::NR1
     m2 = n2;
 }
 
-// Same step for a matrix that sits in shared memory (KT = 48 or 64), in two
-// column panels so that at most two 32-entry row pieces are live in registers
-// (no spills under a 128-register budget).  sq holds Lambda_i row-major with
-// stride KT + 1 (lower triangle valid) and b_i in column KT; it is overwritten
-// with L.  Lane l owns rows r1 = l and r2 = 32 + l (the latter if l < KT - 32).
-//   panel 1: right-looking Cholesky of columns 0..31 on rows r1 (L11) and r2 (L21)
-//   update : A22 -= L21 L21^T, with L21 transposed through the unused upper block
-//   panel 2: Cholesky of the updated A22 (one row per lane)
-template <int KT>
-__device__ __forceinline__ void factor_solve_sample_smem(float* sq, float* colbuf, float* dinv,
-                                                         float* zb, int lane, int K, uint64_t seed,
-                                                         uint32_t row, uint32_t sweep, uint32_t c3,
+// ---------------------------------------------------------------------------
+// K = 64 matrices in shared memory.  Element (i, j) sits at sw64(i, j): row-major
+// with stride 64 and the 16-B chunk index XOR-ed with (i & 7).  Eight lanes that
+// access the same chunk of eight consecutive rows (float4), and 32 lanes that
+// access 32 consecutive columns of one row, both hit distinct banks.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int sw64(int i, int j)
+{
+    return i * 64 + (((j >> 2) ^ (i & 7)) << 2) + (j & 3);
+}
+
+__device__ __forceinline__ float4* chunk_ptr(float* M, int i, int c)
+{
+    return reinterpret_cast<float4*>(M + i * 64 + ((c ^ (i & 7)) << 2));
+}
+
+__device__ __forceinline__ float4 ld_chunk(const float* M, int i, int c)
+{
+    return *reinterpret_cast<const float4*>(M + i * 64 + ((c ^ (i & 7)) << 2));
+}
+
+// Column steps k0 .. k1 - 1 of a right-looking Cholesky with the forward solve
+// fused, for K = 64 with lane l owning rows r1 = l and r2 = 32 + l.  The rows are
+// kept in registers "shifted": a1[t] = A[r1][k + t] and a2[t] = A[r2][k + t] at step
+// k, so the update  A[r][k+1+t] -= L[r][k] L[k+1+t][k]  also slides each row by
+// one (a[t] = a[t+1] - l c[t]) and every register index stays static in a rolled
+// loop.  N1 / N2: entries of a1 / a2 still inside the matrix (N1 = 0 once the
+// rows r1 are finished).  L is written to M (sw64 layout) column by column; the
+// pivot column is broadcast through cbuf (two 64-float buffers, by step parity).
+template <int N1, int N2>
+__device__ __forceinline__ void chol_shifted_steps(float (&a1)[32], float (&a2)[64], float& b1,
+                                                   float& b2, int k0, int k1, float* M,
+                                                   float* cbuf, float* dinv, int lane, bool& bad)
+{
+    static_assert(N1 % 4 == 0 && N2 % 4 == 0 && N2 > 0, "step shape");
+    const int r1 = lane, r2 = 32 + lane;
+#pragma unroll 1
+    for (int k = k0; k < k1; ++k) {
+        const int owner = k & 31;
+        float piv = __shfl_sync(kFullMask, N1 > 0 ? a1[0] : a2[0], owner);
+        const float bk = __shfl_sync(kFullMask, N1 > 0 ? b1 : b2, owner);
+        if (!(piv > 0.f && piv < INFINITY)) {  // also catches NaN
+            bad = true;
+            piv = 1.f;
+        }
+        const float rinv = rsqrtf(piv);
+        const float yk = bk * rinv;
+        if (lane == 0) dinv[k] = rinv;
+        float* cb = cbuf + (k & 1) * 64;
+        float l1 = 0.f, l2 = 0.f;
+        if (N1 > 0) {
+            if (r1 == k) {
+                M[sw64(r1, k)] = piv * rinv;
+                b1 = yk;
+            } else if (r1 > k) {
+                l1 = a1[0] * rinv;
+                M[sw64(r1, k)] = l1;
+                b1 = fmaf(-l1, yk, b1);
+                cb[r1 - k - 1] = l1;
+            }
+        }
+        if (r2 == k) {
+            M[sw64(r2, k)] = piv * rinv;
+            b2 = yk;
+        } else if (r2 > k) {
+            l2 = a2[0] * rinv;
+            M[sw64(r2, k)] = l2;
+            b2 = fmaf(-l2, yk, b2);
+            cb[r2 - k - 1] = l2;
+        }
+        __syncwarp();
+        // cb[t] = L[k + 1 + t][k]; entries past the matrix are stale and only ever
+        // reach register entries past the matrix
+#pragma unroll
+        for (int t4 = 0; t4 < N2; t4 += 4) {
+            const float4 c = *reinterpret_cast<const float4*>(cb + t4);
+            const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = t4 + u;
+                if (t + 1 < N2) a2[t] = fmaf(-l2, cv[u], a2[t + 1]);
+                if (t + 1 < N1) a1[t] = fmaf(-l1, cv[u], a1[t + 1]);
+            }
+        }
+    }
+}
+
+// Factor / solve / sample for K = 64: Lambda_i in shared memory (sw64 layout, lower
+// triangle valid, the rest scratch; overwritten with L), b_i in bv.  Lane l owns
+// rows r1 = l and r2 = 32 + l; the factorization runs in four spans of 16 columns
+// so the register rows shrink as they finish, then x = L^{-T}(y + z).
+__device__ __forceinline__ void factor_solve_sample_rl64(float* M, const float* bv, float* cbuf,
+                                                         float* dinv, float* zb, int lane, int K,
+                                                         uint64_t seed, uint32_t row,
+                                                         uint32_t sweep, uint32_t c3,
                                                          bool want_means, float& x1, float& x2,
                                                          float& m1, float& m2, bool& bad)
 {
-    static_assert(KT == 48 || KT == 64, "two-panel factor needs 32 < KT <= 64");
-    constexpr int Q = KT - 32;
-    constexpr int LD = KT + 1;
     const int r1 = lane, r2 = 32 + lane;
-    const bool v2 = lane < Q;
-    float a1[32], a2[32];
+    float a1[32], a2[64];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        a1[j] = sq[r1 * LD + j];
-        a2[j] = v2 ? sq[r2 * LD + j] : 0.f;
+    for (int c = 0; c < 8; ++c) {
+        const float4 u = ld_chunk(M, r1, c);
+        a1[4 * c + 0] = u.x; a1[4 * c + 1] = u.y; a1[4 * c + 2] = u.z; a1[4 * c + 3] = u.w;
     }
-    float b1 = sq[r1 * LD + KT];
-    float b2 = v2 ? sq[r2 * LD + KT] : 0.f;
-    __syncwarp();
-
-    // ---- panel 1: columns 0..31
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        float* cb = colbuf + (k & 1) * 32;
-        float piv = __shfl_sync(kFullMask, a1[k], k);
-        if (!(piv > 0.f && piv < INFINITY)) {
-            bad = true;
-            piv = 1.f;
-        }
-        const float rinv = rsqrtf(piv);
-        if (lane == 0) dinv[k] = rinv;
-        if (r1 > k) a1[k] *= rinv;
-        else if (r1 == k) a1[k] = piv * rinv;
-        a2[k] *= rinv;
-        if (r1 > k) cb[r1] = a1[k];
-        __syncwarp();
-        const float l1 = a1[k], l2 = a2[k];
-#pragma unroll
-        for (int j4 = ((k + 1) / 4) * 4; j4 < 32; j4 += 4) {
-            const float4 cv = *reinterpret_cast<const float4*>(cb + j4);
-            const float cj[4] = {cv.x, cv.y, cv.z, cv.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = j4 + u;
-                if (j > k) {
-                    a1[j] = fmaf(-l1, cj[u], a1[j]);
-                    a2[j] = fmaf(-l2, cj[u], a2[j]);
-                }
-            }
-        }
+    for (int c = 0; c < 16; ++c) {
+        const float4 v = ld_chunk(M, r2, c);
+        a2[4 * c + 0] = v.x; a2[4 * c + 1] = v.y; a2[4 * c + 2] = v.z; a2[4 * c + 3] = v.w;
     }
-    // ---- forward substitution, columns 0..31 (L11 and L21)
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        const float yk = __shfl_sync(kFullMask, b1, k) * dinv[k];
-        if (r1 == k) b1 = yk;
-        else if (r1 > k) b1 = fmaf(-a1[k], yk, b1);
-        b2 = fmaf(-a2[k], yk, b2);
-    }
-    // L11 and L21 into sq; L21 also transposed into the unused upper block
-    // (row k, columns 32..KT-1) for the trailing update
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        if (j <= r1) sq[r1 * LD + j] = a1[j];
-        if (v2) {
-            sq[r2 * LD + j] = a2[j];
-            sq[j * LD + 32 + lane] = a2[j];
-        }
-    }
-    __syncwarp();
-    // ---- trailing update of row r2: A22[r2][32 + j] -= L21[r2] . L21[32 + j]
-    float a3[Q];
-#pragma unroll
-    for (int j = 0; j < Q; ++j) a3[j] = v2 ? sq[r2 * LD + 32 + j] : 0.f;
-#pragma unroll 2
-    for (int k = 0; k < 32; ++k) {
-        const float lk = v2 ? sq[r2 * LD + k] : 0.f;  // L21[r2][k], already stored
-        const float* Trow = sq + k * LD + 32;
-#pragma unroll
-        for (int j = 0; j < Q; ++j) a3[j] = fmaf(-lk, Trow[j], a3[j]);
-    }
-    // ---- panel 2: Cholesky of the updated A22, row r2 on lane l
-#pragma unroll 32
-    for (int k = 0; k < Q; ++k) {
-        float* cb = colbuf + (k & 1) * 32;
-        float piv = __shfl_sync(kFullMask, a3[k], k);
-        if (!(piv > 0.f && piv < INFINITY)) {
-            bad = true;
-            piv = 1.f;
-        }
-        const float rinv = rsqrtf(piv);
-        if (lane == 0) dinv[32 + k] = rinv;
-        if (lane > k) a3[k] *= rinv;
-        else if (lane == k) a3[k] = piv * rinv;
-        if (lane > k && v2) cb[lane] = a3[k];
-        __syncwarp();
-        const float l3 = a3[k];
-#pragma unroll 8
-        for (int j4 = ((k + 1) / 4) * 4; j4 < Q; j4 += 4) {
-            const float4 cv = *reinterpret_cast<const float4*>(cb + j4);
-            const float cj[4] = {cv.x, cv.y, cv.z, cv.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = j4 + u;
-                if (j > k) a3[j] = fmaf(-l3, cj[u], a3[j]);
-            }
-        }
-    }
-    // ---- forward substitution, columns 32..KT-1 (L22)
-#pragma unroll 32
-    for (int k = 0; k < Q; ++k) {
-        const float yk = __shfl_sync(kFullMask, b2, k) * dinv[32 + k];
-        if (lane == k) b2 = yk;
-        else if (lane > k) b2 = fmaf(-a3[k], yk, b2);
-    }
-#pragma unroll 32
-    for (int j = 0; j < Q; ++j)
-        if (v2 && j <= lane) sq[r2 * LD + 32 + j] = a3[j];
+    float b1 = bv[r1];
+    float b2 = bv[r2];
+    __syncwarp();  // every lane has its rows before L overwrites them
+    chol_shifted_steps<32, 64>(a1, a2, b1, b2, 0, 16, M, cbuf, dinv, lane, bad);
+    chol_shifted_steps<16, 48>(a1, a2, b1, b2, 16, 32, M, cbuf, dinv, lane, bad);
+    chol_shifted_steps<0, 32>(a1, a2, b1, b2, 32, 48, M, cbuf, dinv, lane, bad);
+    chol_shifted_steps<0, 16>(a1, a2, b1, b2, 48, 64, M, cbuf, dinv, lane, bad);
     // ---- noise z (zero beyond K)
-    if (lane < KT / 4) {
+    if (lane < 16) {
         const float4 z4 = normals4_f32(seed, (uint32_t)lane, row, sweep, c3);
         const int kk = 4 * lane;
         zb[kk + 0] = kk + 0 < K ? z4.x : 0.f;
@@ -304,34 +293,31 @@ __device__ __forceinline__ void factor_solve_sample_smem(float* sq, float* colbu
     }
     __syncwarp();
     float t1 = b1 + zb[r1];
-    float t2 = b2 + (v2 ? zb[r2] : 0.f);
+    float t2 = b2 + zb[r2];
     float n1 = b1, n2 = b2;
-    // ---- back substitution x = L^{-T} t (rows r1 = l, r2 = 32 + l)
+    // ---- back substitution x = L^{-T} t: step i broadcasts x_i and every lane
+    // updates its rows with row i of L (conflict-free across lanes)
 #pragma unroll 4
-    for (int i = KT - 1; i >= 0; --i) {
-        const int owner = i < 32 ? i : i - 32;
+    for (int i = 63; i >= 0; --i) {
+        const int owner = i & 31;
         const float di = dinv[i];
+        const float la = M[sw64(i, r1)], lb = M[sw64(i, r2)];
         const float ui = __shfl_sync(kFullMask, i < 32 ? t1 : t2, owner) * di;
         float mi = 0.f;
         if (want_means) mi = __shfl_sync(kFullMask, i < 32 ? n1 : n2, owner) * di;
-        const float* Lrow = sq + i * LD;
         if (r1 == i) {
             t1 = ui;
             n1 = mi;
         } else if (r1 < i) {
-            const float l = Lrow[r1];
-            t1 = fmaf(-l, ui, t1);
-            n1 = fmaf(-l, mi, n1);
+            t1 = fmaf(-la, ui, t1);
+            n1 = fmaf(-la, mi, n1);
         }
-        if (v2) {
-            if (r2 == i) {
-                t2 = ui;
-                n2 = mi;
-            } else if (r2 < i) {
-                const float l = Lrow[r2];
-                t2 = fmaf(-l, ui, t2);
-                n2 = fmaf(-l, mi, n2);
-            }
+        if (r2 == i) {
+            t2 = ui;
+            n2 = mi;
+        } else if (r2 < i) {
+            t2 = fmaf(-lb, ui, t2);
+            n2 = fmaf(-lb, mi, n2);
         }
     }
     x1 = t1;
@@ -341,12 +327,11 @@ __device__ __forceinline__ void factor_solve_sample_smem(float* sq, float* colbu
 }
 
 // Store for the two-panel ownership (rows l and 32 + l).
-template <int KT>
 __device__ __forceinline__ void store_row_panels(const RowArgs& a, int row, int lane, float x1,
                                                  float x2, float m1, float m2)
 {
     const int r1 = lane, r2 = 32 + lane;
-    const bool v2 = lane < KT - 32;
+    const bool v2 = true;
     const int64_t off = (int64_t)row * a.ldx;
     a.X[off + r1] = x1;
     if (v2) a.X[off + r2] = x2;

@@ -40,13 +40,13 @@ def hyper_of(hyper, side, K):
     return hyper[off:off + K].copy(), hyper[off + K:off + K + K * K].reshape(K, K).copy()
 
 
-def step_parity(bp, prob, flags=0, order=0, sweeps=1, seed=None):
+def step_parity(bp, prob, flags=0, order=0, sweeps=1, seed=None, **kw):
     """Run `sweeps` sweeps phase by phase on the GPU, checking each phase against
     the oracle started from the GPU's state.  Returns the worst errors seen."""
     import torch
     K = prob.K
     h = bp.create_from_problem(prob, flags=flags | bp.BPMF_DEBUG_MEANS, burn_in=0, seed=seed,
-                               order=order, stream=bp.torch_stream())
+                               order=order, stream=bp.torch_stream(), **kw)
     worst = {"stats": 0.0, "hyper": 0.0, "x": 0.0, "mean": 0.0, "rmse": 0.0}
     try:
         orc = oracle.Oracle(prob, burn_in=0, seed=seed, order=order, nthreads=4)

@@ -25,16 +25,19 @@ def bp():
     return bp
 
 
-@pytest.mark.parametrize("K", [64, 50])
-def test_long_rows_tensor_core_parity(bp, K):
+@pytest.mark.parametrize("K,long_min", [(64, 0), (50, 0), (64, 150)])
+def test_long_rows_tensor_core_parity(bp, K, long_min):
     # degrees 60..400 on both sides: ragged against the 16-rating MMA step and the
-    # 64-rating stage; a few rows below the long threshold stay on the warp kernel
+    # 64-rating stage; with a threshold of 150 the rows below it stay on the warp
+    # kernel (both kernels in one phase)
     prob = workloads.random_small(600, 300, K, 60000, seed=200 + K, n_test=400, long_rows=6,
                                   long_deg=290)
     for side in (0, 1):
         deg = np.diff(prob.csr_ptr) if side == 0 else prob.col_degrees()
         assert (deg >= 48).sum() > 0.5 * len(deg)
-    assert_worst(step_parity(bp, prob, sweeps=2))
+        if long_min:
+            assert (deg < long_min).sum() > 0
+    assert_worst(step_parity(bp, prob, sweeps=2, long_min_degree=long_min))
 
 
 def test_tensor_core_and_cuda_core_paths_agree(bp):
