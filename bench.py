@@ -137,16 +137,29 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # algorithmic work per phase (stated in the design doc)
 # ----------------------------------------------------------------------------
-def row_phase_flops(nnz, rows, K):
-    """Per rating: symmetric Gram K(K+1) + right-hand side 2K flops.
-    Per row: Cholesky K^3/3 + two triangular solves 2K^2 each + prior terms 2K^2."""
-    return nnz * (K * (K + 1) + 2 * K) + rows * (K**3 / 3.0 + 6.0 * K * K)
+def row_alu_flops(rows, K):
+    """CUDA-core work per row: Cholesky K^3/3, forward and back substitution K^2
+    each, the prior terms and noise add (O(K), ignored)."""
+    return rows * (K**3 / 3.0 + 2.0 * K * K)
 
 
-def row_phase_bytes(nnz, rows, K):
-    """Compulsory bytes: index + value per rating, gathered factor row (4K) per rating,
-    row pointer (8) + factor row written (4K) per row."""
-    return nnz * (8 + 4 * K) + rows * (8 + 4 * K)
+def row_gram_flops(nnz, K):
+    """Tensor-core work per rating: the full K x K Gram tile 2K^2 (the symmetric
+    half is K(K+1)) and the right-hand side 2K."""
+    return nnz * (2.0 * K * K + 2.0 * K)
+
+
+def row_gather_bytes(nnz, rows, K, split=True):
+    """Bytes per rating: index + value (8) and the other side's factor row (FP16
+    hi + lo: 4K, FP32: 4K); per row: row pointers (16) and the written factor row
+    (4K FP32 + 4K FP16 hi/lo)."""
+    return nnz * (8 + 4 * K) + rows * (16 + 8 * K)
+
+
+# DRAM bytes (read + write) per launch of the row kernel on the 480k x 18k, 1e8-rating,
+# K = 64 workload, from one ncu capture of this kernel version (null once the kernel
+# changes).
+TRAFFIC = {}
 
 
 def load_peaks():
@@ -252,21 +265,41 @@ def run_native(args):
     value = aggregate_rows_per_s((prob.M + prob.N) * world, args.steps, max_ms)
     ms_per_step = max_ms / args.steps
 
-    # dominant kernel: the slower row-update phase (one kernel launch per bin)
+    # dominant kernel: the tensor-core row kernel of the slower row phase (with every
+    # rated row in the long bin the phase is that one launch plus the FP16 split of
+    # the new rows)
     nnz = prob.nnz
     dom = max(("rows_movie", "rows_user"), key=lambda n: phase_ms[n])
     dom_rows = prob.N if dom == "rows_movie" else prob.M
-    flops = row_phase_flops(nnz, dom_rows, K)
-    achieved = flops / (phase_ms[dom] / 1e3) / 1e12
+    t_dom = phase_ms[dom] / 1e3
+    alu = row_alu_flops(dom_rows, K)
+    achieved = alu / t_dom / 1e12
     peaks = load_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
-    roofline = {"bound": "alu", "kernel": "rows_warp_kernel<64> (%s)" % dom,
+    tc_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    gram = row_gram_flops(nnz, K)
+    other = "rows_movie" if dom == "rows_user" else "rows_user"
+    other_rows = prob.N if other == "rows_movie" else prob.M
+    gather = row_gather_bytes(nnz, other_rows, K)
+    roofline = {"bound": "alu", "kernel": "rows_tc_kernel (%s)" % dom,
                 "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak, 4), "traffic": None,
-                "peak_source": "FP32 CUDA-core peak from %d SMs x 128 lanes x 2 x %.0f MHz" % (n_sm, sm_max),
-                "algorithmic_tflop_per_launch": round(flops / 1e12, 4),
+                "frac": round(achieved / fp32_peak, 4), "traffic": TRAFFIC.get(dom),
+                "peak_source": "FP32 CUDA-core peak derived from %d SMs x 128 lanes x 2 x %.0f MHz"
+                               % (n_sm, sm_max),
+                "algorithmic_tflop_per_launch": round(alu / 1e12, 4),
+                "tensor": {"achieved": round(gram / t_dom / 1e12, 2), "peak": tc_peak,
+                           "frac": round(gram / t_dom / 1e12 / tc_peak, 4),
+                           "note": "Gram tiles on tcgen05 in the same launch (of measured "
+                                   "sustained bf16; FP16 runs at the bf16 rate)"},
+                "gather": {"phase": other,
+                           "achieved_gbs": round(gather / (phase_ms[other] / 1e3) / 1e9, 1),
+                           "peak_gbs": hbm_peak,
+                           "frac": round(gather / (phase_ms[other] / 1e3) / 1e9 / hbm_peak, 4),
+                           "note": "algorithmic bytes incl. gathered factor rows (mostly L2 "
+                                   "hits) over the other row phase, of measured HBM copy"},
                 "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()}}
 
     e2e = None

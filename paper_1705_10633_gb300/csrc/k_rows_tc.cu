@@ -3,11 +3,14 @@
 //
 // The Gram sum_c y_c y_c^T of a row is a dense contraction over its ratings
 // (the "K x K outer product" of Sec. 3.1).  The other side's factors are kept
-// as an FP16 split y = h + l (|l| <= 2^-11 |h|), and one M = 128 MMA computes
-//     D = [H^T ; L^T] . H     (rows 0..63: H^T H, rows 64..127: L^T H)
-// so that Gram = H^T H + L^T H + (L^T H)^T up to the dropped L^T L term
-// (2^-22 relative): FP32-class accuracy at the FP16 tensor rate.  A second
-// N = 16 MMA with the split ratings (r_hi, r_lo) as B gives sum_c r_c y_c.
+// as an FP16 split y = h + l (|l| <= 2^-11 |h|) and the ratings as r = r_hi +
+// r_lo; one M = 128, N = 144 MMA per 16 ratings computes
+//     D = [H^T ; L^T] . [H | L | R]
+// whose column blocks 0..63 and 64..127, summed over both row halves, give
+// (H + L)^T (H + L) (FP32-class accuracy at the FP16 tensor rate), and whose
+// columns 128, 129 give (H + L)^T r.  A and B are the same three 64-wide
+// 128B-swizzled atoms of a stage (h rows, l rows, and the ratings in the first
+// two columns of an otherwise zero atom), so each k-block reads them once.
 //
 // CTA = 16 warps, one CTA per SM, persistent over the rows of the long bin:
 //   warp 0       MMA issuer (one lane) and TMEM owner (512 columns)
@@ -17,10 +20,11 @@
 //   warps 2-3    gather: cp.async of the 128-B h and l rows of each rating into
 //                128B-swizzled tiles (MN-major operand layout); they never wait
 //                for their copies, the stage barrier completes when they land
-//   warps 4-7    drain: TMEM -> shared Lambda_i = Lambda_X + alpha Gram, b_i
+//   warps 4-7    drain: TMEM -> shared Lambda_i += alpha Gram (the buffer starts
+//                from Lambda_X), b_i
 //   warps 8-15   one row each: Cholesky, solves, Philox noise, store
 // Stages of 64 ratings flow producer -> MMA through mbarriers; accumulators
-// (4 TMEM slots) MMA -> drain; Lambda buffers (one per Cholesky warp) drain ->
+// (3 TMEM slots of 144 columns) MMA -> drain; Lambda buffers (one per Cholesky warp) drain ->
 // Cholesky.  A long row is accumulated in chunks of 16 stages, each in a fresh
 // TMEM accumulator that the drain adds into the row's FP32 buffer: the tensor
 // core's accumulation rounding then grows with the chunk length only, not with
@@ -35,8 +39,8 @@ namespace {
 
 constexpr int kKT = 64;
 constexpr int kStageRatings = 64;
-constexpr int kNStage = 4;
-constexpr int kNAcc = 4;
+constexpr int kNStage = 3;
+constexpr int kNAcc = 3;
 constexpr int kChunkStages = 16;  // stages per TMEM accumulation before it is flushed
 constexpr int kNChol = 8;
 constexpr int kThreads = 512;
@@ -44,11 +48,11 @@ constexpr int kGatherThreads = 64;
 constexpr int kRowRing = 32;   // row descriptors in flight
 constexpr int kIdxRing = 8;    // stages of rating indices / values in flight
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kAccStride = 128;
+constexpr uint32_t kAccStride = 160;  // 144 columns used
 
 constexpr uint32_t kTileBytes = kStageRatings * 128;        // 64 ratings x 64 halves
-constexpr uint32_t kRBytes = 2048;                          // RHS operand, no swizzle
-constexpr uint32_t kStageBytes = 2 * kTileBytes + kRBytes;  // 18 KB (1 KB multiple)
+constexpr uint32_t kRBytes = kTileBytes;                    // ratings atom (2 of 64 columns)
+constexpr uint32_t kStageBytes = 2 * kTileBytes + kRBytes;  // 24 KB (1 KB multiple)
 // A Lambda buffer: the lower triangle of the 64 x 64 precision in the XOR-swizzled
 // layout sw64 (row stride 64, 16-B chunks permuted by row & 7), then b (64 floats).
 constexpr uint32_t kLamFloats = 64 * 64 + 64;
@@ -71,8 +75,7 @@ constexpr uint32_t make_idesc(int M, int N)
     return (1u << 4) | (0u << 7) | (0u << 10) | (1u << 15) | (1u << 16) |
            ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-constexpr uint32_t kIdescGram = make_idesc(128, 64);
-constexpr uint32_t kIdescRhs = make_idesc(128, 16);
+constexpr uint32_t kIdesc = make_idesc(128, 144);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -220,6 +223,36 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 }  // namespace
 
+// One drain thread's share of a TMEM accumulator: row m of the Gram is the sum of
+// accumulator columns c and 64 + c; 16 of each per round, added into the row's
+// lower-triangle chunks (the buffer starts from the prior precision).  Warps
+// whose rows end before column 32 stop after two rounds; the trip count is
+// warp-uniform, as the collective loads require.
+__device__ __forceinline__ void drain_rows(uint32_t taddr, float* L, int m, int quarter, float alpha)
+{
+    const int ngroups = (quarter & 1) ? 4 : 2;
+#pragma unroll 1
+    for (int h = 0; h < ngroups; ++h) {
+        uint32_t g[16], e[16];
+        TMEM_LD16(taddr + 16 * h, g);
+        TMEM_LD16(taddr + 64 + 16 * h, e);
+        tmem_wait_ld();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int cc = 4 * h + q;
+            if (4 * cc <= m) {
+                float4* p = chunk_ptr(L, m, cc);
+                float4 v = *p;
+                v.x = fmaf(alpha, __uint_as_float(g[4 * q + 0]) + __uint_as_float(e[4 * q + 0]), v.x);
+                v.y = fmaf(alpha, __uint_as_float(g[4 * q + 1]) + __uint_as_float(e[4 * q + 1]), v.y);
+                v.z = fmaf(alpha, __uint_as_float(g[4 * q + 2]) + __uint_as_float(e[4 * q + 2]), v.z);
+                v.w = fmaf(alpha, __uint_as_float(g[4 * q + 3]) + __uint_as_float(e[4 * q + 3]), v.w);
+                *p = v;
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
 {
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
@@ -260,6 +293,10 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
         *reinterpret_cast<uint4*>(sm + kOffStages + s * kStageBytes + 2 * kTileBytes + 16 * o) =
             make_uint4(0u, 0u, 0u, 0u);
     }
+    // every precision buffer starts from the prior precision
+    for (int b = 0; b < kNChol; ++b)
+        fill_lower_sw64(lam_bufs + b * kLamFloats, reinterpret_cast<const float4*>(a.lam_ct), tid,
+                        kThreads);
     if (tid == 0) {
         for (int s = 0; s < kNStage; ++s) {
             mbar_init(bar_stage_full + 8 * s, kGatherThreads);
@@ -302,7 +339,9 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
     constexpr int64_t kChunkRatings = (int64_t)kChunkStages * kStageRatings;
 
     if (warp < 4) {
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 56;" ::: "memory");
+        // register split (launch: 512 threads x 128): warps 0-3 72, drain 96,
+        // Cholesky 168 -> 32 x (4 x 72 + 4 x 96 + 8 x 168) = 64,512 <= 65,536
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 72;" ::: "memory");
         if (warp == 0) {
             // ======================= MMA issuer =======================
             if (lane == 0) {
@@ -322,7 +361,6 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
                         }
                         tc_fence_after();
                         const uint32_t dgram = tmem_base + slot * kAccStride;
-                        const uint32_t drhs = dgram + 64;
                         const int64_t c1 = min(p1, c0 + kChunkRatings);
                         for (int64_t base = c0; base < c1; base += kStageRatings, ++g) {
                             const uint32_t s = g % kNStage;
@@ -336,17 +374,14 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
                             tc_fence_after();
                             const int cnt = (int)min((int64_t)kStageRatings, p1 - base);
                             const uint32_t sH = sbase + kOffStages + s * kStageBytes;
-                            const uint32_t sR = sH + 2 * kTileBytes;
                             for (int kb = 0; kb < (cnt + 15) / 16; ++kb) {
-                                // A = [H^T; L^T] (128 x 16); B = H, then B = L (16 x 64)
-                                const uint64_t adesc = sdesc(sH + kb * 2048, kTileBytes, 1024, 2);
-                                const uint64_t ldesc =
-                                    sdesc(sH + kTileBytes + kb * 2048, kTileBytes, 1024, 2);
-                                const uint64_t rdesc = sdesc(sR + kb * 256, 128, 1024, 0);
+                                // A = [H^T; L^T] (M = 128: atoms 0, 1), B = [H | L | R]
+                                // (N = 144: atoms 0, 1 and the first 16 columns of 2):
+                                // one descriptor, atoms kTileBytes apart, 16 ratings
+                                // (16 x 128 B rows) per k-block
+                                const uint64_t desc = sdesc(sH + kb * 2048, kTileBytes, 1024, 2);
                                 const uint32_t acc = (base > c0 || kb > 0) ? 1u : 0u;
-                                tc_mma(dgram, adesc, adesc, kIdescGram, acc);
-                                tc_mma(dgram, adesc, ldesc, kIdescGram, 1u);
-                                tc_mma(drhs, adesc, rdesc, kIdescRhs, acc);
+                                tc_mma(dgram, desc, desc, kIdesc, acc);
                             }
                             tc_commit(bar_stage_empty + 8 * s);
                         }
@@ -455,7 +490,7 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
                     split_f16(rv, hi, lo);
                     const uint32_t packed = (uint32_t)__half_as_ushort(hi) |
                                             ((uint32_t)__half_as_ushort(lo) << 16);
-                    asm volatile("st.shared.b32 [%0], %1;" ::"r"(sR + (gt >> 3) * 128 + (gt & 7) * 16),
+                    asm volatile("st.shared.b32 [%0], %1;" ::"r"(sR + gt * 128 + ((gt & 7) << 4)),
                                  "r"(packed)
                                  : "memory");
                     fence_proxy_async();
@@ -470,7 +505,6 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
         const int quarter = warp & 3;
         const int m = 32 * (quarter & 1) + lane;  // row of Lambda this thread serves
         const float alpha = a.alpha;
-        const float4* lam_ct4 = reinterpret_cast<const float4*>(a.lam_ct);
         uint32_t u = 0;  // accumulation chunks drained
         bool live = true;
         for (int64_t j = 0; j < nj && live; ++j) {
@@ -505,67 +539,17 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
                 }
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + ((uint32_t)(32 * quarter) << 16) + slot * kAccStride;
-                uint32_t r0, r1;
-                tmem_ld2(taddr + 64, r0, r1);
-                // Lambda += alpha (H^T H + L^T H + (L^T H)^T) of this chunk, lower triangle
-                // (column <= row) only, 32 accumulator columns at a time; the first chunk
-                // starts from the prior precision
                 // The accumulator holds H^T (H + L) in its top 64 lanes and L^T (H + L) in
                 // its bottom 64; their sum is the chunk's Gram (H + L is the FP16 split of
-                // the other side's rows).  Bottom rows are stored first, then the top rows
-                // add theirs and, on a row's first chunk, the prior precision.  Only chunks
-                // on or below the diagonal are formed, 32 columns at a time.
-                uint32_t gr[32];
-                if (quarter >= 2) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        TMEM_LD16(taddr + 32 * h, (gr + 0));
-                        TMEM_LD16(taddr + 32 * h + 16, (gr + 16));
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const int cc = 8 * h + q;
-                            if (4 * cc <= m) {
-                                float4* p = chunk_ptr(L, m, cc);
-                                float4 v = make_float4(alpha * __uint_as_float(gr[4 * q + 0]),
-                                                       alpha * __uint_as_float(gr[4 * q + 1]),
-                                                       alpha * __uint_as_float(gr[4 * q + 2]),
-                                                       alpha * __uint_as_float(gr[4 * q + 3]));
-                                if (!first) {
-                                    const float4 o = *p;
-                                    v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
-                                }
-                                *p = v;
-                            }
-                        }
-                    }
-                }
+                // the other side's rows).  Both halves add into the row's buffer, which
+                // starts from the prior precision, the bottom first; only chunks on or
+                // below the diagonal are formed.
+                uint32_t r0, r1;
+                tmem_ld2(taddr + 128, r0, r1);
+                if (quarter >= 2) drain_rows(taddr, L, m, quarter, alpha);
                 named_bar(1, 128);
-                if (quarter < 2) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        TMEM_LD16(taddr + 32 * h, (gr + 0));
-                        TMEM_LD16(taddr + 32 * h + 16, (gr + 16));
-                        tmem_wait_ld();
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const int cc = 8 * h + q;
-                            if (4 * cc <= m) {
-                                float4* p = chunk_ptr(L, m, cc);
-                                float4 o = *p;
-                                if (first) {  // chunk-transposed copy: the lanes' loads coalesce
-                                    const float4 x = __ldg(lam_ct4 + cc * 64 + m);
-                                    o.x += x.x; o.y += x.y; o.z += x.z; o.w += x.w;
-                                }
-                                o.x = fmaf(alpha, __uint_as_float(gr[4 * q + 0]), o.x);
-                                o.y = fmaf(alpha, __uint_as_float(gr[4 * q + 1]), o.y);
-                                o.z = fmaf(alpha, __uint_as_float(gr[4 * q + 2]), o.z);
-                                o.w = fmaf(alpha, __uint_as_float(gr[4 * q + 3]), o.w);
-                                *p = o;
-                            }
-                        }
-                    }
-                }
+                if (quarter < 2) drain_rows(taddr, L, m, quarter, alpha);
+                tmem_wait_ld();
                 tc_fence_before();
                 mbar_arrive(bar_acc_empty + 8 * slot);
                 rsum += __uint_as_float(r0) + __uint_as_float(r1);
@@ -580,7 +564,7 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
         }
     } else {
         // ======================= Cholesky, solve, sample =======================
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 176;" ::: "memory");
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 168;" ::: "memory");
         const int cw = warp - 8;
         float* scratch = chol_scratch + cw * kCholScratchFloats;
         float* colbuf = scratch;
@@ -599,6 +583,10 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
             factor_solve_sample_rl64(L, L + 4096, colbuf, dinv, zb, lane, a.K, a.seed, (uint32_t)row,
                                      sweep, a.c3, a.means != nullptr, x1, x2, m1, m2, bad);
             store_row_panels(a, row, lane, x1, x2, m1, m2);
+            __syncwarp();  // every lane is done reading L
+            // the buffer goes back holding the prior precision, which the drain
+            // accumulates into
+            fill_lower_sw64(L, reinterpret_cast<const float4*>(a.lam_ct), lane, 32);
             __syncwarp();
             mbar_arrive(bar_lam_empty + 8 * cw);
             if (lane == 0) mbar_arrive(bar_row_empty + 8 * rs);

@@ -192,8 +192,10 @@ __device__ __forceinline__ float4 ld_chunk(const float* M, int i, int c)
 // k, so the update  A[r][k+1+t] -= L[r][k] L[k+1+t][k]  also slides each row by
 // one (a[t] = a[t+1] - l c[t]) and every register index stays static in a rolled
 // loop.  N1 / N2: entries of a1 / a2 still inside the matrix (N1 = 0 once the
-// rows r1 are finished).  L is written to M (sw64 layout) column by column; the
-// pivot column is broadcast through cbuf (two 64-float buffers, by step parity).
+// rows r1 are finished).  The strictly lower part of L is written transposed into
+// M (row k of M receives column k of L: a conflict-free row store), the inverse
+// diagonal into dinv; the pivot column is broadcast through cbuf (two 64-float
+// buffers, by step parity).
 template <int N1, int N2>
 __device__ __forceinline__ void chol_shifted_steps(float (&a1)[32], float (&a2)[64], float& b1,
                                                    float& b2, int k0, int k1, float* M,
@@ -217,21 +219,19 @@ __device__ __forceinline__ void chol_shifted_steps(float (&a1)[32], float (&a2)[
         float l1 = 0.f, l2 = 0.f;
         if (N1 > 0) {
             if (r1 == k) {
-                M[sw64(r1, k)] = piv * rinv;
                 b1 = yk;
             } else if (r1 > k) {
                 l1 = a1[0] * rinv;
-                M[sw64(r1, k)] = l1;
+                M[sw64(k, r1)] = l1;
                 b1 = fmaf(-l1, yk, b1);
                 cb[r1 - k - 1] = l1;
             }
         }
         if (r2 == k) {
-            M[sw64(r2, k)] = piv * rinv;
             b2 = yk;
         } else if (r2 > k) {
             l2 = a2[0] * rinv;
-            M[sw64(r2, k)] = l2;
+            M[sw64(k, r2)] = l2;
             b2 = fmaf(-l2, yk, b2);
             cb[r2 - k - 1] = l2;
         }
@@ -252,8 +252,22 @@ __device__ __forceinline__ void chol_shifted_steps(float (&a1)[32], float (&a2)[
     }
 }
 
+// Lower-triangle chunks (4c <= i) of a sw64 matrix set from a chunk-transposed copy
+// in global memory (float4 (i, 4c..4c+3) at c * 64 + i) by `nthreads` threads:
+// consecutive threads take consecutive rows, so the loads coalesce and the stores
+// are conflict-free.
+__device__ __forceinline__ void fill_lower_sw64(float* M, const float4* src_ct, int t, int nthreads)
+{
+#pragma unroll 4
+    for (int e = t; e < 1024; e += nthreads) {
+        const int i = e & 63, c = e >> 6;
+        if (4 * c <= i) *chunk_ptr(M, i, c) = __ldg(src_ct + c * 64 + i);
+    }
+}
+
 // Factor / solve / sample for K = 64: Lambda_i in shared memory (sw64 layout, lower
-// triangle valid, the rest scratch; overwritten with L), b_i in bv.  Lane l owns
+// triangle valid, the rest scratch; overwritten with the strictly lower part of L,
+// transposed), b_i in bv.  Lane l owns
 // rows r1 = l and r2 = 32 + l; the factorization runs in four spans of 16 columns
 // so the register rows shrink as they finish, then x = L^{-T}(y + z).
 __device__ __forceinline__ void factor_solve_sample_rl64(float* M, const float* bv, float* cbuf,
@@ -296,28 +310,36 @@ __device__ __forceinline__ void factor_solve_sample_rl64(float* M, const float* 
     float t2 = b2 + zb[r2];
     float n1 = b1, n2 = b2;
     // ---- back substitution x = L^{-T} t: step i broadcasts x_i and every lane
-    // updates its rows with row i of L (conflict-free across lanes)
-#pragma unroll 4
-    for (int i = 63; i >= 0; --i) {
-        const int owner = i & 31;
-        const float di = dinv[i];
-        const float la = M[sw64(i, r1)], lb = M[sw64(i, r2)];
-        const float ui = __shfl_sync(kFullMask, i < 32 ? t1 : t2, owner) * di;
-        float mi = 0.f;
-        if (want_means) mi = __shfl_sync(kFullMask, i < 32 ? n1 : n2, owner) * di;
-        if (r1 == i) {
-            t1 = ui;
-            n1 = mi;
-        } else if (r1 < i) {
-            t1 = fmaf(-la, ui, t1);
-            n1 = fmaf(-la, mi, n1);
-        }
-        if (r2 == i) {
-            t2 = ui;
-            n2 = mi;
-        } else if (r2 < i) {
-            t2 = fmaf(-lb, ui, t2);
-            n2 = fmaf(-lb, mi, n2);
+    // updates its rows r < i with L[i][r], which sits in row r of M (L^T); one
+    // float4 of that row serves four steps
+#pragma unroll 1
+    for (int g = 15; g >= 0; --g) {
+        const float4 A1 = ld_chunk(M, r1, g), A2 = ld_chunk(M, r2, g);
+        const float4 D = *reinterpret_cast<const float4*>(dinv + 4 * g);
+        const float l1v[4] = {A1.x, A1.y, A1.z, A1.w};
+        const float l2v[4] = {A2.x, A2.y, A2.z, A2.w};
+        const float dv[4] = {D.x, D.y, D.z, D.w};
+#pragma unroll
+        for (int u = 3; u >= 0; --u) {
+            const int i = 4 * g + u;
+            const int owner = i & 31;
+            const float ui = __shfl_sync(kFullMask, i < 32 ? t1 : t2, owner) * dv[u];
+            float mi = 0.f;
+            if (want_means) mi = __shfl_sync(kFullMask, i < 32 ? n1 : n2, owner) * dv[u];
+            if (r1 == i) {
+                t1 = ui;
+                n1 = mi;
+            } else if (r1 < i) {
+                t1 = fmaf(-l1v[u], ui, t1);
+                n1 = fmaf(-l1v[u], mi, n1);
+            }
+            if (r2 == i) {
+                t2 = ui;
+                n2 = mi;
+            } else if (r2 < i) {
+                t2 = fmaf(-l2v[u], ui, t2);
+                n2 = fmaf(-l2v[u], mi, n2);
+            }
         }
     }
     x1 = t1;

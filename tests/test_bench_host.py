@@ -55,9 +55,22 @@ def test_single_rank_is_identity():
     assert bench.aggregate_rows_per_s(500, 4, 2000.0) == 1000.0
 
 
-def test_row_phase_work_figures():
+def _textbook_counts(K):
+    """Multiply-adds of a loop-by-loop Cholesky and of two triangular solves."""
+    chol = sum(j for j in range(K) for _ in range(j, K))  # row i >= j: j products
+    solves = 2 * sum(range(K))
+    return chol, solves
+
+
+def test_row_work_figures_match_loop_counts():
+    for K in (4, 16, 64):
+        chol, solves = _textbook_counts(K)
+        flops = 2 * (chol + solves)
+        # the closed form drops O(K) terms only
+        assert abs(bench.row_alu_flops(1, K) - flops) <= 4 * K
+        assert bench.row_alu_flops(3, K) == pytest.approx(3 * bench.row_alu_flops(1, K))
     K = 64
-    # per rating K(K+1) + 2K flops, per row K^3/3 + 6K^2
-    assert bench.row_phase_flops(1, 0, K) == K * (K + 1) + 2 * K
-    assert bench.row_phase_flops(0, 1, K) == pytest.approx(K**3 / 3 + 6 * K * K)
-    assert bench.row_phase_bytes(1, 1, K) == (8 + 4 * K) + (8 + 4 * K)
+    # one rating adds one outer product (K x K multiply-adds) and one scaled row (K)
+    assert bench.row_gram_flops(1, K) == 2 * (K * K + K)
+    assert bench.row_gather_bytes(1, 0, K) == 4 + 4 + 2 * 2 * K
+    assert bench.row_gather_bytes(0, 1, K) == 2 * 8 + 4 * K + 2 * 2 * K
