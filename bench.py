@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -159,7 +160,12 @@ def row_gather_bytes(nnz, rows, K, split=True):
 # DRAM bytes (read + write) per launch of the row kernel on the 480k x 18k, 1e8-rating,
 # K = 64 workload, from one ncu capture of this kernel version (null once the kernel
 # changes).
-TRAFFIC = {}
+TRAFFIC = {"rows_user": 937e6}
+
+
+def finite_or_none(x):
+    """JSON has no NaN: an RMSE that is not defined yet (before burn-in) prints as null."""
+    return x if x is not None and math.isfinite(x) else None
 
 
 def load_peaks():
@@ -217,7 +223,7 @@ def run_native(args):
     dev = torch.device("cuda", local)
     prob = make_problem(args, rank)
     K = prob.K
-    flags = bp.BPMF_BF16_GRAM if args.bf16 else 0
+    flags = 0
     stream = torch.cuda.Stream(device=dev)
     params = bp.bpmf_default_params(alpha=prob.alpha, seed=prob.seed, burn_in=prob.burn_in,
                                     flags=flags)
@@ -309,13 +315,13 @@ def run_native(args):
     out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "bf16-gram/f32" if args.bf16 else "f32", "data": "synthetic",
+           "dtype": "f32", "data": "synthetic",
            "config": {"workload": prob.name, "M": prob.M, "N": prob.N, "K": K, "nnz": nnz,
                       "test": prob.T, "sweeps_per_s": round(1e3 / ms_per_step, 3),
                       "l2": "inputs larger than L2 (ratings CSR+CSC %.2f GB)" % (nnz * 16 / 1e9),
                       "bins": {"users": [info_u["n_short"], info_u["n_long"]],
                                "movies": [info_v["n_short"], info_v["n_long"]]},
-                      "parallelism": "replicas x%d" % world, "rmse_sample": rs, "rmse_avg": ra},
+                      "parallelism": "replicas x%d" % world, "rmse_sample": finite_or_none(rs), "rmse_avg": finite_or_none(ra)},
            "roofline": roofline, "clocks": clk, "gpu_launches": int(launches), "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, desc = oracle_sample_rate(prob, args.cpu_frac)
@@ -337,7 +343,7 @@ def run_e2e(args, prob, bp, torch, dev, stream, world, local):
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     params = bp.bpmf_default_params(alpha=prob.alpha, seed=prob.seed, burn_in=prob.burn_in,
-                                    flags=bp.BPMF_BF16_GRAM if args.bf16 else 0)
+                                    flags=0)
     h = bp.bpmf_create(prob.M, prob.N, prob.K, prob.csr_ptr, prob.csr_col, prob.csr_val,
                        test_i=prob.test_i, test_j=prob.test_j, test_r=prob.test_r, params=params,
                        stream=stream.cuda_stream)
@@ -395,7 +401,6 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--config", type=int, choices=[1, 2, 3], default=3)
     ap.add_argument("--scale", type=float, default=1.0)
-    ap.add_argument("--bf16", action="store_true", help="BF16-input tensor-core Gram for long rows")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-frac", type=float, default=0.1)

@@ -43,7 +43,8 @@ extern "C" {
 #define BPMF_EGAMMA -7   /* the gamma sampler exhausted its attempts          */
 
 /* ---- flags (bpmf_params.flags) ----------------------------------------- */
-#define BPMF_BF16_GRAM 0x1u   /* long rows: BF16 inputs, FP32 accumulation on tensor cores */
+#define BPMF_BF16_GRAM 0x1u   /* reserved for a BF16-input Gram; not built: bpmf_create      
+                                 rejects it with BPMF_EINVAL                              */
 #define BPMF_CLIP 0x2u        /* clip predictions to [clip_lo, clip_hi]                   */
 #define BPMF_DEBUG_MEANS 0x4u /* keep each row's conditional mean (bpmf_debug_means)      */
 #define BPMF_NO_CENTER 0x8u   /* do not subtract the training mean from the ratings       */

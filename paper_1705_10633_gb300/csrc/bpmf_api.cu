@@ -384,6 +384,7 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
     if (prm.nu0 == 0.0) prm.nu0 = (double)K;
     if (!(prm.alpha > 0.0) || !(prm.beta0 > 0.0) || !(prm.nu0 >= (double)K)) return BPMF_EINVAL;
     if (prm.order != 0 && prm.order != 1) return BPMF_EINVAL;
+    if (prm.flags & BPMF_BF16_GRAM) return BPMF_EINVAL;  // reserved: no BF16 Gram path
     if (!valid_csr(M, N, csr_ptr, csr_col)) return BPMF_EINVAL;
     if (have_csc) {
         if (!valid_csr(N, M, csc_ptr, csc_row) || csc_ptr[N] != csr_ptr[M]) return BPMF_EINVAL;

@@ -61,7 +61,7 @@ def _tiny():
 
 
 @pytest.mark.parametrize("case", ["bad_ptr0", "decreasing", "col_range", "neg_col", "K0", "K65",
-                                  "nu0", "alpha", "W0", "test_range", "order"])
+                                  "nu0", "alpha", "W0", "test_range", "order", "bf16"])
 def test_create_rejects_malformed_input(bp, case):
     ptr, col, val = _tiny()
     M, N, K = 2, 3, 4
@@ -87,6 +87,8 @@ def test_create_rejects_malformed_input(bp, case):
         kw["W0"] = -np.eye(K)
     elif case == "order":
         kw["order"] = 2
+    elif case == "bf16":
+        kw["flags"] = bp.BPMF_BF16_GRAM
     elif case == "test_range":
         ti, tj, tr = np.array([5], np.int32), np.array([0], np.int32), np.array([1.0], np.float32)
     p = bp.bpmf_default_params(**kw)
