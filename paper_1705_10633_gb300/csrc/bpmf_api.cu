@@ -47,7 +47,11 @@ struct DevSide {
 struct bpmf_ctx {
     int device = 0;
     int num_sms = 1;
+    int row_sms = 1;  // CTAs of the row kernels: all SMs, or all but one while the
+                      // next hyper step runs beside them (bpmf_sweep)
     cudaStream_t stream = nullptr;
+    cudaStream_t aux = nullptr;  // hyper steps overlapped with row phases
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int64_t M = 0, N = 0, nnz = 0, T = 0;
     int K = 0, kp = 0;
     bool tc = false;  // long rows on the tensor-core kernel
@@ -202,12 +206,13 @@ int sync_status(bpmf_ctx* h)
     return BPMF_OK;
 }
 
-int phase_hyper(bpmf_ctx* h, int s)
+// Hyper step of side s on `st`; sweep_offset = 1 draws the next sweep's
+// hyper-parameters (the device sweep counter has not advanced yet).
+int phase_hyper(bpmf_ctx* h, int s, cudaStream_t st, uint32_t sweep_offset)
 {
     DevSide& d = h->side[s];
-    cudaError_t e = launch_hyper_reduce(d.X, d.rows, h->kp, d.mu64, d.partials, d.red_blocks,
-                                        h->stream);
-    if (e == cudaSuccess) e = launch_hyper_combine(d.partials, d.red_blocks, h->kp, d.sums, h->stream);
+    cudaError_t e = launch_hyper_reduce(d.X, d.rows, h->kp, d.mu64, d.partials, d.red_blocks, st);
+    if (e == cudaSuccess) e = launch_hyper_combine(d.partials, d.red_blocks, h->kp, d.sums, st);
     if (e != cudaSuccess) return BPMF_ECUDA;
     NWArgs a;
     a.sums = d.sums;
@@ -220,6 +225,7 @@ int phase_hyper(bpmf_ctx* h, int s)
     a.mu0 = h->mu0_d;
     a.W0inv = h->W0inv_d;
     a.seed = h->p.seed;
+    a.sweep_offset = sweep_offset;
     a.c3_normal = d.tag_hyper;
     a.c3_gamma = d.tag_gamma;
     a.ctl = h->ctl;
@@ -229,7 +235,7 @@ int phase_hyper(bpmf_ctx* h, int s)
     a.lam32 = d.lam32;
     a.lammu32 = d.lammu32;
     h->launches += 3;
-    return cuda_rc(launch_nw_sample(a, h->stream));
+    return cuda_rc(launch_nw_sample(a, st));
 }
 
 int phase_rows(bpmf_ctx* h, int s)
@@ -267,19 +273,19 @@ int phase_rows(bpmf_ctx* h, int s)
         a.rows = d.bin_rows;
         a.nrows = d.n_short + d.n_long;
         if (a.nrows > 0) h->launches += 1;
-        return cuda_rc(launch_rows_warp(a, h->kp, h->num_sms, h->stream));
+        return cuda_rc(launch_rows_warp(a, h->kp, h->row_sms, h->stream));
     }
     a.rows = d.bin_rows;
     a.nrows = d.n_short;
     if (a.nrows > 0) {
         h->launches += 1;
-        e = launch_rows_warp(a, h->kp, h->num_sms, h->stream);
+        e = launch_rows_warp(a, h->kp, h->row_sms, h->stream);
     }
     a.rows = d.bin_rows + d.n_short;
     a.nrows = d.n_long;
     if (e == cudaSuccess && a.nrows > 0) {
         h->launches += 1;
-        e = launch_rows_tc(a, h->num_sms, h->stream);
+        e = launch_rows_tc(a, h->row_sms, h->stream);
     }
     return cuda_rc(e);
 }
@@ -304,8 +310,8 @@ int phase_predict(bpmf_ctx* h)
 int run_phase(bpmf_ctx* h, int phase)
 {
     switch (phase) {
-    case BPMF_PHASE_HYPER_USER: return phase_hyper(h, BPMF_USER);
-    case BPMF_PHASE_HYPER_MOVIE: return phase_hyper(h, BPMF_MOVIE);
+    case BPMF_PHASE_HYPER_USER: return phase_hyper(h, BPMF_USER, h->stream, 0);
+    case BPMF_PHASE_HYPER_MOVIE: return phase_hyper(h, BPMF_MOVIE, h->stream, 0);
     case BPMF_PHASE_ROWS_USER: return phase_rows(h, BPMF_USER);
     case BPMF_PHASE_ROWS_MOVIE: return phase_rows(h, BPMF_MOVIE);
     case BPMF_PHASE_PREDICT: return phase_predict(h);
@@ -356,6 +362,12 @@ int bpmf_destroy(bpmf_handle h)
 {
     if (!h) return BPMF_OK;
     cudaStreamSynchronize(h->stream);
+    if (h->aux) {
+        cudaStreamSynchronize(h->aux);
+        cudaStreamDestroy(h->aux);
+    }
+    for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
     for (void* ptr : h->allocs) {
         if (h->p.free) h->p.free(ptr, (void*)h->stream, h->p.alloc_ctx);
         else cudaFree(ptr);
@@ -415,10 +427,19 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
         return BPMF_EINVAL;
     }
     if (cudaGetDevice(&h->device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         delete h;
         return BPMF_ECUDA;
+    }
+    h->row_sms = h->num_sms;
+    for (cudaEvent_t& e : h->ev) {
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            bpmf_destroy(h);
+            return BPMF_ECUDA;
+        }
     }
     // training mean in index order (FP64)
     double total = 0.0;
@@ -527,6 +548,49 @@ int bpmf_step(bpmf_handle h, int32_t phase)
     return run_phase(h, phase);
 }
 
+namespace {
+
+// n sweeps with each hyper step on the aux stream, overlapped with a row phase
+// (Alg. 1's data dependencies: the second side's hyper step needs that side's rows
+// of the previous sweep only, the first side's needs this sweep's first-side rows):
+//   main: [hyper(1st) s0] | rows(1st) | wait H2 | rows(2nd) | predict | wait H1 | advance
+//   aux:    wait A: hyper(2nd) s -> H2 | wait R1: hyper(1st) s+1 -> H1
+// The row kernels leave one SM to the aux stream.  advance waits for the aux stream, so
+// the device sweep counter never moves under a hyper step.
+int sweep_overlapped(bpmf_ctx* h, int n_sweeps, int first)
+{
+    const int second = 1 - first;
+    const int rowp[2] = {BPMF_PHASE_ROWS_USER, BPMF_PHASE_ROWS_MOVIE};
+    cudaEvent_t evA = h->ev[0], evR1 = h->ev[1], evH2 = h->ev[2], evH1 = h->ev[3];
+    int rc = phase_hyper(h, first, h->stream, 0);
+    h->row_sms = h->num_sms - 1;
+    for (int it = 0; it < n_sweeps && rc == BPMF_OK; ++it) {
+        const bool last = it + 1 == n_sweeps;
+        cudaError_t e = cudaEventRecord(evA, h->stream);
+        if (e == cudaSuccess) rc = run_phase(h, rowp[first]);
+        if (e == cudaSuccess && rc == BPMF_OK) e = cudaEventRecord(evR1, h->stream);
+        if (e == cudaSuccess && rc == BPMF_OK) e = cudaStreamWaitEvent(h->aux, evA, 0);
+        if (e == cudaSuccess && rc == BPMF_OK) rc = phase_hyper(h, second, h->aux, 0);
+        if (e == cudaSuccess && rc == BPMF_OK) e = cudaEventRecord(evH2, h->aux);
+        if (e == cudaSuccess && rc == BPMF_OK && !last) {
+            e = cudaStreamWaitEvent(h->aux, evR1, 0);
+            if (e == cudaSuccess) rc = phase_hyper(h, first, h->aux, 1);
+            if (e == cudaSuccess && rc == BPMF_OK) e = cudaEventRecord(evH1, h->aux);
+        }
+        if (e == cudaSuccess && rc == BPMF_OK) e = cudaStreamWaitEvent(h->stream, evH2, 0);
+        if (e == cudaSuccess && rc == BPMF_OK) rc = run_phase(h, rowp[second]);
+        if (e == cudaSuccess && rc == BPMF_OK) rc = run_phase(h, BPMF_PHASE_PREDICT);
+        if (e == cudaSuccess && rc == BPMF_OK && !last) e = cudaStreamWaitEvent(h->stream, evH1, 0);
+        if (e == cudaSuccess && rc == BPMF_OK) rc = run_phase(h, BPMF_PHASE_ADVANCE);
+        if (e != cudaSuccess) rc = BPMF_ECUDA;
+    }
+    h->row_sms = h->num_sms;
+    // the main stream has waited for everything the aux stream was given
+    return rc;
+}
+
+}  // namespace
+
 int bpmf_sweep(bpmf_handle h, int32_t n_sweeps, double* rmse_sample, double* rmse_avg)
 {
     if (!h || n_sweeps < 0) return BPMF_EINVAL;
@@ -534,12 +598,17 @@ int bpmf_sweep(bpmf_handle h, int32_t n_sweeps, double* rmse_sample, double* rms
     const int second = 1 - first;
     const int hyp[2] = {BPMF_PHASE_HYPER_USER, BPMF_PHASE_HYPER_MOVIE};
     const int rowp[2] = {BPMF_PHASE_ROWS_USER, BPMF_PHASE_ROWS_MOVIE};
-    for (int it = 0; it < n_sweeps; ++it) {
-        const int seq[6] = {hyp[first], rowp[first], hyp[second], rowp[second], BPMF_PHASE_PREDICT,
-                            BPMF_PHASE_ADVANCE};
-        for (int ph : seq) {
-            const int rc = run_phase(h, ph);
-            if (rc) return rc;
+    if (n_sweeps > 0 && h->num_sms >= 8) {
+        const int rc = sweep_overlapped(h, n_sweeps, first);
+        if (rc) return rc;
+    } else {
+        for (int it = 0; it < n_sweeps; ++it) {
+            const int seq[6] = {hyp[first], rowp[first], hyp[second], rowp[second],
+                                BPMF_PHASE_PREDICT, BPMF_PHASE_ADVANCE};
+            for (int ph : seq) {
+                const int rc = run_phase(h, ph);
+                if (rc) return rc;
+            }
         }
     }
     if (rmse_sample || rmse_avg) {

@@ -75,6 +75,7 @@ struct NWArgs {
     const double* mu0;      // K
     const double* W0inv;    // K x K
     uint64_t seed;
+    uint32_t sweep_offset;  // the draw belongs to sweep ctl->sweep + sweep_offset
     uint32_t c3_normal, c3_gamma;
     Control* ctl;
     double* stats;          // out: mean (K), S (K x K)

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kNWThreads) nw_sample_kernel(NWArgs a)
     double* w = mustar + K;
     double* z = w + K;
     __shared__ int bad, gbad;
-    const uint32_t sweep = (uint32_t)a.ctl->sweep;
+    const uint32_t sweep = (uint32_t)a.ctl->sweep + a.sweep_offset;
     const double n = (double)a.n;
     if (t == 0) { bad = 0; gbad = 0; }
     // ---- statistics: mean = s + S1/n, S = S2/n - d d^T with d = S1/n ----

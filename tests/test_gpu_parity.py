@@ -131,15 +131,24 @@ def test_three_sweeps_config1(bp):
     assert_worst(step_parity(bp, workloads.config1(), sweeps=3))
 
 
-def test_sweep_entry_point_matches_phases(bp):
-    prob = workloads.random_small(150, 70, 8, 1500, seed=9, n_test=60)
-    a = bp.create_from_problem(prob, stream=bp.torch_stream())
-    b = bp.create_from_problem(prob, stream=bp.torch_stream())
+@pytest.mark.parametrize("K,order", [(8, 0), (64, 0), (64, 1)])
+def test_sweep_entry_point_matches_phases(bp, K, order):
+    """bpmf_sweep overlaps each hyper step with a row phase on a second stream and runs
+    the row kernels on one SM fewer; the chain must equal phase-by-phase stepping bit
+    for bit (both sweep orders, CUDA-core and tensor-core row kernels)."""
+    prob = workloads.random_small(150, 70, K, 1500 if K == 8 else 6000, seed=9, n_test=60)
+    a = bp.create_from_problem(prob, order=order, stream=bp.torch_stream())
+    b = bp.create_from_problem(prob, order=order, stream=bp.torch_stream())
     try:
+        if K == 64:
+            assert bp.bpmf_info(a, 0)["n_long"] > 0
         ra = bp.bpmf_sweep(a, 3)
+        seq = (bp.BPMF_PHASE_HYPER_MOVIE, bp.BPMF_PHASE_ROWS_MOVIE, bp.BPMF_PHASE_HYPER_USER,
+               bp.BPMF_PHASE_ROWS_USER)
+        if order == 1:
+            seq = seq[2:] + seq[:2]
         for _ in range(3):
-            for ph in (bp.BPMF_PHASE_HYPER_MOVIE, bp.BPMF_PHASE_ROWS_MOVIE, bp.BPMF_PHASE_HYPER_USER,
-                       bp.BPMF_PHASE_ROWS_USER, bp.BPMF_PHASE_PREDICT, bp.BPMF_PHASE_ADVANCE):
+            for ph in seq + (bp.BPMF_PHASE_PREDICT, bp.BPMF_PHASE_ADVANCE):
                 bp.bpmf_step(b, ph)
         rb = bp.bpmf_sweep(b, 0)
         sa = bp.bpmf_get_state(a, prob.M, prob.N, prob.K)
