@@ -31,7 +31,9 @@ struct DevSide {
     float* means = nullptr;
     int32_t* bin_rows = nullptr;  // short bin first, then long bin, each longest first
     int64_t n_short = 0, n_long = 0;
+    int64_t long_ratings = 0;  // ratings of the long bin's rows
     double* mu64 = nullptr;
+    double* shift64 = nullptr;  // kp: shift of the hyper statistics
     double* lam64 = nullptr;
     float* lam32 = nullptr;
     float* lammu32 = nullptr;
@@ -176,7 +178,7 @@ void build_csc(int64_t M, int64_t N, const int64_t* rp, const int32_t* ci, const
 // ordered by decreasing degree so that a grid-stride loop hands the longest
 // rows out first (the per-item cost model of Sec. 4.2: fixed + per-rating cost).
 void bin_rows(int64_t rows, const int64_t* ptr, int64_t long_min, std::vector<int32_t>& order,
-              int64_t* n_short, int64_t* n_long)
+              int64_t* n_short, int64_t* n_long, int64_t* long_ratings)
 {
     order.resize((size_t)rows);
     std::iota(order.begin(), order.end(), 0);
@@ -186,11 +188,15 @@ void bin_rows(int64_t rows, const int64_t* ptr, int64_t long_min, std::vector<in
         if (la != lb) return lb;  // short bin first
         return da > db;
     });
-    int64_t ns = 0;
-    for (int64_t r = 0; r < rows; ++r)
-        if (ptr[r + 1] - ptr[r] < long_min) ++ns;
+    int64_t ns = 0, nl_ratings = 0;
+    for (int64_t r = 0; r < rows; ++r) {
+        const int64_t d = ptr[r + 1] - ptr[r];
+        if (d < long_min) ++ns;
+        else nl_ratings += d;
+    }
     *n_short = ns;
     *n_long = rows - ns;
+    *long_ratings = nl_ratings;
 }
 
 int sync_status(bpmf_ctx* h)
@@ -211,12 +217,14 @@ int sync_status(bpmf_ctx* h)
 int phase_hyper(bpmf_ctx* h, int s, cudaStream_t st, uint32_t sweep_offset)
 {
     DevSide& d = h->side[s];
-    cudaError_t e = launch_hyper_reduce(d.X, d.rows, h->kp, d.mu64, d.partials, d.red_blocks, st);
+    cudaError_t e = launch_hyper_shift(d.X, d.rows, h->K, h->kp, d.shift64, st);
+    if (e == cudaSuccess)
+        e = launch_hyper_reduce(d.X, d.rows, h->kp, d.shift64, d.partials, d.red_blocks, st);
     if (e == cudaSuccess) e = launch_hyper_combine(d.partials, d.red_blocks, h->kp, d.sums, st);
     if (e != cudaSuccess) return BPMF_ECUDA;
     NWArgs a;
     a.sums = d.sums;
-    a.shift64 = d.mu64;
+    a.shift64 = d.shift64;
     a.n = d.rows;
     a.K = h->K;
     a.kp = h->kp;
@@ -234,7 +242,7 @@ int phase_hyper(bpmf_ctx* h, int s, cudaStream_t st, uint32_t sweep_offset)
     a.lam64 = d.lam64;
     a.lam32 = d.lam32;
     a.lammu32 = d.lammu32;
-    h->launches += 3;
+    h->launches += 4;
     return cuda_rc(launch_nw_sample(a, st));
 }
 
@@ -285,7 +293,7 @@ int phase_rows(bpmf_ctx* h, int s)
     a.nrows = d.n_long;
     if (e == cudaSuccess && a.nrows > 0) {
         h->launches += 1;
-        e = launch_rows_tc(a, h->row_sms, h->stream);
+        e = launch_rows_tc(a, d.long_ratings, h->row_sms, h->stream);
     }
     return cuda_rc(e);
 }
@@ -474,7 +482,7 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
         d.red_blocks = hyper_reduce_blocks(d.rows, h->num_sms);
         bool ok = alloc_n(h, &d.ptr, d.rows + 1) && alloc_n(h, &d.idx, h->nnz) &&
                   alloc_n(h, &d.val, h->nnz) && alloc_n(h, &d.X, (size_t)d.rows * kp) &&
-                  alloc_n(h, &d.bin_rows, d.rows) && alloc_n(h, &d.mu64, K) &&
+                  alloc_n(h, &d.bin_rows, d.rows) && alloc_n(h, &d.mu64, K) && alloc_n(h, &d.shift64, kp) &&
                   alloc_n(h, &d.lam64, (size_t)K * K) && alloc_n(h, &d.lam32, (size_t)2 * kp * kp) &&
                   alloc_n(h, &d.lammu32, kp) &&
                   alloc_n(h, &d.partials, (size_t)d.red_blocks * hyper_partial_doubles(kp)) &&
@@ -487,7 +495,7 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
             rc = BPMF_ENOMEM;
             break;
         }
-        bin_rows(d.rows, hp[s], long_min, order, &d.n_short, &d.n_long);
+        bin_rows(d.rows, hp[s], long_min, order, &d.n_short, &d.n_long, &d.long_ratings);
         cudaError_t e = cudaMemcpyAsync(d.ptr, hp[s], sizeof(int64_t) * (d.rows + 1),
                                         cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess && h->nnz)

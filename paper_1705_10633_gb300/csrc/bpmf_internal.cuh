@@ -54,6 +54,10 @@ cudaError_t launch_init_factors(float* X, int64_t rows, int K, int ld, uint64_t 
                                 cudaStream_t s);
 cudaError_t launch_center_values(float* val, int64_t n, double rbar, cudaStream_t s);
 
+// Hyper step, part 0: the shift (FP64 mean of the first rows, kp entries, zero
+// beyond K) that parts 1 and 2 subtract.
+cudaError_t launch_hyper_shift(const float* X, int64_t rows, int K, int kp, double* shift64,
+                               cudaStream_t s);
 // Hyper step, part 1: per-block partial sums of (x - shift) and (x - shift)(x - shift)^T.
 int hyper_reduce_blocks(int64_t rows, int num_sms);
 __host__ __device__ inline size_t hyper_partial_doubles(int kp)
@@ -68,7 +72,7 @@ cudaError_t launch_hyper_combine(const double* partials, int nblocks, int kp, do
 
 struct NWArgs {
     const double* sums;     // kp + kp*kp raw sums from the reduction
-    const double* shift64;  // kp, shift used by the reduction (= previous mu)
+    const double* shift64;  // kp, shift used by the reduction (mean of the first rows)
     int64_t n;              // rows of this side
     int K, kp;
     double beta0, nu0;
@@ -98,7 +102,8 @@ cudaError_t launch_hyper_refresh(const double* mu64, const double* lam64, int K,
 // Row updates on CUDA cores: one warp per row (any degree).
 cudaError_t launch_rows_warp(const RowArgs& a, int kp, int num_sms, cudaStream_t s);
 // Row updates with the Gram on tensor cores (kp == 64, rows of the long bin).
-cudaError_t launch_rows_tc(const RowArgs& a, int num_sms, cudaStream_t s);
+// nratings: ratings of the rows in a.rows (their mean degree picks the CTA shape).
+cudaError_t launch_rows_tc(const RowArgs& a, int64_t nratings, int num_sms, cudaStream_t s);
 // FP16 hi/lo split of a factor matrix (after init or set_state).
 cudaError_t launch_split_factors(const float* X, int64_t rows, int ld, __half* Xh, __half* Xl,
                                  cudaStream_t s);

@@ -102,6 +102,32 @@ __global__ void __launch_bounds__(kRedThreads) hyper_reduce_kernel(const float* 
         for (int j = 0; j < TT; ++j) out[KT + (ty * TT + i) * KT + tx * TT + j] = acc64[i][j];
 }
 
+// Shift for the statistics: the FP64 mean of the first rows (at most kShiftRows),
+// zero beyond K.  Subtracting a value near the mean keeps the FP32 chunk sums of
+// (x - s)(x - s)^T from cancelling against d d^T; a shift taken from the data itself
+// (rather than from the last drawn mu, which can sit far from the sample mean when a
+// side has few rows) and computed in a fixed order keeps resumed chains bit-identical.
+constexpr int64_t kShiftRows = 256;
+
+__global__ void hyper_shift_kernel(const float* __restrict__ X, int64_t rows, int K, int kp,
+                                   double* __restrict__ shift64)
+{
+    const int t = threadIdx.x;
+    if (t >= kp) return;
+    const int64_t n = rows < kShiftRows ? rows : kShiftRows;
+    double s = 0.0;
+    if (t < K)
+        for (int64_t r = 0; r < n; ++r) s += (double)X[r * kp + t];
+    shift64[t] = (t < K && n > 0) ? s / (double)n : 0.0;
+}
+
+cudaError_t launch_hyper_shift(const float* X, int64_t rows, int K, int kp, double* shift64,
+                               cudaStream_t s)
+{
+    hyper_shift_kernel<<<1, 64, 0, s>>>(X, rows, K, kp, shift64);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_hyper_reduce(const float* X, int64_t rows, int kp, const double* shift64,
                                 double* partials, int nblocks, cudaStream_t s)
 {

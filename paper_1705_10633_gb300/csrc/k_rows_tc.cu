@@ -39,11 +39,8 @@ namespace {
 
 constexpr int kKT = 64;
 constexpr int kStageRatings = 64;
-constexpr int kNStage = 3;
 constexpr int kNAcc = 3;
 constexpr int kChunkStages = 16;  // stages per TMEM accumulation before it is flushed
-constexpr int kNChol = 8;
-constexpr int kThreads = 512;
 constexpr int kGatherThreads = 64;
 constexpr int kRowRing = 32;   // row descriptors in flight
 constexpr int kIdxRing = 8;    // stages of rating indices / values in flight
@@ -58,16 +55,36 @@ constexpr uint32_t kStageBytes = 2 * kTileBytes + kRBytes;  // 24 KB (1 KB multi
 constexpr uint32_t kLamFloats = 64 * 64 + 64;
 constexpr uint32_t kCholScratchFloats = 2 * 64 + 64 + 64;
 
-constexpr uint32_t kOffStages = 0;
-constexpr uint32_t kOffLam = kOffStages + kNStage * kStageBytes;
-constexpr uint32_t kOffChol = kOffLam + kNChol * kLamFloats * 4;
-constexpr uint32_t kOffRtmp = kOffChol + kNChol * kCholScratchFloats * 4;
-constexpr uint32_t kOffRowRing = kOffRtmp + 64 * 4;          // kRowRing x 32 B
-constexpr uint32_t kOffIdxRing = kOffRowRing + kRowRing * 32;  // kIdxRing x (64 idx + 64 val)
-constexpr uint32_t kOffBars = kOffIdxRing + kIdxRing * 512;
-constexpr int kNumBars = 2 * kNStage + 2 * kNAcc + 2 * kNChol + 2 * kRowRing + 2 * kIdxRing + 1;
-constexpr uint32_t kOffMisc = kOffBars + kNumBars * 8;
-constexpr uint32_t kSmemBytes = kOffMisc + 16 + 1024;  // + alignment slack
+// Two shapes of the CTA, chosen per launch by the rows' mean degree:
+//   NCHOL Cholesky warps (and Lambda buffers) and NSTAGE gather stages.
+// Rows of a few hundred ratings need many rows in factorisation at once (8, 3);
+// rows of thousands of ratings, whose gathered rows come partly from HBM, need
+// more copies in flight and few rows in factorisation (4, 6).  Registers after
+// setmaxnreg: warps 0-3 kProdRegs, drain kDrainRegs, Cholesky kCholRegs.
+template <int NCHOL, int NSTAGE>
+struct TcShape {
+    static constexpr int kNChol = NCHOL;
+    static constexpr int kNStage = NSTAGE;
+    static constexpr int kThreads = (8 + NCHOL) * 32;
+    static constexpr uint32_t kOffStages = 0;
+    static constexpr uint32_t kOffLam = kOffStages + NSTAGE * kStageBytes;
+    static constexpr uint32_t kOffChol = kOffLam + NCHOL * kLamFloats * 4;
+    static constexpr uint32_t kOffRtmp = kOffChol + NCHOL * kCholScratchFloats * 4;
+    static constexpr uint32_t kOffRowRing = kOffRtmp + 64 * 4;          // kRowRing x 32 B
+    static constexpr uint32_t kOffIdxRing = kOffRowRing + kRowRing * 32;  // kIdxRing x (64 idx + 64 val)
+    static constexpr uint32_t kOffBars = kOffIdxRing + kIdxRing * 512;
+    static constexpr int kNumBars = 2 * NSTAGE + 2 * kNAcc + 2 * NCHOL + 2 * kRowRing + 2 * kIdxRing + 1;
+    static constexpr uint32_t kOffMisc = kOffBars + kNumBars * 8;
+    static constexpr uint32_t kSmemBytes = kOffMisc + 16 + 1024;  // + alignment slack
+    // the launch gives 65536 / kThreads registers a thread (128 or 168)
+    static constexpr int kProdRegs = NCHOL == 8 ? 72 : 96;
+    static constexpr int kDrainRegs = NCHOL == 8 ? 96 : 128;
+    static constexpr int kCholRegs = NCHOL == 8 ? 168 : 176;
+    static_assert(kSmemBytes <= 232448, "shared memory");
+    static_assert(32 * (4 * kProdRegs + 4 * kDrainRegs + NCHOL * kCholRegs) <= 65536, "registers");
+};
+using ShapeShortRows = TcShape<8, 3>;
+using ShapeLongRows = TcShape<4, 6>;
 
 // Instruction descriptor of kind::f16: D = F32, A = B = F16, both MN-major.
 constexpr uint32_t make_idesc(int M, int N)
@@ -253,8 +270,14 @@ __device__ __forceinline__ void drain_rows(uint32_t taddr, float* L, int m, int 
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
+template <class Shape>
+__global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
 {
+    constexpr int kNChol = Shape::kNChol, kNStage = Shape::kNStage, kThreads = Shape::kThreads;
+    constexpr uint32_t kOffStages = Shape::kOffStages, kOffLam = Shape::kOffLam;
+    constexpr uint32_t kOffChol = Shape::kOffChol, kOffRtmp = Shape::kOffRtmp;
+    constexpr uint32_t kOffRowRing = Shape::kOffRowRing, kOffIdxRing = Shape::kOffIdxRing;
+    constexpr uint32_t kOffBars = Shape::kOffBars, kOffMisc = Shape::kOffMisc;
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
@@ -339,9 +362,7 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
     constexpr int64_t kChunkRatings = (int64_t)kChunkStages * kStageRatings;
 
     if (warp < 4) {
-        // register split (launch: 512 threads x 128): warps 0-3 72, drain 96,
-        // Cholesky 168 -> 32 x (4 x 72 + 4 x 96 + 8 x 168) = 64,512 <= 65,536
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 72;" ::: "memory");
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(Shape::kProdRegs) : "memory");
         if (warp == 0) {
             // ======================= MMA issuer =======================
             if (lane == 0) {
@@ -501,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
         }
     } else if (warp < 8) {
         // ======================= TMEM drain =======================
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 96;" ::: "memory");
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(Shape::kDrainRegs) : "memory");
         const int quarter = warp & 3;
         const int m = 32 * (quarter & 1) + lane;  // row of Lambda this thread serves
         const float alpha = a.alpha;
@@ -564,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
         }
     } else {
         // ======================= Cholesky, solve, sample =======================
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 168;" ::: "memory");
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(Shape::kCholRegs) : "memory");
         const int cw = warp - 8;
         float* scratch = chol_scratch + cw * kCholScratchFloats;
         float* colbuf = scratch;
@@ -604,15 +625,26 @@ __global__ void __launch_bounds__(kThreads, 1) rows_tc_kernel(RowArgs a)
     }
 }
 
-cudaError_t launch_rows_tc(const RowArgs& a, int num_sms, cudaStream_t s)
+template <class Shape>
+cudaError_t launch_shape(const RowArgs& a, int num_sms, cudaStream_t s)
 {
-    if (a.nrows <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(rows_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(rows_tc_kernel<Shape>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Shape::kSmemBytes);
     if (e != cudaSuccess) return e;
     int64_t grid = a.nrows < num_sms ? a.nrows : num_sms;
-    rows_tc_kernel<<<(unsigned)grid, kThreads, kSmemBytes, s>>>(a);
+    rows_tc_kernel<Shape><<<(unsigned)grid, Shape::kThreads, Shape::kSmemBytes, s>>>(a);
     return cudaGetLastError();
+}
+
+// Rows averaging this many ratings or more take the shape with more gather stages.
+constexpr int64_t kLongRowShapeDegree = 1024;
+
+cudaError_t launch_rows_tc(const RowArgs& a, int64_t nratings, int num_sms, cudaStream_t s)
+{
+    if (a.nrows <= 0) return cudaSuccess;
+    if (nratings >= kLongRowShapeDegree * a.nrows) return launch_shape<ShapeLongRows>(a, num_sms, s);
+    return launch_shape<ShapeShortRows>(a, num_sms, s);
 }
 
 __global__ void split_factors_kernel(const float* __restrict__ X, int64_t n, __half* __restrict__ Xh,

@@ -40,6 +40,16 @@ def test_long_rows_tensor_core_parity(bp, K, long_min):
     assert_worst(step_parity(bp, prob, sweeps=2, long_min_degree=long_min))
 
 
+def test_long_row_shape_parity(bp):
+    # 40 movies with ~3,000 ratings each: the movie side's mean degree selects the CTA
+    # shape with 6 gather stages and 4 factorisation warps; rows span 1-3 chunks of
+    # 1024 ratings (so a row's accumulator is drained more than once)
+    prob = workloads.random_small(8000, 40, 64, 150000, seed=31, n_test=300)
+    deg = prob.col_degrees()
+    assert deg.mean() >= 1024 and deg.max() > 2048
+    assert_worst(step_parity(bp, prob, sweeps=2))
+
+
 def test_tensor_core_and_cuda_core_paths_agree(bp):
     prob = workloads.random_small(500, 260, 64, 30000, seed=77, n_test=100)
     K = prob.K

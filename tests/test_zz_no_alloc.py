@@ -28,10 +28,15 @@ def test_row_stats_noalloc_matches_hyper_step_twice():
         try:
             rng = np.random.default_rng(K)
             U = (rng.standard_normal((prob.M, K)) * 0.7 + 0.2).astype(np.float32)
+            assert prob.M >= 256
             _, V, hyper, s = bp.bpmf_get_state(h, prob.M, prob.N, K)
-            hyper[:K] = rng.standard_normal(K) * 0.1  # mu_U: the shift the hyper step uses
-            shift = hyper[:K].copy()
             bp.bpmf_set_state(h, U, V, hyper, s)
+            # the shift the hyper step uses: the FP64 mean of the first 256 rows, summed
+            # row by row in order
+            acc = np.zeros(K)
+            for r in range(256):
+                acc += U[r].astype(np.float64)
+            shift = acc / 256.0
             bp.bpmf_step(h, bp.BPMF_PHASE_HYPER_USER)
             n, mean_ref, S_ref = bp.bpmf_get_stats(h, 0, K)
         finally:
