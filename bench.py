@@ -223,7 +223,7 @@ def run_native(args):
     dev = torch.device("cuda", local)
     prob = make_problem(args, rank)
     K = prob.K
-    flags = 0
+    flags = bp.BPMF_BF16_GRAM if args.bf16 else 0
     stream = torch.cuda.Stream(device=dev)
     params = bp.bpmf_default_params(alpha=prob.alpha, seed=prob.seed, burn_in=prob.burn_in,
                                     flags=flags)
@@ -329,7 +329,7 @@ def run_native(args):
     out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32", "data": "synthetic",
+           "dtype": "bf16-gram/f32" if args.bf16 else "f32", "data": "synthetic",
            "config": {"workload": prob.name, "M": prob.M, "N": prob.N, "K": K, "nnz": nnz,
                       "test": prob.T, "sweeps_per_s": round(1e3 / ms_per_step, 3),
                       "l2": "inputs larger than L2 (ratings CSR+CSC %.2f GB)" % (nnz * 16 / 1e9),
@@ -357,7 +357,7 @@ def run_e2e(args, prob, bp, torch, dev, stream, world, local):
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     params = bp.bpmf_default_params(alpha=prob.alpha, seed=prob.seed, burn_in=prob.burn_in,
-                                    flags=0)
+                                    flags=bp.BPMF_BF16_GRAM if args.bf16 else 0)
     h = bp.bpmf_create(prob.M, prob.N, prob.K, prob.csr_ptr, prob.csr_col, prob.csr_val,
                        test_i=prob.test_i, test_j=prob.test_j, test_r=prob.test_r, params=params,
                        stream=stream.cuda_stream)
@@ -415,6 +415,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--config", type=int, choices=[1, 2, 3], default=3)
     ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--bf16", action="store_true",
+                    help="BF16-input tensor-core Gram (lower precision; not the headline)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-frac", type=float, default=0.1)

@@ -43,8 +43,11 @@ extern "C" {
 #define BPMF_EGAMMA -7   /* the gamma sampler exhausted its attempts          */
 
 /* ---- flags (bpmf_params.flags) ----------------------------------------- */
-#define BPMF_BF16_GRAM 0x1u   /* reserved for a BF16-input Gram; not built: bpmf_create      
-                                 rejects it with BPMF_EINVAL                              */
+#define BPMF_BF16_GRAM 0x1u   /* tensor-core Gram from BF16 copies of the other side's
+                                 rows (one 128-B row per rating instead of the FP16 hi/lo
+                                 pair): half the gathered bytes, ~2^-8 relative error in
+                                 the Gram; needs K in 49..64 without BPMF_CUDA_CORE_GRAM,
+                                 else bpmf_create returns BPMF_EINVAL                     */
 #define BPMF_CLIP 0x2u        /* clip predictions to [clip_lo, clip_hi]                   */
 #define BPMF_DEBUG_MEANS 0x4u /* keep each row's conditional mean (bpmf_debug_means)      */
 #define BPMF_NO_CENTER 0x8u   /* do not subtract the training mean from the ratings       */

@@ -275,6 +275,7 @@ int phase_rows(bpmf_ctx* h, int s)
     a.timeout_ns = (int64_t)(h->p.wait_timeout_ms > 0 ? h->p.wait_timeout_ms : kDefaultWaitTimeoutMs) *
                    1000000LL;
     a.test_stall = (h->p.flags & BPMF_TEST_STALL) ? 1 : 0;
+    a.bf16 = (h->p.flags & BPMF_BF16_GRAM) ? 1 : 0;
     cudaError_t e = cudaSuccess;
     if (!h->tc) {
         // every row on the CUDA-core kernel
@@ -404,7 +405,6 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
     if (prm.nu0 == 0.0) prm.nu0 = (double)K;
     if (!(prm.alpha > 0.0) || !(prm.beta0 > 0.0) || !(prm.nu0 >= (double)K)) return BPMF_EINVAL;
     if (prm.order != 0 && prm.order != 1) return BPMF_EINVAL;
-    if (prm.flags & BPMF_BF16_GRAM) return BPMF_EINVAL;  // reserved: no BF16 Gram path
     if (!valid_csr(M, N, csr_ptr, csr_col)) return BPMF_EINVAL;
     if (have_csc) {
         if (!valid_csr(N, M, csc_ptr, csc_row) || csc_ptr[N] != csr_ptr[M]) return BPMF_EINVAL;
@@ -420,6 +420,11 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
     h->K = K;
     h->kp = (K + 15) / 16 * 16;
     h->tc = h->kp == 64 && !(prm.flags & BPMF_CUDA_CORE_GRAM);
+    // the BF16 Gram is a mode of the tensor-core kernel
+    if ((prm.flags & BPMF_BF16_GRAM) && !h->tc) {
+        delete h;
+        return BPMF_EINVAL;
+    }
     h->T = T;
     h->nnz = csr_ptr[M];
     h->stream = (cudaStream_t)cuda_stream;
@@ -507,7 +512,7 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
                                 cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = launch_center_values(d.val, h->nnz, h->rbar, st);
         if (e == cudaSuccess) e = launch_init_factors(d.X, d.rows, K, kp, prm.seed, d.tag_init, st);
-        if (e == cudaSuccess && d.Xh) e = launch_split_factors(d.X, d.rows, kp, d.Xh, d.Xl, st);
+        if (e == cudaSuccess && d.Xh) e = launch_split_factors(d.X, d.rows, kp, d.Xh, d.Xl, (h->p.flags & BPMF_BF16_GRAM) ? 1 : 0, st);
         if (e == cudaSuccess && d.means) e = cudaMemsetAsync(d.means, 0, sizeof(float) * d.rows * kp, st);
         // initial hyper state: mu = 0, Lambda = I
         std::vector<double> I((size_t)K * K, 0.0);
@@ -710,7 +715,7 @@ int bpmf_set_state(bpmf_handle h, const float* U, const float* V, const double* 
             rc = cuda_rc(cudaMemcpy2DAsync(d.X, sizeof(float) * kp, src[s], sizeof(float) * K,
                                            sizeof(float) * K, (size_t)d.rows,
                                            cudaMemcpyHostToDevice, st));
-        if (!rc && d.Xh) rc = cuda_rc(launch_split_factors(d.X, d.rows, kp, d.Xh, d.Xl, st));
+        if (!rc && d.Xh) rc = cuda_rc(launch_split_factors(d.X, d.rows, kp, d.Xh, d.Xl, (h->p.flags & BPMF_BF16_GRAM) ? 1 : 0, st));
     }
     if (!rc && hyper) {
         const double* in = hyper;

@@ -44,6 +44,7 @@ struct RowArgs {
     uint32_t c3;           // Philox tag word of this side's row noise
     int64_t timeout_ns;    // bound on every device wait (tensor-core kernel)
     int test_stall;        // test only: producers never signal (exercises the timeout path)
+    int bf16;              // Xh / Xl / Yh hold BF16 (the tensor-core Gram takes Yh only)
     int ldx, ldy;
     int K;
     float alpha;
@@ -106,7 +107,7 @@ cudaError_t launch_rows_warp(const RowArgs& a, int kp, int num_sms, cudaStream_t
 cudaError_t launch_rows_tc(const RowArgs& a, int64_t nratings, int num_sms, cudaStream_t s);
 // FP16 hi/lo split of a factor matrix (after init or set_state).
 cudaError_t launch_split_factors(const float* X, int64_t rows, int ld, __half* Xh, __half* Xl,
-                                 cudaStream_t s);
+                                 int bf16, cudaStream_t s);
 
 enum : unsigned int { kStatusTimeout = 8u };
 

@@ -93,6 +93,7 @@ constexpr uint32_t make_idesc(int M, int N)
            ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 constexpr uint32_t kIdesc = make_idesc(128, 144);
+constexpr uint32_t kIdescBf16 = kIdesc | (1u << 7) | (1u << 10);  // A and B in BF16
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -270,7 +271,7 @@ __device__ __forceinline__ void drain_rows(uint32_t taddr, float* L, int m, int 
     }
 }
 
-template <class Shape>
+template <class Shape, bool kBf16>
 __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
 {
     constexpr int kNChol = Shape::kNChol, kNStage = Shape::kNStage, kThreads = Shape::kThreads;
@@ -310,11 +311,15 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
     const int64_t nj = a.nrows > blockIdx.x ? (a.nrows - blockIdx.x + G - 1) / G : 0;
     const WaitCtx wc{abort_flag, a.timeout_ns, a.ctl};
 
-    // ---- set-up: zero the RHS operand tiles, barriers, TMEM
+    // ---- set-up: zero the ratings atoms (and the l atoms, which the BF16 Gram leaves
+    // unused), barriers, TMEM
     for (uint32_t e = tid; e < kNStage * kRBytes / 16; e += kThreads) {
         const uint32_t s = e / (kRBytes / 16), o = e % (kRBytes / 16);
         *reinterpret_cast<uint4*>(sm + kOffStages + s * kStageBytes + 2 * kTileBytes + 16 * o) =
             make_uint4(0u, 0u, 0u, 0u);
+        if (kBf16)
+            *reinterpret_cast<uint4*>(sm + kOffStages + s * kStageBytes + kTileBytes + 16 * o) =
+                make_uint4(0u, 0u, 0u, 0u);
     }
     // every precision buffer starts from the prior precision
     for (int b = 0; b < kNChol; ++b)
@@ -366,6 +371,7 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
         if (warp == 0) {
             // ======================= MMA issuer =======================
             if (lane == 0) {
+                constexpr uint32_t idesc = kBf16 ? kIdescBf16 : kIdesc;
                 uint32_t g = 0, u = 0;  // stages consumed, accumulation chunks issued
                 bool ok = true;
                 for (int64_t j = 0; j < nj && ok; ++j) {
@@ -402,7 +408,7 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
                                 // (16 x 128 B rows) per k-block
                                 const uint64_t desc = sdesc(sH + kb * 2048, kTileBytes, 1024, 2);
                                 const uint32_t acc = (base > c0 || kb > 0) ? 1u : 0u;
-                                tc_mma(dgram, desc, desc, kIdesc, acc);
+                                tc_mma(dgram, desc, desc, idesc, acc);
                             }
                             tc_commit(bar_stage_empty + 8 * s);
                         }
@@ -484,31 +490,56 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
                     }
                     const int cnt = (int)min((int64_t)kStageRatings, p1 - base);
                     // this thread's copies: id = gt + 64 k -> rating id / 16, 16-B chunk id % 16
+                    // this thread's rows (-1 past the row's end), read before the slot is
+                    // released: FP16 split, rating (gt >> 4) + 4k, 16-B chunk gt & 15 of its
+                    // h and l rows; BF16, rating (gt >> 3) + 8k, chunk gt & 7 of its h row
                     int cols[16];
+                    if constexpr (!kBf16) {
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        const int qq = (gt >> 4) + 4 * k;
-                        cols[k] = qq < cnt ? idx_ring[is * 128 + qq] : -1;
+                        for (int k = 0; k < 16; ++k) {
+                            const int qq = (gt >> 4) + 4 * k;
+                            cols[k] = qq < cnt ? idx_ring[is * 128 + qq] : -1;
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int qq = (gt >> 3) + 8 * k;
+                            cols[k] = qq < cnt ? idx_ring[is * 128 + qq] : -1;
+                        }
                     }
                     const float rv = gt < cnt ? val_ring[is * 128 + gt] : 0.f;
                     mbar_arrive(bar_idx_empty + 8 * is);
                     const uint32_t sH = sbase + kOffStages + s * kStageBytes;
                     const uint32_t sL = sH + kTileBytes;
                     const uint32_t sR = sL + kTileBytes;
-                    const int c = gt & 15, ch = c & 7;
-                    const __half* Ysrc = (c >> 3) ? a.Yl : a.Yh;
-                    const uint32_t tile = (c >> 3) ? sL : sH;
+                    if constexpr (!kBf16) {
+                        const int c = gt & 15, ch = c & 7;
+                        const __half* Ysrc = (c >> 3) ? a.Yl : a.Yh;
+                        const uint32_t tile = (c >> 3) ? sL : sH;
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        const int qq = (gt >> 4) + 4 * k;
-                        const uint32_t dst = tile + qq * 128 + ((ch ^ (qq & 7)) << 4);
-                        if (cols[k] >= 0)
-                            cp_async16(dst, Ysrc + (int64_t)cols[k] * kKT + ch * 8, 16);
-                        else
-                            cp_async16(dst, a.Yh, 0);  // zero fill past the row's end
+                        for (int k = 0; k < 16; ++k) {
+                            const int qq = (gt >> 4) + 4 * k;
+                            const uint32_t dst = tile + qq * 128 + ((ch ^ (qq & 7)) << 4);
+                            if (cols[k] >= 0)
+                                cp_async16(dst, Ysrc + (int64_t)cols[k] * kKT + ch * 8, 16);
+                            else
+                                cp_async16(dst, a.Yh, 0);  // zero fill past the row's end
+                        }
+                    } else {
+                        // h rows only; the l atom stays zero
+                        const int ch = gt & 7;
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int qq = (gt >> 3) + 8 * k;
+                            const uint32_t dst = sH + qq * 128 + ((ch ^ (qq & 7)) << 4);
+                            if (cols[k] >= 0)
+                                cp_async16(dst, a.Yh + (int64_t)cols[k] * kKT + ch * 8, 16);
+                            else
+                                cp_async16(dst, a.Yh, 0);
+                        }
                     }
                     __half hi, lo;
-                    split_f16(rv, hi, lo);
+                    split16(rv, kBf16, hi, lo);
                     const uint32_t packed = (uint32_t)__half_as_ushort(hi) |
                                             ((uint32_t)__half_as_ushort(lo) << 16);
                     asm volatile("st.shared.b32 [%0], %1;" ::"r"(sR + gt * 128 + ((gt & 7) << 4)),
@@ -625,15 +656,15 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
     }
 }
 
-template <class Shape>
+template <class Shape, bool kBf16>
 cudaError_t launch_shape(const RowArgs& a, int num_sms, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(rows_tc_kernel<Shape>,
+    cudaError_t e = cudaFuncSetAttribute(rows_tc_kernel<Shape, kBf16>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Shape::kSmemBytes);
     if (e != cudaSuccess) return e;
     int64_t grid = a.nrows < num_sms ? a.nrows : num_sms;
-    rows_tc_kernel<Shape><<<(unsigned)grid, Shape::kThreads, Shape::kSmemBytes, s>>>(a);
+    rows_tc_kernel<Shape, kBf16><<<(unsigned)grid, Shape::kThreads, Shape::kSmemBytes, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -643,29 +674,33 @@ constexpr int64_t kLongRowShapeDegree = 1024;
 cudaError_t launch_rows_tc(const RowArgs& a, int64_t nratings, int num_sms, cudaStream_t s)
 {
     if (a.nrows <= 0) return cudaSuccess;
-    if (nratings >= kLongRowShapeDegree * a.nrows) return launch_shape<ShapeLongRows>(a, num_sms, s);
-    return launch_shape<ShapeShortRows>(a, num_sms, s);
+    const bool longrows = nratings >= kLongRowShapeDegree * a.nrows;
+    if (a.bf16)
+        return longrows ? launch_shape<ShapeLongRows, true>(a, num_sms, s)
+                        : launch_shape<ShapeShortRows, true>(a, num_sms, s);
+    return longrows ? launch_shape<ShapeLongRows, false>(a, num_sms, s)
+                    : launch_shape<ShapeShortRows, false>(a, num_sms, s);
 }
 
 __global__ void split_factors_kernel(const float* __restrict__ X, int64_t n, __half* __restrict__ Xh,
-                                     __half* __restrict__ Xl)
+                                     __half* __restrict__ Xl, int bf16)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
         __half h, l;
-        split_f16(X[e], h, l);
+        split16(X[e], bf16 != 0, h, l);
         Xh[e] = h;
         Xl[e] = l;
     }
 }
 
 cudaError_t launch_split_factors(const float* X, int64_t rows, int ld, __half* Xh, __half* Xl,
-                                 cudaStream_t s)
+                                 int bf16, cudaStream_t s)
 {
     const int64_t n = rows * ld;
     if (n <= 0) return cudaSuccess;
     const int64_t want = (n + 255) / 256;
-    split_factors_kernel<<<(int)(want < 8192 ? want : 8192), 256, 0, s>>>(X, n, Xh, Xl);
+    split_factors_kernel<<<(int)(want < 8192 ? want : 8192), 256, 0, s>>>(X, n, Xh, Xl, bf16);
     return cudaGetLastError();
 }
 

@@ -7,6 +7,7 @@
 // 65 lower-triangle entries per lane at KT = 64.  On return the lane holds its
 // entries of x = L^{-T}(L^{-1} b + z) (and of the mean L^{-T} L^{-1} b).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -22,6 +23,19 @@ __device__ __forceinline__ void split_f16(float x, __half& hi, __half& lo)
 {
     hi = __float2half_rn(x);
     lo = __float2half_rn(x - __half2float(hi));
+}
+
+// The 16-bit copies of a factor entry the tensor-core kernel gathers: the FP16 split
+// (hi, lo), or with bf16 set the BF16 rounding of x (hi) and of the remainder (lo).
+__device__ __forceinline__ void split16(float x, bool bf16, __half& hi, __half& lo)
+{
+    if (bf16) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        hi = __ushort_as_half(__bfloat16_as_ushort(h));
+        lo = __ushort_as_half(__bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h))));
+    } else {
+        split_f16(x, hi, lo);
+    }
 }
 
 template <int KT>
@@ -359,11 +373,11 @@ __device__ __forceinline__ void store_row_panels(const RowArgs& a, int row, int 
     if (v2) a.X[off + r2] = x2;
     if (a.Xh) {
         __half h, l;
-        split_f16(x1, h, l);
+        split16(x1, a.bf16, h, l);
         a.Xh[off + r1] = h;
         a.Xl[off + r1] = l;
         if (v2) {
-            split_f16(x2, h, l);
+            split16(x2, a.bf16, h, l);
             a.Xh[off + r2] = h;
             a.Xl[off + r2] = l;
         }
@@ -391,12 +405,12 @@ __device__ __forceinline__ void store_row(const RowArgs& a, int row, int lane, f
     if (a.Xh) {
         __half h, l;
         if (v1) {
-            split_f16(x1, h, l);
+            split16(x1, a.bf16, h, l);
             a.Xh[off + i1] = h;
             a.Xl[off + i1] = l;
         }
         if (v2) {
-            split_f16(x2, h, l);
+            split16(x2, a.bf16, h, l);
             a.Xh[off + i2] = h;
             a.Xl[off + i2] = l;
         }

@@ -50,6 +50,30 @@ def test_long_row_shape_parity(bp):
     assert_worst(step_parity(bp, prob, sweeps=2))
 
 
+# BF16 Gram: the other side's rows enter the MMA rounded to 8 significant bits
+# (relative error <= 2^-9 per entry), so each Gram entry carries up to ~2^-8 relative
+# error; through the K = 64 solve this stays below 2e-2 of the row's norm for the
+# prior-dominated to data-dominated rows here (measured worst is printed).
+BF16_ROW_TOL = 2e-2
+
+
+def test_bf16_gram_parity(bp):
+    prob = workloads.random_small(600, 300, 64, 60000, seed=264, n_test=400, long_rows=6,
+                                  long_deg=290)
+    w = step_parity(bp, prob, flags=bp.BPMF_BF16_GRAM, sweeps=2)
+    print("bf16 worst:", {k: "%.2e" % v for k, v in w.items()})
+    assert w["stats"] <= 1e-5 and w["hyper"] <= 1e-9 and w["rmse"] <= 1e-5, w
+    assert w["x"] <= BF16_ROW_TOL and w["mean"] <= BF16_ROW_TOL, w
+    assert w["x"] > 1e-5  # the BF16 path really ran (FP32-class errors would be ~1e-6)
+
+
+def test_bf16_gram_rejected_without_tensor_cores(bp):
+    prob = workloads.random_small(100, 60, 32, 2000, seed=3)
+    with pytest.raises(bp.BpmfError) as ei:
+        bp.create_from_problem(prob, flags=bp.BPMF_BF16_GRAM)
+    assert ei.value.code == bp.BPMF_EINVAL
+
+
 def test_tensor_core_and_cuda_core_paths_agree(bp):
     prob = workloads.random_small(500, 260, 64, 30000, seed=77, n_test=100)
     K = prob.K
