@@ -50,11 +50,10 @@ def test_long_row_shape_parity(bp):
     assert_worst(step_parity(bp, prob, sweeps=2))
 
 
-# BF16 Gram: the other side's rows enter the MMA rounded to 8 significant bits
-# (relative error <= 2^-9 per entry), so each Gram entry carries up to ~2^-8 relative
-# error; through the K = 64 solve this stays below 2e-2 of the row's norm for the
-# prior-dominated to data-dominated rows here (measured worst is printed).
-BF16_ROW_TOL = 2e-2
+# BF16 Gram: per-row means and samples within 1e-2 relative of the FP64 oracle (the
+# rows enter the MMA rounded to 8 significant bits, 2^-9 relative per entry; the
+# measured worst is printed).
+BF16_ROW_TOL = 1e-2
 
 
 def test_bf16_gram_parity(bp):
