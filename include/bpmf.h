@@ -119,13 +119,27 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
 
 /*
  * Run n_sweeps full Gibbs sweeps (Alg. 1): hyper(V), movies, hyper(U), users,
- * predict (order 0; order 1 swaps the sides).  If either RMSE pointer is
- * non-NULL, the call waits for the sweeps and writes the RMSE of the last
- * sweep's sample and of the running-average prediction (NaN before burn-in;
- * both NaN when T = 0).  Host pointers.  A sticky device error from any
+ * predict (order 0; order 1 swaps the sides).  Each hyper step runs on a second
+ * stream of the handle beside the other side's row update (each depends only on
+ * its own side's factors), and sweeps after the first replay a CUDA graph of the
+ * launches when the handle's stream can be captured (not the legacy default
+ * stream); results are bit-identical to running the phases one by one.  If either
+ * RMSE pointer is non-NULL, the call waits for the sweeps and writes the RMSE of
+ * the last sweep's sample and of the running-average prediction (NaN before
+ * burn-in; both NaN when T = 0).  Host pointers.  A sticky device error from any
  * kernel is returned as its code.
  */
 int bpmf_sweep(bpmf_handle h, int32_t n_sweeps, double* rmse_sample, double* rmse_avg);
+
+/*
+ * n_sweeps sweeps of each of n independent chains, issued sweep by sweep and
+ * chain by chain, so chains created on different streams run concurrently on the
+ * device (small jobs do not fill the GPU alone).  hs: host array of n handles,
+ * borrowed.  Each chain's result equals bpmf_sweep(hs[k], n_sweeps) alone.  Does
+ * not wait; read RMSEs with bpmf_sweep(h, 0, ...).  BPMF_EINVAL for a NULL handle
+ * or negative counts; the first launch error stops the batch.
+ */
+int bpmf_sweep_batch(bpmf_handle* hs, int32_t n, int32_t n_sweeps);
 
 /* Run one BPMF_PHASE_* step of a sweep (for checking the steps one by one). */
 int bpmf_step(bpmf_handle h, int32_t phase);

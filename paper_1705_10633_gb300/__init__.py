@@ -71,6 +71,7 @@ def lib():
     L.bpmf_create.argtypes = [P(vp), i64, i64, i32, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp,
                               P(bpmf_params), vp]
     L.bpmf_sweep.argtypes = [vp, i32, P(C.c_double), P(C.c_double)]
+    L.bpmf_sweep_batch.argtypes = [P(vp), i32, i32]
     L.bpmf_step.argtypes = [vp, i32]
     L.bpmf_predict.argtypes = [vp, i64, vp, vp, vp, i32]
     L.bpmf_get_state.argtypes = [vp, vp, vp, vp, P(C.c_uint64)]
@@ -185,6 +186,14 @@ def bpmf_sweep(h, n_sweeps=1, want_rmse=True):
     return None
 
 
+def bpmf_sweep_batch(handles, n_sweeps=1):
+    """n_sweeps sweeps of every chain in `handles`, interleaved (chains on different
+    streams run concurrently).  Does not wait."""
+    arr = (C.c_void_p * len(handles))(*[int(h) if not isinstance(h, C.c_void_p) else h.value
+                                         for h in handles])
+    _check(lib().bpmf_sweep_batch(arr, len(handles), int(n_sweeps)), "bpmf_sweep_batch")
+
+
 def bpmf_step(h, phase):
     _check(lib().bpmf_step(h, int(phase)), "bpmf_step")
 
@@ -285,7 +294,8 @@ def create_from_problem(prob, flags=0, seed=None, burn_in=None, params=None, str
                        stream=stream)
 
 
-EXPORTED = ["bpmf_default_params", "bpmf_create", "bpmf_sweep", "bpmf_step", "bpmf_predict",
+EXPORTED = ["bpmf_default_params", "bpmf_create", "bpmf_sweep", "bpmf_sweep_batch", "bpmf_step",
+            "bpmf_predict",
             "bpmf_get_state", "bpmf_set_state", "bpmf_get_accum", "bpmf_set_accum",
             "bpmf_get_stats", "bpmf_debug_means", "bpmf_status", "bpmf_info", "bpmf_launch_count",
             "bpmf_row_stats_noalloc",

@@ -54,6 +54,11 @@ struct bpmf_ctx {
     cudaStream_t stream = nullptr;
     cudaStream_t aux = nullptr;  // hyper steps overlapped with row phases
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // the steady-state overlapped sweep as a CUDA graph (0: not tried, 1: ready,
+    // -1: the stream cannot be captured)
+    int graph_state = 0;
+    cudaGraphExec_t sweep_graph = nullptr;
+    int64_t graph_launches = 0;
     int64_t M = 0, N = 0, nnz = 0, T = 0;
     int K = 0, kp = 0;
     bool tc = false;  // long rows on the tensor-core kernel
@@ -375,6 +380,7 @@ int bpmf_destroy(bpmf_handle h)
         cudaStreamSynchronize(h->aux);
         cudaStreamDestroy(h->aux);
     }
+    if (h->sweep_graph) cudaGraphExecDestroy(h->sweep_graph);
     for (cudaEvent_t e : h->ev)
         if (e) cudaEventDestroy(e);
     for (void* ptr : h->allocs) {
@@ -563,43 +569,127 @@ int bpmf_step(bpmf_handle h, int32_t phase)
 
 namespace {
 
-// n sweeps with each hyper step on the aux stream, overlapped with a row phase
+// Overlapped sweeps: each hyper step runs on the aux stream beside a row phase
 // (Alg. 1's data dependencies: the second side's hyper step needs that side's rows
 // of the previous sweep only, the first side's needs this sweep's first-side rows):
 //   main: [hyper(1st) s0] | rows(1st) | wait H2 | rows(2nd) | predict | wait H1 | advance
 //   aux:    wait A: hyper(2nd) s -> H2 | wait R1: hyper(1st) s+1 -> H1
 // The row kernels leave one SM to the aux stream.  advance waits for the aux stream, so
 // the device sweep counter never moves under a hyper step.
-int sweep_overlapped(bpmf_ctx* h, int n_sweeps, int first)
+
+// Start: the first side's hyper step of the first sweep, row kernels on one SM fewer.
+int sweep_begin(bpmf_ctx* h, int first)
+{
+    const int rc = phase_hyper(h, first, h->stream, 0);
+    h->row_sms = h->num_sms - 1;
+    return rc;
+}
+
+void sweep_end(bpmf_ctx* h) { h->row_sms = h->num_sms; }
+
+// One sweep; with next_hyper, also the following sweep's first-side hyper step.
+int sweep_body(bpmf_ctx* h, int first, bool next_hyper)
 {
     const int second = 1 - first;
     const int rowp[2] = {BPMF_PHASE_ROWS_USER, BPMF_PHASE_ROWS_MOVIE};
     cudaEvent_t evA = h->ev[0], evR1 = h->ev[1], evH2 = h->ev[2], evH1 = h->ev[3];
-    int rc = phase_hyper(h, first, h->stream, 0);
-    h->row_sms = h->num_sms - 1;
-    for (int it = 0; it < n_sweeps && rc == BPMF_OK; ++it) {
-        const bool last = it + 1 == n_sweeps;
-        cudaError_t e = cudaEventRecord(evA, h->stream);
-        if (e == cudaSuccess) rc = run_phase(h, rowp[first]);
-        if (e == cudaSuccess && rc == BPMF_OK) e = cudaEventRecord(evR1, h->stream);
-        if (e == cudaSuccess && rc == BPMF_OK) e = cudaStreamWaitEvent(h->aux, evA, 0);
-        if (e == cudaSuccess && rc == BPMF_OK) rc = phase_hyper(h, second, h->aux, 0);
-        if (e == cudaSuccess && rc == BPMF_OK) e = cudaEventRecord(evH2, h->aux);
-        if (e == cudaSuccess && rc == BPMF_OK && !last) {
-            e = cudaStreamWaitEvent(h->aux, evR1, 0);
-            if (e == cudaSuccess) rc = phase_hyper(h, first, h->aux, 1);
-            if (e == cudaSuccess && rc == BPMF_OK) e = cudaEventRecord(evH1, h->aux);
-        }
-        if (e == cudaSuccess && rc == BPMF_OK) e = cudaStreamWaitEvent(h->stream, evH2, 0);
-        if (e == cudaSuccess && rc == BPMF_OK) rc = run_phase(h, rowp[second]);
-        if (e == cudaSuccess && rc == BPMF_OK) rc = run_phase(h, BPMF_PHASE_PREDICT);
-        if (e == cudaSuccess && rc == BPMF_OK && !last) e = cudaStreamWaitEvent(h->stream, evH1, 0);
-        if (e == cudaSuccess && rc == BPMF_OK) rc = run_phase(h, BPMF_PHASE_ADVANCE);
-        if (e != cudaSuccess) rc = BPMF_ECUDA;
+    int rc = BPMF_OK;
+    cudaError_t e = cudaEventRecord(evA, h->stream);
+    if (e == cudaSuccess) rc = run_phase(h, rowp[first]);
+    if (e == cudaSuccess && rc == BPMF_OK) e = cudaEventRecord(evR1, h->stream);
+    if (e == cudaSuccess && rc == BPMF_OK) e = cudaStreamWaitEvent(h->aux, evA, 0);
+    if (e == cudaSuccess && rc == BPMF_OK) rc = phase_hyper(h, second, h->aux, 0);
+    if (e == cudaSuccess && rc == BPMF_OK) e = cudaEventRecord(evH2, h->aux);
+    if (e == cudaSuccess && rc == BPMF_OK && next_hyper) {
+        e = cudaStreamWaitEvent(h->aux, evR1, 0);
+        if (e == cudaSuccess) rc = phase_hyper(h, first, h->aux, 1);
+        if (e == cudaSuccess && rc == BPMF_OK) e = cudaEventRecord(evH1, h->aux);
     }
-    h->row_sms = h->num_sms;
-    // the main stream has waited for everything the aux stream was given
-    return rc;
+    if (e == cudaSuccess && rc == BPMF_OK) e = cudaStreamWaitEvent(h->stream, evH2, 0);
+    if (e == cudaSuccess && rc == BPMF_OK) rc = run_phase(h, rowp[second]);
+    if (e == cudaSuccess && rc == BPMF_OK) rc = run_phase(h, BPMF_PHASE_PREDICT);
+    if (e == cudaSuccess && rc == BPMF_OK && next_hyper) e = cudaStreamWaitEvent(h->stream, evH1, 0);
+    if (e == cudaSuccess && rc == BPMF_OK) rc = run_phase(h, BPMF_PHASE_ADVANCE);
+    if (e != cudaSuccess) rc = BPMF_ECUDA;
+    return rc;  // the main stream has waited for everything the aux stream was given
+}
+
+// The sweep that is followed by another, captured once per handle into a CUDA graph
+// (kernel arguments are fixed per handle; counters are read from device memory).
+// Returns false when the stream cannot be captured (the legacy default stream).
+bool ensure_sweep_graph(bpmf_ctx* h, int first)
+{
+    if (h->graph_state != 0) return h->graph_state > 0;
+    h->graph_state = -1;
+    if (!h->stream) return false;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int64_t l0 = h->launches;
+    const int rc = sweep_body(h, first, true);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    const int64_t captured = h->launches - l0;
+    h->launches = l0;
+    if (rc != BPMF_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return false;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&h->sweep_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        h->sweep_graph = nullptr;
+        return false;
+    }
+    h->graph_launches = captured;
+    h->graph_state = 1;
+    return true;
+}
+
+// One sweep of a run that began with sweep_begin; the last one leaves the next
+// sweep's hyper step undrawn, so the state after a run is the phase-by-phase one.
+int sweep_next(bpmf_ctx* h, int first, bool last)
+{
+    if (!last && ensure_sweep_graph(h, first)) {
+        h->launches += h->graph_launches;
+        return cuda_rc(cudaGraphLaunch(h->sweep_graph, h->stream));
+    }
+    return sweep_body(h, first, !last);
+}
+
+int sweep_plain(bpmf_ctx* h, int n_sweeps)
+{
+    const int first = h->p.order == 0 ? BPMF_MOVIE : BPMF_USER;
+    const int second = 1 - first;
+    const int hyp[2] = {BPMF_PHASE_HYPER_USER, BPMF_PHASE_HYPER_MOVIE};
+    const int rowp[2] = {BPMF_PHASE_ROWS_USER, BPMF_PHASE_ROWS_MOVIE};
+    for (int it = 0; it < n_sweeps; ++it) {
+        const int seq[6] = {hyp[first], rowp[first], hyp[second], rowp[second], BPMF_PHASE_PREDICT,
+                            BPMF_PHASE_ADVANCE};
+        for (int ph : seq) {
+            const int rc = run_phase(h, ph);
+            if (rc) return rc;
+        }
+    }
+    return BPMF_OK;
+}
+
+int read_rmse(bpmf_ctx* h, double* rmse_sample, double* rmse_avg)
+{
+    Control c;
+    cudaError_t e = cudaMemcpyAsync(&c, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return BPMF_ECUDA;
+    if (rmse_sample) *rmse_sample = c.rmse_sample;
+    if (rmse_avg) *rmse_avg = c.rmse_avg;
+    if (c.status & kStatusNotPD) return BPMF_ENOTPD;
+    if (c.status & kStatusNaN) return BPMF_ENAN;
+    if (c.status & kStatusGamma) return BPMF_EGAMMA;
+    if (c.status & kStatusTimeout) return BPMF_ETIMEOUT;
+    return BPMF_OK;
 }
 
 }  // namespace
@@ -607,36 +697,47 @@ int sweep_overlapped(bpmf_ctx* h, int n_sweeps, int first)
 int bpmf_sweep(bpmf_handle h, int32_t n_sweeps, double* rmse_sample, double* rmse_avg)
 {
     if (!h || n_sweeps < 0) return BPMF_EINVAL;
-    const int first = h->p.order == 0 ? BPMF_MOVIE : BPMF_USER;
-    const int second = 1 - first;
-    const int hyp[2] = {BPMF_PHASE_HYPER_USER, BPMF_PHASE_HYPER_MOVIE};
-    const int rowp[2] = {BPMF_PHASE_ROWS_USER, BPMF_PHASE_ROWS_MOVIE};
     if (n_sweeps > 0 && h->num_sms >= 8) {
-        const int rc = sweep_overlapped(h, n_sweeps, first);
+        const int first = h->p.order == 0 ? BPMF_MOVIE : BPMF_USER;
+        int rc = sweep_begin(h, first);
+        for (int it = 0; it < n_sweeps && rc == BPMF_OK; ++it) rc = sweep_next(h, first, it + 1 == n_sweeps);
+        sweep_end(h);
         if (rc) return rc;
     } else {
-        for (int it = 0; it < n_sweeps; ++it) {
-            const int seq[6] = {hyp[first], rowp[first], hyp[second], rowp[second],
-                                BPMF_PHASE_PREDICT, BPMF_PHASE_ADVANCE};
-            for (int ph : seq) {
-                const int rc = run_phase(h, ph);
-                if (rc) return rc;
-            }
+        const int rc = sweep_plain(h, n_sweeps);
+        if (rc) return rc;
+    }
+    if (rmse_sample || rmse_avg) return read_rmse(h, rmse_sample, rmse_avg);
+    return BPMF_OK;
+}
+
+int bpmf_sweep_batch(bpmf_handle* hs, int32_t n, int32_t n_sweeps)
+{
+    if (n < 0 || n_sweeps < 0 || (n > 0 && !hs)) return BPMF_EINVAL;
+    for (int32_t k = 0; k < n; ++k)
+        if (!hs[k]) return BPMF_EINVAL;
+    int rc = BPMF_OK;
+    std::vector<char> overlapped((size_t)n, 0);
+    for (int32_t k = 0; k < n && rc == BPMF_OK; ++k) {
+        bpmf_ctx* h = hs[k];
+        if (n_sweeps > 0 && h->num_sms >= 8) {
+            rc = sweep_begin(h, h->p.order == 0 ? BPMF_MOVIE : BPMF_USER);
+            overlapped[(size_t)k] = 1;
         }
     }
-    if (rmse_sample || rmse_avg) {
-        Control c;
-        cudaError_t e = cudaMemcpyAsync(&c, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) return BPMF_ECUDA;
-        if (rmse_sample) *rmse_sample = c.rmse_sample;
-        if (rmse_avg) *rmse_avg = c.rmse_avg;
-        if (c.status & kStatusNotPD) return BPMF_ENOTPD;
-        if (c.status & kStatusNaN) return BPMF_ENAN;
-        if (c.status & kStatusGamma) return BPMF_EGAMMA;
-        if (c.status & kStatusTimeout) return BPMF_ETIMEOUT;
-    }
-    return BPMF_OK;
+    // sweep by sweep, job by job: each job's launches go to its own streams, so
+    // independent jobs overlap on the device
+    for (int32_t it = 0; it < n_sweeps && rc == BPMF_OK; ++it)
+        for (int32_t k = 0; k < n && rc == BPMF_OK; ++k) {
+            bpmf_ctx* h = hs[k];
+            if (overlapped[(size_t)k])
+                rc = sweep_next(h, h->p.order == 0 ? BPMF_MOVIE : BPMF_USER, it + 1 == n_sweeps);
+            else
+                rc = sweep_plain(h, 1);
+        }
+    for (int32_t k = 0; k < n; ++k)
+        if (overlapped[(size_t)k]) sweep_end(hs[k]);
+    return rc;
 }
 
 int bpmf_predict(bpmf_handle h, int64_t n, const int32_t* i, const int32_t* j, float* out,

@@ -133,12 +133,16 @@ def test_three_sweeps_config1(bp):
 
 @pytest.mark.parametrize("K,order", [(8, 0), (64, 0), (64, 1)])
 def test_sweep_entry_point_matches_phases(bp, K, order):
-    """bpmf_sweep overlaps each hyper step with a row phase on a second stream and runs
-    the row kernels on one SM fewer; the chain must equal phase-by-phase stepping bit
-    for bit (both sweep orders, CUDA-core and tensor-core row kernels)."""
+    """bpmf_sweep overlaps each hyper step with a row phase on a second stream, runs
+    the row kernels on one SM fewer and replays a CUDA graph after the first sweep; the
+    chain must equal phase-by-phase stepping bit for bit (both sweep orders, CUDA-core
+    and tensor-core row kernels)."""
+    import torch
     prob = workloads.random_small(150, 70, K, 1500 if K == 8 else 6000, seed=9, n_test=60)
-    a = bp.create_from_problem(prob, order=order, stream=bp.torch_stream())
-    b = bp.create_from_problem(prob, order=order, stream=bp.torch_stream())
+    # a stream of its own: the sweeps after the first replay a captured CUDA graph
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    a = bp.create_from_problem(prob, order=order, stream=sa.cuda_stream)
+    b = bp.create_from_problem(prob, order=order, stream=sb.cuda_stream)
     try:
         if K == 64:
             assert bp.bpmf_info(a, 0)["n_long"] > 0
