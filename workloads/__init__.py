@@ -304,6 +304,23 @@ def random_small(M, N, K, nnz, seed, n_test=0, empty_rows=0, empty_cols=0, alpha
                      alpha=alpha, seed=seed, burn_in=0, sweeps=4, noise_sd=0.3)
 
 
+def config4(seed: int = 3, n_jobs: int = 256) -> list:
+    """Many independent small jobs (batched form): per job M log-uniform in
+    [1,000, 100,000], N log-uniform in [500, 10,000], density log-uniform in
+    [0.1%, 2%], K drawn from {16, 32, 64}, planted Gaussian ratings (noise sd 0.3),
+    1% of the ratings' count as test points.  Job j is seeded with 1000 seed + j."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for j in range(n_jobs):
+        M = int(round(np.exp(rng.uniform(np.log(1e3), np.log(1e5)))))
+        N = int(round(np.exp(rng.uniform(np.log(500.0), np.log(1e4)))))
+        dens = float(np.exp(rng.uniform(np.log(1e-3), np.log(2e-2))))
+        K = int(rng.choice([16, 32, 64]))
+        nnz = max(1, int(dens * M * N))
+        jobs.append(random_small(M, N, K, nnz, seed=1000 * seed + j, n_test=max(1, nnz // 100)))
+    return jobs
+
+
 def subsample_rows(prob: Problem, n_rows: int, seed: int = 123) -> Problem:
     """Stand-alone problem made of `n_rows` rows chosen by a seeded permutation.
 
