@@ -482,15 +482,82 @@ def run_batched(args):
     print(json.dumps(out), flush=True)
 
 
+def run_serving(args):
+    """Serving loop (continuous batching): jobs arrive as a Poisson process (rate
+    args.rate per second for args.duration seconds), each drawn from a pool of
+    config-4-sized problems with its own chain seed, asking for args.job_sweeps sweeps
+    and predictions at 1,000 query points.  The same arrival sequence is served with
+    up to args.slots jobs resident and with one job at a time.  Prints one JSON line
+    (latency percentiles, aggregate rows/s) for each form side by side."""
+    import torch
+
+    import workloads
+    from paper_1705_10633_gb300.serve import Job, Server, latency_percentiles
+
+    torch.cuda.set_device(0)
+    pool = workloads.config4(seed=5, n_jobs=args.jobs)
+    rng = np.random.default_rng(17)
+    t, arrivals = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / args.rate)
+        if t > args.duration:
+            break
+        prob = pool[int(rng.integers(len(pool)))]
+        qi = rng.integers(0, prob.M, 1000).astype(np.int32)
+        qj = rng.integers(0, prob.N, 1000).astype(np.int32)
+        arrivals.append((t, prob, qi, qj, int(rng.integers(1 << 30))))
+
+    def serve(slots):
+        srv = Server(memory_limit=150e9, max_active=slots, sweeps_per_round=5)
+        futs, t0 = [], time.perf_counter()
+        for at, prob, qi, qj, seed in arrivals:
+            delay = t0 + at - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            futs.append(srv.submit(Job(problem=prob, sweeps=args.job_sweeps, query_i=qi,
+                                       query_j=qj, seed=seed)))
+        res = [f.result() for f in futs]
+        srv.close()
+        span = max(r.finished_at for r in res) - min(r.submitted_at for r in res)
+        rows = sum((a[1].M + a[1].N) * args.job_sweeps for a in arrivals)
+        lat = latency_percentiles(res)
+        return {"p50_s": round(lat["p50"], 4), "p99_s": round(lat["p99"], 4),
+                "rows_per_s": round(rows / span, 1), "jobs_per_s": round(len(res) / span, 2),
+                "makespan_s": round(span, 3), "rounds": srv.rounds,
+                "peak_memory_gb": round(srv.peak_memory / 1e9, 3)}, res
+
+    batched, rb = serve(args.slots)
+    alone, ra = serve(1)
+    same = all(np.array_equal(x.predictions, y.predictions) for x, y in zip(rb, ra))
+    out = {"metric": "serving job latency p50/p99 (s) and aggregate rows/s",
+           "value": batched["p99_s"], "unit": "s (p99 job latency)", "n_gpus": 1,
+           "higher_is_better": False, "data": "synthetic",
+           "config": {"workload": "config5_poisson", "rate_jobs_per_s": args.rate,
+                      "duration_s": args.duration, "jobs": len(arrivals),
+                      "sweeps_per_job": args.job_sweeps, "queries_per_job": 1000,
+                      "pool": "%d config-4-sized problems" % len(pool), "slots": args.slots,
+                      "sweeps_per_round": 5, "memory_budget_gb": 150},
+           "batched": batched, "one_at_a_time": alone,
+           "p99_ratio_alone_over_batched": round(alone["p99_s"] / batched["p99_s"], 3),
+           "rows_per_s_ratio": round(batched["rows_per_s"] / alone["rows_per_s"], 3),
+           "same_predictions_alone_and_in_mix": same}
+    print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--config", type=int, choices=[1, 2, 3, 4], default=3,
-                    help="4: batched independent jobs (bpmf_sweep_batch against one at a time)")
-    ap.add_argument("--jobs", type=int, default=256, help="jobs of config 4")
+    ap.add_argument("--config", type=int, choices=[1, 2, 3, 4, 5], default=3,
+                    help="4: batched independent jobs (bpmf_sweep_batch against one at a time); "
+                         "5: serving loop with Poisson arrivals")
+    ap.add_argument("--jobs", type=int, default=256, help="jobs of config 4 (pool size for 5)")
+    ap.add_argument("--rate", type=float, default=50.0, help="config 5: arrivals per second")
+    ap.add_argument("--duration", type=float, default=4.0, help="config 5: arrival window (s)")
+    ap.add_argument("--job-sweeps", type=int, default=100, help="config 5: sweeps per job")
+    ap.add_argument("--slots", type=int, default=64, help="config 5: jobs resident at once")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--bf16", action="store_true",
                     help="BF16-input tensor-core Gram (lower precision; not the headline)")
@@ -501,14 +568,16 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference" and args.config == 4:
+    if args.impl == "reference" and args.config in (4, 5):
         print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the "
-                          "single-job configs 1-3; config 4 compares batched and one-at-a-time "
-                          "forms of this library"}), flush=True)
+                          "single-job configs 1-3; configs 4 and 5 compare batched and "
+                          "one-at-a-time forms of this library"}), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     elif args.config == 4:
         run_batched(args)
+    elif args.config == 5:
+        run_serving(args)
     else:
         run_native(args)
 
