@@ -89,6 +89,9 @@ typedef struct {
     int32_t long_min_degree; /* rows with at least this many ratings use the tensor-core
                                 kernel (K in 49..64); <= 0 = library default (1)       */
     int32_t wait_timeout_ms; /* limit of every device-side wait, <= 0 = 2000 ms         */
+    int32_t long_shape_degree; /* tensor-core launches whose rows average at least this
+                                  many ratings use the CTA shape with more gather stages
+                                  and fewer factorisation warps; <= 0 = default (1024)  */
     bpmf_alloc_fn alloc; /* NULL = cudaMalloc / cudaFree */
     bpmf_free_fn free;
     void* alloc_ctx;
@@ -140,6 +143,16 @@ int bpmf_sweep(bpmf_handle h, int32_t n_sweeps, double* rmse_sample, double* rms
  * or negative counts; the first launch error stops the batch.
  */
 int bpmf_sweep_batch(bpmf_handle* hs, int32_t n, int32_t n_sweeps);
+
+/*
+ * Change the two tuning thresholds of a live handle (long_min_degree and
+ * long_shape_degree of bpmf_params; <= 0 = library default): the rows of both
+ * sides are binned again (host sort of the degrees kept from bpmf_create, one
+ * host-to-device copy per side, waited for).  The chain state is untouched; rows
+ * may move between the CUDA-core and tensor-core kernels, whose results agree
+ * within the FP32 tolerance, not bit for bit.  For autotuning.
+ */
+int bpmf_set_tuning(bpmf_handle h, int32_t long_min_degree, int32_t long_shape_degree);
 
 /* Run one BPMF_PHASE_* step of a sweep (for checking the steps one by one). */
 int bpmf_step(bpmf_handle h, int32_t phase);

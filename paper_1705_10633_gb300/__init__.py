@@ -43,7 +43,7 @@ class bpmf_params(C.Structure):
                 ("seed", C.c_uint64), ("job_id", C.c_uint32), ("burn_in", C.c_int32),
                 ("order", C.c_int32), ("flags", C.c_uint32), ("clip_lo", C.c_double),
                 ("clip_hi", C.c_double), ("long_min_degree", C.c_int32),
-                ("wait_timeout_ms", C.c_int32),
+                ("wait_timeout_ms", C.c_int32), ("long_shape_degree", C.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
@@ -73,6 +73,7 @@ def lib():
     L.bpmf_sweep.argtypes = [vp, i32, P(C.c_double), P(C.c_double)]
     L.bpmf_sweep_batch.argtypes = [P(vp), i32, i32]
     L.bpmf_step.argtypes = [vp, i32]
+    L.bpmf_set_tuning.argtypes = [vp, i32, i32]
     L.bpmf_predict.argtypes = [vp, i64, vp, vp, vp, i32]
     L.bpmf_get_state.argtypes = [vp, vp, vp, vp, P(C.c_uint64)]
     L.bpmf_set_state.argtypes = [vp, vp, vp, vp, C.c_uint64]
@@ -194,6 +195,12 @@ def bpmf_sweep_batch(handles, n_sweeps=1):
     _check(lib().bpmf_sweep_batch(arr, len(handles), int(n_sweeps)), "bpmf_sweep_batch")
 
 
+def bpmf_set_tuning(h, long_min_degree=0, long_shape_degree=0):
+    """Re-bin a live handle's rows under new thresholds (<= 0: library defaults)."""
+    _check(lib().bpmf_set_tuning(h, int(long_min_degree), int(long_shape_degree)),
+           "bpmf_set_tuning")
+
+
 def bpmf_step(h, phase):
     _check(lib().bpmf_step(h, int(phase)), "bpmf_step")
 
@@ -294,7 +301,8 @@ def create_from_problem(prob, flags=0, seed=None, burn_in=None, params=None, str
                        stream=stream)
 
 
-EXPORTED = ["bpmf_default_params", "bpmf_create", "bpmf_sweep", "bpmf_sweep_batch", "bpmf_step",
+EXPORTED = ["bpmf_default_params", "bpmf_create", "bpmf_sweep", "bpmf_sweep_batch",
+            "bpmf_set_tuning", "bpmf_step",
             "bpmf_predict",
             "bpmf_get_state", "bpmf_set_state", "bpmf_get_accum", "bpmf_set_accum",
             "bpmf_get_stats", "bpmf_debug_means", "bpmf_status", "bpmf_info", "bpmf_launch_count",

@@ -18,6 +18,7 @@ using namespace bpmf;
 namespace {
 
 constexpr int kDefaultLongMinDegree = 1;
+constexpr int kDefaultLongShapeDegree = 1024;
 constexpr int kDefaultWaitTimeoutMs = 2000;
 
 struct DevSide {
@@ -32,6 +33,7 @@ struct DevSide {
     int32_t* bin_rows = nullptr;  // short bin first, then long bin, each longest first
     int64_t n_short = 0, n_long = 0;
     int64_t long_ratings = 0;  // ratings of the long bin's rows
+    std::vector<int64_t> ptr_h;  // host copy of ptr, for binning again (bpmf_set_tuning)
     double* mu64 = nullptr;
     double* shift64 = nullptr;  // kp: shift of the hyper statistics
     double* lam64 = nullptr;
@@ -49,6 +51,8 @@ struct DevSide {
 struct bpmf_ctx {
     int device = 0;
     int num_sms = 1;
+    int64_t long_min = 1;            // binning threshold of the tensor-core kernel
+    int64_t long_shape_degree = 1024;  // mean degree that selects the many-stage CTA shape
     int row_sms = 1;  // CTAs of the row kernels: all SMs, or all but one while the
                       // next hyper step runs beside them (bpmf_sweep)
     cudaStream_t stream = nullptr;
@@ -299,7 +303,7 @@ int phase_rows(bpmf_ctx* h, int s)
     a.nrows = d.n_long;
     if (e == cudaSuccess && a.nrows > 0) {
         h->launches += 1;
-        e = launch_rows_tc(a, d.long_ratings, h->row_sms, h->stream);
+        e = launch_rows_tc(a, d.long_ratings, h->long_shape_degree, h->row_sms, h->stream);
     }
     return cuda_rc(e);
 }
@@ -475,6 +479,8 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
         csc_val = cv.data();
     }
     const int64_t long_min = prm.long_min_degree > 0 ? prm.long_min_degree : kDefaultLongMinDegree;
+    h->long_min = long_min;
+    h->long_shape_degree = prm.long_shape_degree > 0 ? prm.long_shape_degree : kDefaultLongShapeDegree;
     const int64_t* hp[2] = {csr_ptr, csc_ptr};
     const int32_t* hi[2] = {csr_col, csc_row};
     const float* hv[2] = {csr_val, csc_val};
@@ -507,6 +513,7 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
             break;
         }
         bin_rows(d.rows, hp[s], long_min, order, &d.n_short, &d.n_long, &d.long_ratings);
+        d.ptr_h.assign(hp[s], hp[s] + d.rows + 1);
         cudaError_t e = cudaMemcpyAsync(d.ptr, hp[s], sizeof(int64_t) * (d.rows + 1),
                                         cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess && h->nnz)
@@ -558,6 +565,27 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
         return rc;
     }
     *out = h;
+    return BPMF_OK;
+}
+
+int bpmf_set_tuning(bpmf_handle h, int32_t long_min_degree, int32_t long_shape_degree)
+{
+    if (!h) return BPMF_EINVAL;
+    h->long_min = long_min_degree > 0 ? long_min_degree : kDefaultLongMinDegree;
+    h->long_shape_degree = long_shape_degree > 0 ? long_shape_degree : kDefaultLongShapeDegree;
+    std::vector<int32_t> order;
+    for (int s = 0; s < 2; ++s) {
+        DevSide& d = h->side[s];
+        bin_rows(d.rows, d.ptr_h.data(), h->long_min, order, &d.n_short, &d.n_long, &d.long_ratings);
+        cudaError_t e = cudaMemcpyAsync(d.bin_rows, order.data(), sizeof(int32_t) * d.rows,
+                                        cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // `order` is reused
+        if (e != cudaSuccess) return BPMF_ECUDA;
+    }
+    // the captured sweep holds the old bins' launch shapes
+    if (h->sweep_graph) cudaGraphExecDestroy(h->sweep_graph);
+    h->sweep_graph = nullptr;
+    h->graph_state = 0;
     return BPMF_OK;
 }
 

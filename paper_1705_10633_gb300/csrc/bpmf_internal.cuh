@@ -103,8 +103,10 @@ cudaError_t launch_hyper_refresh(const double* mu64, const double* lam64, int K,
 // Row updates on CUDA cores: one warp per row (any degree).
 cudaError_t launch_rows_warp(const RowArgs& a, int kp, int num_sms, cudaStream_t s);
 // Row updates with the Gram on tensor cores (kp == 64, rows of the long bin).
-// nratings: ratings of the rows in a.rows (their mean degree picks the CTA shape).
-cudaError_t launch_rows_tc(const RowArgs& a, int64_t nratings, int num_sms, cudaStream_t s);
+// nratings: ratings of the rows in a.rows; rows averaging shape_degree ratings or more
+// take the CTA shape with more gather stages.
+cudaError_t launch_rows_tc(const RowArgs& a, int64_t nratings, int64_t shape_degree, int num_sms,
+                           cudaStream_t s);
 // FP16 hi/lo split of a factor matrix (after init or set_state).
 cudaError_t launch_split_factors(const float* X, int64_t rows, int ld, __half* Xh, __half* Xl,
                                  int bf16, cudaStream_t s);

@@ -668,13 +668,11 @@ cudaError_t launch_shape(const RowArgs& a, int num_sms, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Rows averaging this many ratings or more take the shape with more gather stages.
-constexpr int64_t kLongRowShapeDegree = 1024;
-
-cudaError_t launch_rows_tc(const RowArgs& a, int64_t nratings, int num_sms, cudaStream_t s)
+cudaError_t launch_rows_tc(const RowArgs& a, int64_t nratings, int64_t shape_degree, int num_sms,
+                           cudaStream_t s)
 {
     if (a.nrows <= 0) return cudaSuccess;
-    const bool longrows = nratings >= kLongRowShapeDegree * a.nrows;
+    const bool longrows = nratings >= shape_degree * a.nrows;
     if (a.bf16)
         return longrows ? launch_shape<ShapeLongRows, true>(a, num_sms, s)
                         : launch_shape<ShapeShortRows, true>(a, num_sms, s);

@@ -114,3 +114,10 @@ def test_product_code_never_touches_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.lower(), f
+
+
+def test_set_tuning_and_batch_reject_null(bp):
+    assert bp.lib().bpmf_set_tuning(None, 1, 1) == bp.BPMF_EINVAL
+    arr = (__import__("ctypes").c_void_p * 1)(None)
+    assert bp.lib().bpmf_sweep_batch(arr, 1, 1) == bp.BPMF_EINVAL
+    assert bp.lib().bpmf_sweep_batch(arr, -1, 1) == bp.BPMF_EINVAL
