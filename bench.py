@@ -233,7 +233,13 @@ def run_native(args):
     phases = [bp.BPMF_PHASE_HYPER_MOVIE, bp.BPMF_PHASE_ROWS_MOVIE, bp.BPMF_PHASE_HYPER_USER,
               bp.BPMF_PHASE_ROWS_USER, bp.BPMF_PHASE_PREDICT, bp.BPMF_PHASE_ADVANCE]
     names = ["hyper_movie", "rows_movie", "hyper_user", "rows_user", "predict", "advance"]
+    tuning = None
     try:
+        if args.autotune:
+            from paper_1705_10633_gb300.autotune import autotune
+            best, times = autotune(h, prob.M, prob.N, K, stream.cuda_stream)
+            tuning = {"long_min_degree": best[0], "long_shape_degree": best[1],
+                      "trials_ms": {"%d/%d" % k: round(v, 3) for k, v in sorted(times.items())}}
         for _ in range(args.warmup):
             bp.bpmf_sweep(h, 1, want_rmse=False)
         torch.cuda.synchronize(dev)
@@ -335,7 +341,7 @@ def run_native(args):
                       "l2": "inputs larger than L2 (ratings CSR+CSC %.2f GB)" % (nnz * 16 / 1e9),
                       "bins": {"users": [info_u["n_short"], info_u["n_long"]],
                                "movies": [info_v["n_short"], info_v["n_long"]]},
-                      "parallelism": "replicas x%d" % world, "rmse_sample": finite_or_none(rs), "rmse_avg": finite_or_none(ra)},
+                      "tuning": tuning, "parallelism": "replicas x%d" % world, "rmse_sample": finite_or_none(rs), "rmse_avg": finite_or_none(ra)},
            "roofline": roofline, "clocks": clk, "gpu_launches": int(launches), "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, desc = oracle_sample_rate(prob, args.cpu_frac)
@@ -561,6 +567,8 @@ def main(argv=None):
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--bf16", action="store_true",
                     help="BF16-input tensor-core Gram (lower precision; not the headline)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="tune the row kernels' thresholds on the workload before timing")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-frac", type=float, default=0.1)
