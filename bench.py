@@ -160,7 +160,7 @@ def row_gather_bytes(nnz, rows, K, split=True):
 # DRAM bytes (read + write) per launch of the row kernel on the 480k x 18k, 1e8-rating,
 # K = 64 workload, from one ncu capture of this kernel version (null once the kernel
 # changes).
-TRAFFIC = {"rows_user": 937e6}
+TRAFFIC = {"rows_user": 934e6}
 
 
 def finite_or_none(x):
