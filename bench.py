@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "latent rows sampled/s (Gibbs sweep, K=64)"
+METRIC = "latent rows sampled/s (Gibbs sweep, K=%d)"
 UNIT = "rows/s"
 
 
@@ -332,7 +332,7 @@ def run_native(args):
     if not args.no_e2e:
         e2e = run_e2e(args, prob, bp, torch, dev, stream, world, local)
 
-    out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+    out = {"metric": METRIC % K, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "bf16-gram/f32" if args.bf16 else "f32", "data": "synthetic",
@@ -399,7 +399,7 @@ def run_reference(args):
             rates.append(rate)
             times.append(t1 - t0)
     value = float(np.mean(rates))
-    out = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+    out = {"metric": METRIC % prob.K, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(1e3 * (prob.M + prob.N) / value, 2), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -106,6 +106,28 @@ void* dalloc(bpmf_ctx* h, size_t bytes)
     return p;
 }
 
+// Scratch for one call: through the caller's hook when there is one, not kept.
+void* temp_alloc(size_t bytes, void* ctx)
+{
+    bpmf_ctx* h = static_cast<bpmf_ctx*>(ctx);
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (h->p.alloc) return h->p.alloc(bytes, (void*)h->stream, h->p.alloc_ctx);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void temp_free(void* p, void* ctx)
+{
+    bpmf_ctx* h = static_cast<bpmf_ctx*>(ctx);
+    if (!p) return;
+    if (h->p.free) h->p.free(p, (void*)h->stream, h->p.alloc_ctx);
+    else cudaFree(p);
+}
+
 template <class T>
 bool alloc_n(bpmf_ctx* h, T** out, size_t n)
 {
@@ -472,7 +494,10 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
     std::vector<int64_t> cp;
     std::vector<int32_t> ri;
     std::vector<float> cv;
-    if (!have_csc) {
+    // without a caller-supplied CSC the column view is built on the device from the
+    // uploaded CSR (same order as the host counting sort, which serves the rest)
+    const bool device_csc = !have_csc && h->nnz > 0 && h->nnz < INT32_MAX;
+    if (!have_csc && !device_csc) {
         build_csc(M, N, csr_ptr, csr_col, csr_val, cp, ri, cv);
         csc_ptr = cp.data();
         csc_row = ri.data();
@@ -481,7 +506,7 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
     const int64_t long_min = prm.long_min_degree > 0 ? prm.long_min_degree : kDefaultLongMinDegree;
     h->long_min = long_min;
     h->long_shape_degree = prm.long_shape_degree > 0 ? prm.long_shape_degree : kDefaultLongShapeDegree;
-    const int64_t* hp[2] = {csr_ptr, csc_ptr};
+    const int64_t* hp[2] = {csr_ptr, device_csc ? nullptr : csc_ptr};
     const int32_t* hi[2] = {csr_col, csc_row};
     const float* hv[2] = {csr_val, csc_val};
     const int64_t rows[2] = {M, N};
@@ -512,18 +537,37 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
             rc = BPMF_ENOMEM;
             break;
         }
+        cudaError_t e = cudaSuccess;
+        const bool built = s == 1 && device_csc;
+        if (built) {
+            // from the user side's arrays, whose values are already centred (centring
+            // is per entry, so gathering centred values equals centring gathered ones)
+            const DevSide& u = h->side[0];
+            const TempAlloc tmp{temp_alloc, temp_free, h};
+            e = build_csc_device(u.ptr, u.idx, u.val, M, N, h->nnz, d.ptr, d.idx, d.val, tmp, st);
+            cp.resize((size_t)N + 1);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(cp.data(), d.ptr, sizeof(int64_t) * (N + 1),
+                                    cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            hp[1] = cp.data();
+        } else {
+            e = cudaMemcpyAsync(d.ptr, hp[s], sizeof(int64_t) * (d.rows + 1), cudaMemcpyHostToDevice,
+                                st);
+            if (e == cudaSuccess && h->nnz)
+                e = cudaMemcpyAsync(d.idx, hi[s], sizeof(int32_t) * h->nnz, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess && h->nnz)
+                e = cudaMemcpyAsync(d.val, hv[s], sizeof(float) * h->nnz, cudaMemcpyHostToDevice, st);
+        }
+        if (e != cudaSuccess) {
+            rc = BPMF_ECUDA;
+            break;
+        }
         bin_rows(d.rows, hp[s], long_min, order, &d.n_short, &d.n_long, &d.long_ratings);
         d.ptr_h.assign(hp[s], hp[s] + d.rows + 1);
-        cudaError_t e = cudaMemcpyAsync(d.ptr, hp[s], sizeof(int64_t) * (d.rows + 1),
-                                        cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess && h->nnz)
-            e = cudaMemcpyAsync(d.idx, hi[s], sizeof(int32_t) * h->nnz, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess && h->nnz)
-            e = cudaMemcpyAsync(d.val, hv[s], sizeof(float) * h->nnz, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(d.bin_rows, order.data(), sizeof(int32_t) * d.rows,
-                                cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = launch_center_values(d.val, h->nnz, h->rbar, st);
+        e = cudaMemcpyAsync(d.bin_rows, order.data(), sizeof(int32_t) * d.rows,
+                            cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !built) e = launch_center_values(d.val, h->nnz, h->rbar, st);
         if (e == cudaSuccess) e = launch_init_factors(d.X, d.rows, K, kp, prm.seed, d.tag_init, st);
         if (e == cudaSuccess && d.Xh) e = launch_split_factors(d.X, d.rows, kp, d.Xh, d.Xl, (h->p.flags & BPMF_BF16_GRAM) ? 1 : 0, st);
         if (e == cudaSuccess && d.means) e = cudaMemsetAsync(d.means, 0, sizeof(float) * d.rows * kp, st);

@@ -103,6 +103,22 @@ cudaError_t launch_hyper_refresh(const double* mu64, const double* lam64, int K,
 // Row updates on CUDA cores: one warp per row (any degree).
 cudaError_t launch_rows_warp(const RowArgs& a, int kp, int num_sms, cudaStream_t s);
 // Row updates with the Gram on tensor cores (kp == 64, rows of the long bin).
+// Scratch device memory for one call (allocated and returned inside it).
+struct TempAlloc {
+    void* (*alloc_fn)(size_t bytes, void* ctx);
+    void (*free_fn)(void* p, void* ctx);
+    void* ctx;
+    void* alloc(size_t bytes) const { return alloc_fn(bytes, ctx); }
+    void free(void* p) const { free_fn(p, ctx); }
+};
+
+// CSC of the ratings from the CSR on the device (same order as a stable counting
+// sort by column).  csc_ptr: N + 1, csc_row / csc_val: nnz (< 2^31).  Waits for the
+// stream before returning its scratch.
+cudaError_t build_csc_device(const int64_t* csr_ptr, const int32_t* csr_col, const float* csr_val,
+                             int64_t M, int64_t N, int64_t nnz, int64_t* csc_ptr, int32_t* csc_row,
+                             float* csc_val, const TempAlloc& tmp, cudaStream_t s);
+
 // nratings: ratings of the rows in a.rows; rows averaging shape_degree ratings or more
 // take the CTA shape with more gather stages.
 cudaError_t launch_rows_tc(const RowArgs& a, int64_t nratings, int64_t shape_degree, int num_sms,

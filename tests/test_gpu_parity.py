@@ -131,6 +131,33 @@ def test_three_sweeps_config1(bp):
     assert_worst(step_parity(bp, workloads.config1(), sweeps=3))
 
 
+@pytest.mark.parametrize("K", [10, 64])
+def test_device_column_view_equals_host_one(bp, K):
+    """Without a caller CSC the library builds the column view on the device; with the
+    host's CSC passed in, every sweep must come out bit-identical (same column order)."""
+    import torch
+    prob = workloads.random_small(900, 300, K, 30000, seed=81, n_test=100, empty_cols=5)
+    cp, cr, cv = prob.csc()
+    runs = []
+    for csc in (None, (cp, cr, cv)):
+        p = bp.bpmf_default_params(alpha=prob.alpha, seed=prob.seed, burn_in=1)
+        kw = {} if csc is None else {"csc_ptr": csc[0], "csc_row": csc[1], "csc_val": csc[2]}
+        st = torch.cuda.Stream()
+        h = bp.bpmf_create(prob.M, prob.N, prob.K, prob.csr_ptr, prob.csr_col, prob.csr_val,
+                           test_i=prob.test_i, test_j=prob.test_j, test_r=prob.test_r, params=p,
+                           stream=st.cuda_stream, **kw)
+        try:
+            r = bp.bpmf_sweep(h, 3)
+            runs.append((bp.bpmf_get_state(h, prob.M, prob.N, prob.K), r,
+                         bp.bpmf_info(h, 1)["n_long"]))
+        finally:
+            bp.bpmf_destroy(h)
+    (sa, ra, na), (sb, rb, nb) = runs
+    for x, y in zip(sa[:3], sb[:3]):
+        np.testing.assert_array_equal(x, y)
+    assert ra == rb and na == nb
+
+
 @pytest.mark.parametrize("K,order", [(8, 0), (64, 0), (64, 1)])
 def test_sweep_entry_point_matches_phases(bp, K, order):
     """bpmf_sweep overlaps each hyper step with a row phase on a second stream, runs
