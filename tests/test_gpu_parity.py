@@ -300,3 +300,60 @@ def test_torch_caching_allocator_hook(bp):
         assert bp.bpmf_sweep(h, 2) == r1
     finally:
         bp.bpmf_destroy(h)
+
+
+def full_size_sampled_rows(bp, prob):
+    """One sweep of a full-size workload, each half-sweep checked on sampled rows (200
+    uniform, the 8 longest and 8 shortest) against the oracle started from the GPU's
+    state: statistics, Normal-Wishart draw, factors and conditional means."""
+    K = prob.K
+    h = bp.create_from_problem(prob, flags=bp.BPMF_DEBUG_MEANS, stream=bp.torch_stream())
+    rng = np.random.default_rng(0)
+    try:
+        bp.bpmf_sweep(h, 1)  # leave the initial state
+        U, V, hyper, s = bp.bpmf_get_state(h, prob.M, prob.N, K)
+        orc = oracle.Oracle(prob, nthreads=None)
+        orc.set_factors(0, U)
+        orc.set_factors(1, V)
+        orc.set_counters(s, 0)
+        for side, hp, rp, n in ((1, bp.BPMF_PHASE_HYPER_MOVIE, bp.BPMF_PHASE_ROWS_MOVIE, prob.N),
+                                (0, bp.BPMF_PHASE_HYPER_USER, bp.BPMF_PHASE_ROWS_USER, prob.M)):
+            bp.bpmf_step(h, hp)
+            nst, mean, S = bp.bpmf_get_stats(h, side, K)
+            m_ref, S_ref = oracle.row_stats(orc.get_factors(side))
+            assert np.linalg.norm(S - S_ref) <= 1e-5 * np.linalg.norm(S_ref)
+            _, _, hyper, _ = bp.bpmf_get_state(h, prob.M, prob.N, K)
+            off = 0 if side == 0 else K + K * K
+            mu_g, Lam_g = hyper[off:off + K], hyper[off + K:off + K + K * K].reshape(K, K)
+            Lam_ref, mu_ref = orc.nw_from_stats(side, nst, mean, S, s)
+            assert np.linalg.norm(Lam_g - Lam_ref) <= 1e-9 * np.linalg.norm(Lam_ref)
+            orc.set_hyper(side, mu_g, Lam_g)
+            bp.bpmf_step(h, rp)
+            deg = np.diff(prob.csr_ptr) if side == 0 else prob.col_degrees()
+            order = np.argsort(deg)
+            sample = np.unique(np.concatenate([rng.choice(n, 200, replace=False), order[-8:],
+                                               order[:8]]))
+            orc.rows_subset(side, sample)
+            Xg = bp.bpmf_get_state(h, prob.M, prob.N, K)[side]
+            Mg = bp.bpmf_debug_means(h, side, n, K)
+            ex = rowwise_rel(Xg[sample], orc.get_factors(side)[sample])
+            em = rowwise_rel(Mg[sample], orc.get_means(side)[sample])
+            worst = sorted(zip(ex, deg[sample]), reverse=True)[:5]
+            print("side %d worst (err, degree):" % side, [("%.2e" % e, int(d)) for e, d in worst])
+            assert ex.max() <= ROW_TOL, (side, worst)
+            assert em.max() <= ROW_TOL, (side, em.max(), deg[sample[np.argmax(em)]])
+            orc.set_factors(side, Xg)
+        assert bp.bpmf_status(h) == 0
+    finally:
+        bp.bpmf_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def config2():
+    return workloads.config2()
+
+
+def test_full_size_config2_sampled_rows(bp, config2):
+    """The 200,000 x 5,000, 2M-rating, K = 32 workload on the CUDA-core kernel (Zipf
+    columns up to tens of thousands of ratings in one warp)."""
+    full_size_sampled_rows(bp, config2)
