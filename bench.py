@@ -239,7 +239,8 @@ def run_native(args):
             from paper_1705_10633_gb300.autotune import autotune
             best, times = autotune(h, prob.M, prob.N, K, stream.cuda_stream)
             tuning = {"long_min_degree": best[0], "long_shape_degree": best[1],
-                      "trials_ms": {"%d/%d" % k: round(v, 3) for k, v in sorted(times.items())}}
+                      "split_degree": best[2],
+                      "trials_ms": {"%d/%d/%d" % k: round(v, 3) for k, v in sorted(times.items())}}
         for _ in range(args.warmup):
             bp.bpmf_sweep(h, 1, want_rmse=False)
         torch.cuda.synchronize(dev)
@@ -340,7 +341,9 @@ def run_native(args):
                       "test": prob.T, "sweeps_per_s": round(1e3 / ms_per_step, 3),
                       "l2": "inputs larger than L2 (ratings CSR+CSC %.2f GB)" % (nnz * 16 / 1e9),
                       "bins": {"users": [info_u["n_short"], info_u["n_long"]],
-                               "movies": [info_v["n_short"], info_v["n_long"]]},
+                               "movies": [info_v["n_short"], info_v["n_long"]],
+                               "split_rows_segments": [[info_u["n_split"], info_u["n_segments"]],
+                                                       [info_v["n_split"], info_v["n_segments"]]]},
                       "tuning": tuning, "parallelism": "replicas x%d" % world, "rmse_sample": finite_or_none(rs), "rmse_avg": finite_or_none(ra)},
            "roofline": roofline, "clocks": clk, "gpu_launches": int(launches), "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -92,6 +92,10 @@ typedef struct {
     int32_t long_shape_degree; /* tensor-core launches whose rows average at least this
                                   many ratings use the CTA shape with more gather stages
                                   and fewer factorisation warps; <= 0 = default (1024)  */
+    int32_t split_degree; /* rows on the CUDA-core kernel with at least this many ratings
+                             are split into runs of split_degree / 2 ratings done by
+                             separate warps (Sec. 3.2), the partial Gram matrices summed
+                             in run order by the last warp; <= 0 = default (1024)      */
     bpmf_alloc_fn alloc; /* NULL = cudaMalloc / cudaFree */
     bpmf_free_fn free;
     void* alloc_ctx;
@@ -145,14 +149,17 @@ int bpmf_sweep(bpmf_handle h, int32_t n_sweeps, double* rmse_sample, double* rms
 int bpmf_sweep_batch(bpmf_handle* hs, int32_t n, int32_t n_sweeps);
 
 /*
- * Change the two tuning thresholds of a live handle (long_min_degree and
- * long_shape_degree of bpmf_params; <= 0 = library default): the rows of both
- * sides are binned again (host sort of the degrees kept from bpmf_create, one
- * host-to-device copy per side, waited for).  The chain state is untouched; rows
- * may move between the CUDA-core and tensor-core kernels, whose results agree
- * within the FP32 tolerance, not bit for bit.  For autotuning.
+ * Change the tuning thresholds of a live handle (long_min_degree, long_shape_degree
+ * and split_degree of bpmf_params; <= 0 = library default): the rows of both sides
+ * are binned and split again (host sort of the degrees kept from bpmf_create,
+ * host-to-device copies waited for; the segment arrays grow when a smaller
+ * split_degree needs more, the old ones held until bpmf_destroy).  The chain state
+ * is untouched; rows may move between the CUDA-core and tensor-core kernels or
+ * between split and whole, whose results agree within the FP32 tolerance, not bit
+ * for bit.  For autotuning.  BPMF_ENOMEM / BPMF_ECUDA leave the handle unusable.
  */
-int bpmf_set_tuning(bpmf_handle h, int32_t long_min_degree, int32_t long_shape_degree);
+int bpmf_set_tuning(bpmf_handle h, int32_t long_min_degree, int32_t long_shape_degree,
+                    int32_t split_degree);
 
 /* Run one BPMF_PHASE_* step of a sweep (for checking the steps one by one). */
 int bpmf_step(bpmf_handle h, int32_t phase);
@@ -193,9 +200,10 @@ int bpmf_debug_means(bpmf_handle h, int32_t side, float* out);
 int bpmf_status(bpmf_handle h);
 
 /* Diagnostics: number of rows of `side` on the CUDA-core kernel and on the
- * tensor-core kernel, the centring mean, and device bytes held. */
-int bpmf_info(bpmf_handle h, int32_t side, int64_t* n_short, int64_t* n_long, double* rbar,
-              int64_t* device_bytes);
+ * tensor-core kernel, how many of the former are split and into how many
+ * segments, the centring mean, and device bytes held.  NULL outputs are skipped. */
+int bpmf_info(bpmf_handle h, int32_t side, int64_t* n_short, int64_t* n_long, int64_t* n_split,
+              int64_t* n_segments, double* rbar, int64_t* device_bytes);
 
 /* Number of kernels this handle has launched so far (all phases, all sweeps). */
 int bpmf_launch_count(bpmf_handle h, int64_t* launches);

@@ -44,6 +44,7 @@ class bpmf_params(C.Structure):
                 ("order", C.c_int32), ("flags", C.c_uint32), ("clip_lo", C.c_double),
                 ("clip_hi", C.c_double), ("long_min_degree", C.c_int32),
                 ("wait_timeout_ms", C.c_int32), ("long_shape_degree", C.c_int32),
+                ("split_degree", C.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
@@ -73,7 +74,7 @@ def lib():
     L.bpmf_sweep.argtypes = [vp, i32, P(C.c_double), P(C.c_double)]
     L.bpmf_sweep_batch.argtypes = [P(vp), i32, i32]
     L.bpmf_step.argtypes = [vp, i32]
-    L.bpmf_set_tuning.argtypes = [vp, i32, i32]
+    L.bpmf_set_tuning.argtypes = [vp, i32, i32, i32]
     L.bpmf_predict.argtypes = [vp, i64, vp, vp, vp, i32]
     L.bpmf_get_state.argtypes = [vp, vp, vp, vp, P(C.c_uint64)]
     L.bpmf_set_state.argtypes = [vp, vp, vp, vp, C.c_uint64]
@@ -82,7 +83,7 @@ def lib():
     L.bpmf_get_stats.argtypes = [vp, i32, P(i64), vp, vp]
     L.bpmf_debug_means.argtypes = [vp, i32, vp]
     L.bpmf_status.argtypes = [vp]
-    L.bpmf_info.argtypes = [vp, i32, P(i64), P(i64), P(C.c_double), P(i64)]
+    L.bpmf_info.argtypes = [vp, i32, P(i64), P(i64), P(i64), P(i64), P(C.c_double), P(i64)]
     L.bpmf_launch_count.argtypes = [vp, P(i64)]
     L.bpmf_row_stats_noalloc.argtypes = [vp, i64, i32, vp, vp, vp, vp]
     L.bpmf_strerror.argtypes = [C.c_int]
@@ -195,10 +196,11 @@ def bpmf_sweep_batch(handles, n_sweeps=1):
     _check(lib().bpmf_sweep_batch(arr, len(handles), int(n_sweeps)), "bpmf_sweep_batch")
 
 
-def bpmf_set_tuning(h, long_min_degree=0, long_shape_degree=0):
-    """Re-bin a live handle's rows under new thresholds (<= 0: library defaults)."""
-    _check(lib().bpmf_set_tuning(h, int(long_min_degree), int(long_shape_degree)),
-           "bpmf_set_tuning")
+def bpmf_set_tuning(h, long_min_degree=0, long_shape_degree=0, split_degree=0):
+    """Re-bin and re-split a live handle's rows under new thresholds (<= 0: library
+    defaults)."""
+    _check(lib().bpmf_set_tuning(h, int(long_min_degree), int(long_shape_degree),
+                                 int(split_degree)), "bpmf_set_tuning")
 
 
 def bpmf_step(h, phase):
@@ -265,11 +267,12 @@ def bpmf_status(h):
 
 
 def bpmf_info(h, side):
-    ns, nl, nb = C.c_int64(), C.c_int64(), C.c_int64()
+    ns, nl, nsp, nsg, nb = (C.c_int64() for _ in range(5))
     rb = C.c_double()
-    _check(lib().bpmf_info(h, int(side), C.byref(ns), C.byref(nl), C.byref(rb), C.byref(nb)),
-           "bpmf_info")
-    return {"n_short": ns.value, "n_long": nl.value, "rbar": rb.value, "device_bytes": nb.value}
+    _check(lib().bpmf_info(h, int(side), C.byref(ns), C.byref(nl), C.byref(nsp), C.byref(nsg),
+                           C.byref(rb), C.byref(nb)), "bpmf_info")
+    return {"n_short": ns.value, "n_long": nl.value, "n_split": nsp.value,
+            "n_segments": nsg.value, "rbar": rb.value, "device_bytes": nb.value}
 
 
 def bpmf_launch_count(h):

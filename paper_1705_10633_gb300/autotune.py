@@ -1,11 +1,14 @@
-"""Autotuner for the row kernels' two thresholds, on a job's own data.
+"""Autotuner for the row kernels' thresholds, on a job's own data.
 
 The thresholds are the degree from which a row takes the tensor-core kernel
-(below it, the CUDA-core warp-per-row kernel) and the mean degree from which a
+(below it, the CUDA-core warp-per-row kernel), the mean degree from which a
 tensor-core launch uses the CTA shape with more gather stages and fewer
-factorisation warps.  Each candidate pair is applied to the live handle
-(`bpmf_set_tuning` bins the rows again), the two row phases are run and timed
-with CUDA events on the handle's stream, and the fastest pair is kept.  The
+factorisation warps, and the degree from which a CUDA-core row is split into
+segments done by separate warps.  At K in 49..64 the first two are tuned (the
+CUDA-core kernel then holds few rows), below that the third.  Each candidate is
+applied to the live handle (`bpmf_set_tuning` bins and splits the rows again),
+the two row phases are run and timed with CUDA events on the handle's stream,
+and the fastest candidate is kept.  The
 chain's factors, hyper-parameters and sweep counter are saved first and
 restored after every trial, so tuning does not move the chain (the row phases
 do not touch the running prediction sums).
@@ -16,25 +19,29 @@ import itertools
 
 LONG_MIN_CANDIDATES = (1, 16, 48, 128)
 SHAPE_CANDIDATES = (256, 1024, 4096, 1 << 30)
+SPLIT_CANDIDATES = (128, 512, 1024, 4096, 1 << 30)
 
 
-def autotune(h, M, N, K, stream, long_min=LONG_MIN_CANDIDATES, shape=SHAPE_CANDIDATES, reps=2):
-    """Returns ((long_min_degree, long_shape_degree), {pair: ms for one pass of both row
-    phases}).  `stream` is the raw cudaStream_t the handle was created with.  At K <= 48
-    every row takes the CUDA-core kernel and nothing is tuned."""
+def autotune(h, M, N, K, stream, long_min=LONG_MIN_CANDIDATES, shape=SHAPE_CANDIDATES,
+             split=SPLIT_CANDIDATES, reps=2):
+    """Returns ((long_min_degree, long_shape_degree, split_degree), {triple: ms for one
+    pass of both row phases}).  `stream` is the raw cudaStream_t the handle was created
+    with.  0 in a triple is the library default."""
     import torch
 
     import paper_1705_10633_gb300 as bp
 
-    if (K + 15) // 16 * 16 != 64:
-        return (0, 0), {}
+    if (K + 15) // 16 * 16 == 64:
+        grid = [(lm, sd, 0) for lm, sd in itertools.product(long_min, shape)]
+    else:
+        grid = [(0, 0, sp) for sp in split]
     st = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
     U, V, hyper, sweep = bp.bpmf_get_state(h, M, N, K)
     rows = (bp.BPMF_PHASE_ROWS_MOVIE, bp.BPMF_PHASE_ROWS_USER)
     times = {}
     try:
-        for lm, sd in itertools.product(long_min, shape):
-            bp.bpmf_set_tuning(h, lm, sd)
+        for cand in grid:
+            bp.bpmf_set_tuning(h, *cand)
             for ph in rows:  # warm-up: launch shapes, caches
                 bp.bpmf_step(h, ph)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -44,7 +51,7 @@ def autotune(h, M, N, K, stream, long_min=LONG_MIN_CANDIDATES, shape=SHAPE_CANDI
                     bp.bpmf_step(h, ph)
             e1.record(st)
             e1.synchronize()
-            times[(lm, sd)] = e0.elapsed_time(e1) / reps
+            times[cand] = e0.elapsed_time(e1) / reps
             bp.bpmf_set_state(h, U, V, hyper, sweep)
         best = min(times, key=times.get)
         bp.bpmf_set_tuning(h, *best)

@@ -19,6 +19,7 @@ namespace {
 
 constexpr int kDefaultLongMinDegree = 1;
 constexpr int kDefaultLongShapeDegree = 1024;
+constexpr int kDefaultSplitDegree = 1024;
 constexpr int kDefaultWaitTimeoutMs = 2000;
 
 struct DevSide {
@@ -34,6 +35,13 @@ struct DevSide {
     int64_t n_short = 0, n_long = 0;
     int64_t long_ratings = 0;  // ratings of the long bin's rows
     std::vector<int64_t> ptr_h;  // host copy of ptr, for binning again (bpmf_set_tuning)
+    // long rows of the CUDA-core kernel, cut into segments (first n_split rows of
+    // the short bin); capacities grow when bpmf_set_tuning asks for more
+    Segment* segs = nullptr;
+    int64_t n_segs = 0, seg_cap = 0;
+    int64_t n_split = 0, split_cap = 0;
+    float* part = nullptr;           // seg_cap partials
+    unsigned int* seg_done = nullptr;  // split_cap counters, zero between launches
     double* mu64 = nullptr;
     double* shift64 = nullptr;  // kp: shift of the hyper statistics
     double* lam64 = nullptr;
@@ -53,6 +61,7 @@ struct bpmf_ctx {
     int num_sms = 1;
     int64_t long_min = 1;            // binning threshold of the tensor-core kernel
     int64_t long_shape_degree = 1024;  // mean degree that selects the many-stage CTA shape
+    int64_t split_degree = 1024;  // CUDA-core rows with this many ratings are split
     int row_sms = 1;  // CTAs of the row kernels: all SMs, or all but one while the
                       // next hyper step runs beside them (bpmf_sweep)
     cudaStream_t stream = nullptr;
@@ -230,6 +239,63 @@ void bin_rows(int64_t rows, const int64_t* ptr, int64_t long_min, std::vector<in
     *long_ratings = nl_ratings;
 }
 
+// Segments of the CUDA-core kernel's long rows (Sec. 3.2's split of items with many
+// ratings into smaller parallel tasks): the rows at the head of the short bin (longest
+// first) with at least split_degree ratings are cut into ceil(d / (split_degree / 2))
+// near-equal runs of consecutive ratings.  Uploads the list (waited for) and zeroes
+// the rows' counters; grows the device arrays when the list outgrows them.
+int plan_segments(bpmf_ctx* h, DevSide& d, const std::vector<int32_t>& order)
+{
+    std::vector<Segment> segs;
+    int64_t nsplit = 0;
+    const int64_t seg_len = h->split_degree / 2 > 0 ? h->split_degree / 2 : 1;
+    for (int64_t r = 0; r < d.n_short; ++r) {
+        const int32_t row = order[(size_t)r];
+        const int64_t p0 = d.ptr_h[(size_t)row], deg = d.ptr_h[(size_t)row + 1] - p0;
+        if (deg < h->split_degree || deg < 2) break;  // the bin is ordered longest first
+        const int64_t n = (deg + seg_len - 1) / seg_len;
+        const int32_t first = (int32_t)segs.size();
+        for (int64_t t = 0; t < n; ++t)
+            segs.push_back(Segment{p0 + t * deg / n, p0 + (t + 1) * deg / n, row, (int32_t)nsplit,
+                                   first, (int32_t)n});
+        ++nsplit;
+    }
+    const int64_t nsegs = (int64_t)segs.size();
+    if (nsegs > d.seg_cap) {
+        if (!alloc_n(h, &d.segs, (size_t)nsegs) ||
+            !alloc_n(h, &d.part, (size_t)nsegs * warp_partial_floats(h->kp)))
+            return BPMF_ENOMEM;
+        d.seg_cap = nsegs;
+    }
+    if (nsplit > d.split_cap) {
+        if (!alloc_n(h, &d.seg_done, (size_t)nsplit)) return BPMF_ENOMEM;
+        d.split_cap = nsplit;
+    }
+    cudaError_t e = cudaSuccess;
+    if (nsegs)
+        e = cudaMemcpyAsync(d.segs, segs.data(), sizeof(Segment) * nsegs, cudaMemcpyHostToDevice,
+                            h->stream);
+    if (e == cudaSuccess && nsplit)
+        e = cudaMemsetAsync(d.seg_done, 0, sizeof(unsigned int) * nsplit, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // `segs` goes out of scope
+    if (e != cudaSuccess) return BPMF_ECUDA;
+    d.n_segs = nsegs;
+    d.n_split = nsplit;
+    return BPMF_OK;
+}
+
+// Bins of one side (every row in the short bin when the tensor-core kernel is off)
+// and the split of its long CUDA-core rows.
+int bin_side(bpmf_ctx* h, DevSide& d, std::vector<int32_t>& order)
+{
+    bin_rows(d.rows, d.ptr_h.data(), h->tc ? h->long_min : INT64_MAX, order, &d.n_short, &d.n_long,
+             &d.long_ratings);
+    cudaError_t e = cudaMemcpyAsync(d.bin_rows, order.data(), sizeof(int32_t) * d.rows,
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return BPMF_ECUDA;
+    return plan_segments(h, d, order);  // waits for the stream: `order` may be reused
+}
+
 int sync_status(bpmf_ctx* h)
 {
     Control c;
@@ -308,19 +374,20 @@ int phase_rows(bpmf_ctx* h, int s)
     a.test_stall = (h->p.flags & BPMF_TEST_STALL) ? 1 : 0;
     a.bf16 = (h->p.flags & BPMF_BF16_GRAM) ? 1 : 0;
     cudaError_t e = cudaSuccess;
-    if (!h->tc) {
-        // every row on the CUDA-core kernel
-        a.rows = d.bin_rows;
-        a.nrows = d.n_short + d.n_long;
-        if (a.nrows > 0) h->launches += 1;
-        return cuda_rc(launch_rows_warp(a, h->kp, h->row_sms, h->stream));
-    }
+    // the short bin (every row when the tensor-core kernel is off) on the CUDA-core
+    // kernel, its longest rows as segments
     a.rows = d.bin_rows;
     a.nrows = d.n_short;
+    a.segs = d.segs;
+    a.nsegs = d.n_segs;
+    a.nsplit = d.n_split;
+    a.part = d.part;
+    a.seg_done = d.seg_done;
     if (a.nrows > 0) {
         h->launches += 1;
         e = launch_rows_warp(a, h->kp, h->row_sms, h->stream);
     }
+    a.nsegs = a.nsplit = 0;
     a.rows = d.bin_rows + d.n_short;
     a.nrows = d.n_long;
     if (e == cudaSuccess && a.nrows > 0) {
@@ -506,6 +573,7 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
     const int64_t long_min = prm.long_min_degree > 0 ? prm.long_min_degree : kDefaultLongMinDegree;
     h->long_min = long_min;
     h->long_shape_degree = prm.long_shape_degree > 0 ? prm.long_shape_degree : kDefaultLongShapeDegree;
+    h->split_degree = prm.split_degree > 0 ? prm.split_degree : kDefaultSplitDegree;
     const int64_t* hp[2] = {csr_ptr, device_csc ? nullptr : csc_ptr};
     const int32_t* hi[2] = {csr_col, csc_row};
     const float* hv[2] = {csr_val, csc_val};
@@ -563,10 +631,9 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
             rc = BPMF_ECUDA;
             break;
         }
-        bin_rows(d.rows, hp[s], long_min, order, &d.n_short, &d.n_long, &d.long_ratings);
         d.ptr_h.assign(hp[s], hp[s] + d.rows + 1);
-        e = cudaMemcpyAsync(d.bin_rows, order.data(), sizeof(int32_t) * d.rows,
-                            cudaMemcpyHostToDevice, st);
+        rc = bin_side(h, d, order);
+        if (rc != BPMF_OK) break;
         if (e == cudaSuccess && !built) e = launch_center_values(d.val, h->nnz, h->rbar, st);
         if (e == cudaSuccess) e = launch_init_factors(d.X, d.rows, K, kp, prm.seed, d.tag_init, st);
         if (e == cudaSuccess && d.Xh) e = launch_split_factors(d.X, d.rows, kp, d.Xh, d.Xl, (h->p.flags & BPMF_BF16_GRAM) ? 1 : 0, st);
@@ -612,19 +679,17 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
     return BPMF_OK;
 }
 
-int bpmf_set_tuning(bpmf_handle h, int32_t long_min_degree, int32_t long_shape_degree)
+int bpmf_set_tuning(bpmf_handle h, int32_t long_min_degree, int32_t long_shape_degree,
+                    int32_t split_degree)
 {
     if (!h) return BPMF_EINVAL;
     h->long_min = long_min_degree > 0 ? long_min_degree : kDefaultLongMinDegree;
     h->long_shape_degree = long_shape_degree > 0 ? long_shape_degree : kDefaultLongShapeDegree;
+    h->split_degree = split_degree > 0 ? split_degree : kDefaultSplitDegree;
     std::vector<int32_t> order;
     for (int s = 0; s < 2; ++s) {
-        DevSide& d = h->side[s];
-        bin_rows(d.rows, d.ptr_h.data(), h->long_min, order, &d.n_short, &d.n_long, &d.long_ratings);
-        cudaError_t e = cudaMemcpyAsync(d.bin_rows, order.data(), sizeof(int32_t) * d.rows,
-                                        cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // `order` is reused
-        if (e != cudaSuccess) return BPMF_ECUDA;
+        const int rc = bin_side(h, h->side[s], order);
+        if (rc != BPMF_OK) return rc;
     }
     // the captured sweep holds the old bins' launch shapes
     if (h->sweep_graph) cudaGraphExecDestroy(h->sweep_graph);
@@ -976,12 +1041,14 @@ int bpmf_launch_count(bpmf_handle h, int64_t* launches)
     return BPMF_OK;
 }
 
-int bpmf_info(bpmf_handle h, int32_t side, int64_t* n_short, int64_t* n_long, double* rbar,
-              int64_t* device_bytes)
+int bpmf_info(bpmf_handle h, int32_t side, int64_t* n_short, int64_t* n_long, int64_t* n_split,
+              int64_t* n_segments, double* rbar, int64_t* device_bytes)
 {
     if (!h || (side != 0 && side != 1)) return BPMF_EINVAL;
     if (n_short) *n_short = h->side[side].n_short;
     if (n_long) *n_long = h->side[side].n_long;
+    if (n_split) *n_split = h->side[side].n_split;
+    if (n_segments) *n_segments = h->side[side].n_segs;
     if (rbar) *rbar = h->rbar;
     if (device_bytes) *device_bytes = h->bytes;
     return BPMF_OK;

@@ -22,6 +22,14 @@ struct Control {
 
 enum : unsigned int { kStatusNotPD = 1u, kStatusNaN = 2u, kStatusGamma = 4u };
 
+// One segment of a long row on the CUDA-core kernel: ratings [lo, hi) of `row`, the
+// `slot`-th split row, whose segments are first .. first + count - 1 (Sec. 3.2: an
+// item with many ratings is cut into smaller tasks that run in parallel).
+struct Segment {
+    int64_t lo, hi;
+    int32_t row, slot, first, count;
+};
+
 // Arguments of one row-update launch (one side, one degree bin).
 struct RowArgs {
     const int64_t* ptr;    // rows + 1 offsets into idx/val
@@ -36,6 +44,15 @@ struct RowArgs {
     const __half* Yl;
     const int32_t* rows;   // rows of this bin, longest first
     int64_t nrows;
+    // CUDA-core kernel only: the first nsplit rows are done as nsegs segments, each
+    // writing its partial Gram rows and right-hand side to part; the last segment of
+    // a row to finish (counted in seg_done, which it resets) sums them in segment
+    // order and samples the row
+    const Segment* segs;
+    int64_t nsegs;
+    int64_t nsplit;
+    float* part;
+    unsigned int* seg_done;
     const float* lam;      // prior precision, kp x kp, identity beyond K
     const float* lam_ct;   // the same, chunk-transposed: float4 (i, 4c..4c+3) at c * kp + i
     const float* lammu;    // prior precision times prior mean, kp (zero beyond K)
@@ -102,6 +119,9 @@ cudaError_t launch_hyper_refresh(const double* mu64, const double* lam64, int K,
 
 // Row updates on CUDA cores: one warp per row (any degree).
 cudaError_t launch_rows_warp(const RowArgs& a, int kp, int num_sms, cudaStream_t s);
+// Floats of one segment's partial in `part` (Gram rows owned by a lane, and the
+// right-hand side, lane-interleaved).
+int warp_partial_floats(int kp);
 // Row updates with the Gram on tensor cores (kp == 64, rows of the long bin).
 // Scratch device memory for one call (allocated and returned inside it).
 struct TempAlloc {

@@ -17,6 +17,15 @@
 //            shared memory each step and every lane updates its own rows.
 //   solves : forward substitution with the pivot broadcast by shuffle, back
 //            substitution reading L from shared memory.
+//
+// Long rows (Sec. 3.2: items with many ratings are split into smaller tasks so that
+// one item does not hold up the rest): the launch's work items are first the
+// segments of its split rows, then its other rows.  A segment's warp accumulates
+// the Gram rows and right-hand side of its ratings only and writes them to global
+// memory; the warp that finishes a row's last segment (a counter per row, taken
+// after a device-wide fence) adds the row's partials in segment order -- the sum
+// is the same whichever warp comes last -- and factors and samples the row.  No
+// warp waits for another.
 #include "bpmf_internal.cuh"
 #include "philox.cuh"
 #include "rows_common.cuh"
@@ -37,7 +46,98 @@ struct WarpLayout {
     static constexpr int SQ = KT * LD;
     static constexpr int PER_WARP = STAGE + SQ + 2 * KT + KT + KT + kChunk;  // floats
     static constexpr int PER_WARP_ALIGNED = (PER_WARP + 3) & ~3;
+    // a segment's partial: NR1 + (TWO ? KT : 0) Gram rows' entries and two right-hand
+    // side entries per lane, entry-major (32 consecutive floats per entry)
+    static constexpr int NA = TWO ? KT : 0;
+    static constexpr int PART = (NR1 + NA + 2) * 32;
 };
+
+// Gram rows i1, i2 and right-hand side entries of ratings [p0, p1), added to the
+// registers (the stage holds 32 gathered rows of Y at a time).
+template <int KT>
+__device__ __forceinline__ void accumulate_ratings(const RowArgs& a, int64_t p0, int64_t p1,
+                                                   float* stage, float* rb, int lane, bool v1,
+                                                   bool v2, float (&a1)[RowRegs<KT>::NR1],
+                                                   float (&a2)[RowRegs<KT>::NA2], float& rhs1,
+                                                   float& rhs2)
+{
+    using W = WarpLayout<KT>;
+    const int i1 = lane, i2 = 63 - lane;
+    for (int64_t base = p0; base < p1; base += kChunk) {
+        const int cnt = (int)min((int64_t)kChunk, p1 - base);
+        int c = 0;
+        float r = 0.f;
+        if (lane < cnt) {
+            c = __ldg(a.idx + base + lane);
+            r = __ldg(a.val + base + lane);
+        }
+        rb[lane] = r;
+        // gather the chunk's rows of Y into the stage (rows >= cnt are zero)
+        const int f = lane % W::F4, sub = lane / W::F4;
+#pragma unroll 4
+        for (int it = 0; it < kChunk / W::RPI; ++it) {
+            const int qq = it * W::RPI + sub;
+            const int cq = __shfl_sync(kFullMask, c, qq & 31);
+            if (sub < W::RPI) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (qq < cnt)
+                    v = __ldg(reinterpret_cast<const float4*>(a.Y + (int64_t)cq * a.ldy) + f);
+                reinterpret_cast<float4*>(stage + qq * KT)[f] = v;
+            }
+        }
+        __syncwarp();
+        // one rating at a time: row i of the Gram += y[i] * y (lower part used)
+#pragma unroll 2
+        for (int qq = 0; qq < cnt; ++qq) {
+            const float* srow = stage + qq * KT;
+            const float rq = rb[qq];
+            const float x1 = v1 ? srow[i1] : 0.f;
+            const float x2 = v2 ? srow[i2] : 0.f;
+            rhs1 = fmaf(rq, x1, rhs1);
+            rhs2 = fmaf(rq, x2, rhs2);
+#pragma unroll
+            for (int j4 = 0; j4 < KT; j4 += 4) {
+                const float4 y4 = *reinterpret_cast<const float4*>(srow + j4);
+                const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j4 + u;
+                    if (j < W::NR1) a1[j < W::NR1 ? j : 0] = fmaf(x1, yv[u], a1[j < W::NR1 ? j : 0]);
+                    if (W::TWO) a2[W::TWO ? j : 0] = fmaf(x2, yv[u], a2[W::TWO ? j : 0]);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int KT>
+__device__ __forceinline__ void store_partial(float* pp, int lane, const float (&a1)[RowRegs<KT>::NR1],
+                                              const float (&a2)[RowRegs<KT>::NA2], float rhs1,
+                                              float rhs2)
+{
+    using W = WarpLayout<KT>;
+#pragma unroll
+    for (int j = 0; j < W::NR1; ++j) __stcg(pp + j * 32 + lane, a1[j]);
+#pragma unroll
+    for (int j = 0; j < W::NA; ++j) __stcg(pp + (W::NR1 + j) * 32 + lane, a2[W::TWO ? j : 0]);
+    __stcg(pp + (W::NR1 + W::NA) * 32 + lane, rhs1);
+    __stcg(pp + (W::NR1 + W::NA + 1) * 32 + lane, rhs2);
+}
+
+// L2 loads: the partials were written by other SMs during this launch.
+template <int KT>
+__device__ __forceinline__ void add_partial(const float* pp, int lane, float (&a1)[RowRegs<KT>::NR1],
+                                            float (&a2)[RowRegs<KT>::NA2], float& rhs1, float& rhs2)
+{
+    using W = WarpLayout<KT>;
+#pragma unroll
+    for (int j = 0; j < W::NR1; ++j) a1[j] += __ldcg(pp + j * 32 + lane);
+#pragma unroll
+    for (int j = 0; j < W::NA; ++j) a2[W::TWO ? j : 0] += __ldcg(pp + (W::NR1 + j) * 32 + lane);
+    rhs1 += __ldcg(pp + (W::NR1 + W::NA) * 32 + lane);
+    rhs2 += __ldcg(pp + (W::NR1 + W::NA + 1) * 32 + lane);
+}
 
 template <int KT>
 __global__ void __launch_bounds__(kWarpsPerCta * 32) rows_warp_kernel(RowArgs a)
@@ -62,10 +162,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) rows_warp_kernel(RowArgs a)
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerCta;
     bool bad = false;
 
-    for (int64_t q = (int64_t)blockIdx.x * kWarpsPerCta + wib; q < a.nrows; q += nwarps) {
-        const int row = a.rows[q];
-        const int64_t p0 = a.ptr[row], p1 = a.ptr[row + 1];
-
+    const int64_t nitems = a.nsegs + a.nrows - a.nsplit;
+    for (int64_t q = (int64_t)blockIdx.x * kWarpsPerCta + wib; q < nitems; q += nwarps) {
         // Gram rows i1, i2 accumulate in the registers the Cholesky works on
         float a1[RowRegs<KT>::NR1];
         float a2[RowRegs<KT>::NA2];
@@ -74,52 +172,38 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) rows_warp_kernel(RowArgs a)
 #pragma unroll
         for (int j = 0; j < (W::TWO ? KT : 1); ++j) a2[j] = 0.f;
         float rhs1 = 0.f, rhs2 = 0.f;
-
-        for (int64_t base = p0; base < p1; base += kChunk) {
-            const int cnt = (int)min((int64_t)kChunk, p1 - base);
-            int c = 0;
-            float r = 0.f;
-            if (lane < cnt) {
-                c = __ldg(a.idx + base + lane);
-                r = __ldg(a.val + base + lane);
-            }
-            rb[lane] = r;
-            // gather the chunk's rows of Y into the stage (rows >= cnt are zero)
-            const int f = lane % W::F4, sub = lane / W::F4;
-#pragma unroll 4
-            for (int it = 0; it < kChunk / W::RPI; ++it) {
-                const int qq = it * W::RPI + sub;
-                const int cq = __shfl_sync(kFullMask, c, qq & 31);
-                if (sub < W::RPI) {
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (qq < cnt)
-                        v = __ldg(reinterpret_cast<const float4*>(a.Y + (int64_t)cq * a.ldy) + f);
-                    reinterpret_cast<float4*>(stage + qq * KT)[f] = v;
-                }
-            }
+        const bool is_seg = q < a.nsegs;
+        int row = 0;
+        int64_t p0, p1;
+        if (is_seg) {
+            p0 = __ldg(&a.segs[q].lo);
+            p1 = __ldg(&a.segs[q].hi);
+        } else {
+            row = a.rows[a.nsplit + (q - a.nsegs)];
+            p0 = a.ptr[row];
+            p1 = a.ptr[row + 1];
+        }
+        accumulate_ratings<KT>(a, p0, p1, stage, rb, lane, v1, v2, a1, a2, rhs1, rhs2);
+        if (is_seg) {
+            store_partial<KT>(a.part + q * W::PART, lane, a1, a2, rhs1, rhs2);
+            const Segment* sg = a.segs + q;
+            const int slot = __ldg(&sg->slot), first = __ldg(&sg->first), count = __ldg(&sg->count);
+            __threadfence();
             __syncwarp();
-            // one rating at a time: row i of the Gram += y[i] * y (lower part used)
-#pragma unroll 2
-            for (int qq = 0; qq < cnt; ++qq) {
-                const float* srow = stage + qq * KT;
-                const float rq = rb[qq];
-                const float x1 = v1 ? srow[i1] : 0.f;
-                const float x2 = v2 ? srow[i2] : 0.f;
-                rhs1 = fmaf(rq, x1, rhs1);
-                rhs2 = fmaf(rq, x2, rhs2);
+            unsigned int prev = 0;
+            if (lane == 0) prev = atomicAdd(a.seg_done + slot, 1u);
+            prev = __shfl_sync(kFullMask, prev, 0);
+            if (prev + 1 != (unsigned int)count) continue;  // another warp finishes the row
+            __threadfence();
 #pragma unroll
-                for (int j4 = 0; j4 < KT; j4 += 4) {
-                    const float4 y4 = *reinterpret_cast<const float4*>(srow + j4);
-                    const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+            for (int j = 0; j < W::NR1; ++j) a1[j] = 0.f;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int j = j4 + u;
-                        if (j < W::NR1) a1[j < W::NR1 ? j : 0] = fmaf(x1, yv[u], a1[j < W::NR1 ? j : 0]);
-                        if (W::TWO) a2[W::TWO ? j : 0] = fmaf(x2, yv[u], a2[W::TWO ? j : 0]);
-                    }
-                }
-            }
-            __syncwarp();
+            for (int j = 0; j < (W::TWO ? KT : 1); ++j) a2[j] = 0.f;
+            rhs1 = rhs2 = 0.f;
+            for (int g = 0; g < count; ++g)
+                add_partial<KT>(a.part + (int64_t)(first + g) * W::PART, lane, a1, a2, rhs1, rhs2);
+            if (lane == 0) a.seg_done[slot] = 0u;  // ready for the next launch
+            row = __ldg(&sg->row);
         }
         // Lambda_i rows = Lambda_X rows + alpha * Gram rows; b = alpha * rhs + Lambda_X mu_X
 #pragma unroll
@@ -156,7 +240,8 @@ static cudaError_t launch_kt(const RowArgs& a, int num_sms, cudaStream_t s)
                                                       kWarpsPerCta * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    int64_t need = (a.nrows + kWarpsPerCta - 1) / kWarpsPerCta;
+    const int64_t nitems = a.nsegs + a.nrows - a.nsplit;
+    int64_t need = (nitems + kWarpsPerCta - 1) / kWarpsPerCta;
     int64_t grid = (int64_t)num_sms * per_sm;
     if (need < grid) grid = need;
     if (grid < 1) return cudaSuccess;
@@ -164,9 +249,19 @@ static cudaError_t launch_kt(const RowArgs& a, int num_sms, cudaStream_t s)
     return cudaGetLastError();
 }
 
+int warp_partial_floats(int kp)
+{
+    switch (kp) {
+    case 16: return WarpLayout<16>::PART;
+    case 32: return WarpLayout<32>::PART;
+    case 48: return WarpLayout<48>::PART;
+    default: return WarpLayout<64>::PART;
+    }
+}
+
 cudaError_t launch_rows_warp(const RowArgs& a, int kp, int num_sms, cudaStream_t s)
 {
-    if (a.nrows <= 0) return cudaSuccess;
+    if (a.nsegs + a.nrows - a.nsplit <= 0) return cudaSuccess;
     switch (kp) {
     case 16: return launch_kt<16>(a, num_sms, s);
     case 32: return launch_kt<32>(a, num_sms, s);

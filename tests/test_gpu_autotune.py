@@ -63,9 +63,33 @@ def test_autotune_restores_state_and_applies_a_grid_pair(bp):
         best, times = autotune(h, prob.M, prob.N, prob.K, st.cuda_stream, long_min=(1, 60),
                                shape=(50, 1024))
         assert best in times and len(times) == 4 and all(t > 0 for t in times.values())
+        assert best[2] == 0
         after = bp.bpmf_get_state(h, prob.M, prob.N, prob.K)
         for x, y in zip(before, after):
             np.testing.assert_array_equal(x, y)
+        bp.bpmf_sweep(h, 1)
+        assert bp.bpmf_status(h) == 0
+    finally:
+        bp.bpmf_destroy(h)
+
+
+def test_autotune_split_degree_below_k64(bp):
+    import torch
+
+    from paper_1705_10633_gb300.autotune import autotune
+    prob = workloads.random_small(500, 100, 24, 20000, seed=72, n_test=50, long_rows=3,
+                                  long_deg=90)
+    st = torch.cuda.Stream()
+    h = bp.create_from_problem(prob, stream=st.cuda_stream)
+    try:
+        bp.bpmf_sweep(h, 1)
+        before = bp.bpmf_get_state(h, prob.M, prob.N, prob.K)
+        best, times = autotune(h, prob.M, prob.N, prob.K, st.cuda_stream, split=(32, 1 << 30))
+        assert sorted(times) == [(0, 0, 32), (0, 0, 1 << 30)] and best in times
+        after = bp.bpmf_get_state(h, prob.M, prob.N, prob.K)
+        for x, y in zip(before, after):
+            np.testing.assert_array_equal(x, y)
+        assert (bp.bpmf_info(h, 1)["n_split"] > 0) == (best[2] == 32)
         bp.bpmf_sweep(h, 1)
         assert bp.bpmf_status(h) == 0
     finally:
