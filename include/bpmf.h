@@ -96,6 +96,11 @@ typedef struct {
                              are split into runs of split_degree / 2 ratings done by
                              separate warps (Sec. 3.2), the partial Gram matrices summed
                              in run order by the last warp; <= 0 = default (1024)      */
+    int32_t rank_one_degree; /* rows on the CUDA-core kernel with fewer ratings than this
+                                take the rank-one route (Sec. 3.1): chol(Lambda_X) from the
+                                hyper step updated once per rating, no Gram and no
+                                factorization; 1 = empty rows only, 0 = default (1),
+                                < 0 = none                                             */
     bpmf_alloc_fn alloc; /* NULL = cudaMalloc / cudaFree */
     bpmf_free_fn free;
     void* alloc_ctx;
@@ -149,17 +154,18 @@ int bpmf_sweep(bpmf_handle h, int32_t n_sweeps, double* rmse_sample, double* rms
 int bpmf_sweep_batch(bpmf_handle* hs, int32_t n, int32_t n_sweeps);
 
 /*
- * Change the tuning thresholds of a live handle (long_min_degree, long_shape_degree
- * and split_degree of bpmf_params; <= 0 = library default): the rows of both sides
+ * Change the tuning thresholds of a live handle (long_min_degree, long_shape_degree,
+ * split_degree and rank_one_degree of bpmf_params, each with its meaning of 0 and of
+ * negative values there): the rows of both sides
  * are binned and split again (host sort of the degrees kept from bpmf_create,
  * host-to-device copies waited for; the segment arrays grow when a smaller
  * split_degree needs more, the old ones held until bpmf_destroy).  The chain state
  * is untouched; rows may move between the CUDA-core and tensor-core kernels or
- * between split and whole, whose results agree within the FP32 tolerance, not bit
- * for bit.  For autotuning.  BPMF_ENOMEM / BPMF_ECUDA leave the handle unusable.
+ * between split and whole or between the Gram and rank-one routes, whose results agree
+ * within the FP32 tolerance, not bit for bit.  For autotuning.  BPMF_ENOMEM / BPMF_ECUDA leave the handle unusable.
  */
 int bpmf_set_tuning(bpmf_handle h, int32_t long_min_degree, int32_t long_shape_degree,
-                    int32_t split_degree);
+                    int32_t split_degree, int32_t rank_one_degree);
 
 /* Run one BPMF_PHASE_* step of a sweep (for checking the steps one by one). */
 int bpmf_step(bpmf_handle h, int32_t phase);

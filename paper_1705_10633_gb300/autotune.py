@@ -3,15 +3,17 @@
 The thresholds are the degree from which a row takes the tensor-core kernel
 (below it, the CUDA-core warp-per-row kernel), the mean degree from which a
 tensor-core launch uses the CTA shape with more gather stages and fewer
-factorisation warps, and the degree from which a CUDA-core row is split into
-segments done by separate warps.  At K in 49..64 the first two are tuned (the
-CUDA-core kernel then holds few rows), below that the third.  Each candidate is
-applied to the live handle (`bpmf_set_tuning` bins and splits the rows again),
-the two row phases are run and timed with CUDA events on the handle's stream,
-and the fastest candidate is kept.  The
-chain's factors, hyper-parameters and sweep counter are saved first and
-restored after every trial, so tuning does not move the chain (the row phases
-do not touch the running prediction sums).
+factorisation warps, the degree from which a CUDA-core row is split into
+segments done by separate warps, and the degree below which a CUDA-core row takes
+the rank-one route (Sec. 3.1; the GPU analogue of the paper's measured crossover
+between its per-item methods, Sec. 3.2).  At K in 49..64 the first two are tuned
+together (the CUDA-core kernel then holds few rows); below that the split degree
+is tuned first and the rank-one degree second, at the best split.  Each candidate
+is applied to the live handle (`bpmf_set_tuning` bins and splits the rows again),
+the two row phases are run and timed with CUDA events on the handle's stream, and
+the fastest candidate is kept.  The chain's factors, hyper-parameters and sweep
+counter are saved first and restored after every trial, so tuning does not move
+the chain (the row phases do not touch the running prediction sums).
 """
 from __future__ import annotations
 
@@ -20,39 +22,48 @@ import itertools
 LONG_MIN_CANDIDATES = (1, 16, 48, 128)
 SHAPE_CANDIDATES = (256, 1024, 4096, 1 << 30)
 SPLIT_CANDIDATES = (128, 512, 1024, 4096, 1 << 30)
+RANK_ONE_CANDIDATES = (-1, 2, 4)
 
 
 def autotune(h, M, N, K, stream, long_min=LONG_MIN_CANDIDATES, shape=SHAPE_CANDIDATES,
-             split=SPLIT_CANDIDATES, reps=2):
-    """Returns ((long_min_degree, long_shape_degree, split_degree), {triple: ms for one
-    pass of both row phases}).  `stream` is the raw cudaStream_t the handle was created
-    with.  0 in a triple is the library default."""
+             split=SPLIT_CANDIDATES, rank_one=RANK_ONE_CANDIDATES, reps=2):
+    """Returns ((long_min_degree, long_shape_degree, split_degree, rank_one_degree),
+    {tuple: ms for one pass of both row phases}).  `stream` is the raw cudaStream_t the
+    handle was created with.  0 in a tuple is the library default."""
     import torch
 
     import paper_1705_10633_gb300 as bp
 
-    if (K + 15) // 16 * 16 == 64:
-        grid = [(lm, sd, 0) for lm, sd in itertools.product(long_min, shape)]
-    else:
-        grid = [(0, 0, sp) for sp in split]
     st = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
     U, V, hyper, sweep = bp.bpmf_get_state(h, M, N, K)
     rows = (bp.BPMF_PHASE_ROWS_MOVIE, bp.BPMF_PHASE_ROWS_USER)
     times = {}
-    try:
-        for cand in grid:
-            bp.bpmf_set_tuning(h, *cand)
-            for ph in rows:  # warm-up: launch shapes, caches
+
+    def trial(cand):
+        bp.bpmf_set_tuning(h, *cand)
+        for ph in rows:  # warm-up: launch shapes, caches
+            bp.bpmf_step(h, ph)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            for ph in rows:
                 bp.bpmf_step(h, ph)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            for _ in range(reps):
-                for ph in rows:
-                    bp.bpmf_step(h, ph)
-            e1.record(st)
-            e1.synchronize()
-            times[cand] = e0.elapsed_time(e1) / reps
-            bp.bpmf_set_state(h, U, V, hyper, sweep)
+        e1.record(st)
+        e1.synchronize()
+        times[cand] = e0.elapsed_time(e1) / reps
+        bp.bpmf_set_state(h, U, V, hyper, sweep)
+
+    try:
+        if (K + 15) // 16 * 16 == 64:
+            for lm, sd in itertools.product(long_min, shape):
+                trial((lm, sd, 0, 0))
+        else:
+            for sp in split:
+                trial((0, 0, sp, 0))
+            sp = min(times, key=times.get)[2]
+            for r1 in rank_one:
+                if (0, 0, sp, r1) not in times:
+                    trial((0, 0, sp, r1))
         best = min(times, key=times.get)
         bp.bpmf_set_tuning(h, *best)
     finally:

@@ -20,6 +20,7 @@ namespace {
 constexpr int kDefaultLongMinDegree = 1;
 constexpr int kDefaultLongShapeDegree = 1024;
 constexpr int kDefaultSplitDegree = 1024;
+constexpr int kDefaultRankOneDegree = 1;
 constexpr int kDefaultWaitTimeoutMs = 2000;
 
 struct DevSide {
@@ -40,6 +41,7 @@ struct DevSide {
     Segment* segs = nullptr;
     int64_t n_segs = 0, seg_cap = 0;
     int64_t n_split = 0, split_cap = 0;
+    int64_t n_rank_one = 0;  // last rows of the short bin, on the rank-one route
     float* part = nullptr;           // seg_cap partials
     unsigned int* seg_done = nullptr;  // split_cap counters, zero between launches
     double* mu64 = nullptr;
@@ -62,6 +64,7 @@ struct bpmf_ctx {
     int64_t long_min = 1;            // binning threshold of the tensor-core kernel
     int64_t long_shape_degree = 1024;  // mean degree that selects the many-stage CTA shape
     int64_t split_degree = 1024;  // CUDA-core rows with this many ratings are split
+    int rank_one_max = 0;  // CUDA-core rows with at most this many ratings: rank-one route
     int row_sms = 1;  // CTAs of the row kernels: all SMs, or all but one while the
                       // next hyper step runs beside them (bpmf_sweep)
     cudaStream_t stream = nullptr;
@@ -239,6 +242,10 @@ void bin_rows(int64_t rows, const int64_t* ptr, int64_t long_min, std::vector<in
     *long_ratings = nl_ratings;
 }
 
+// rank_one_degree of bpmf_params (rows with fewer ratings take the rank-one route; 0
+// the default, < 0 none) as the largest degree on that route (-1: none).
+int rank_one_from(int32_t v) { return (v > 0 ? v : (v == 0 ? kDefaultRankOneDegree : 0)) - 1; }
+
 // Segments of the CUDA-core kernel's long rows (Sec. 3.2's split of items with many
 // ratings into smaller parallel tasks): the rows at the head of the short bin (longest
 // first) with at least split_degree ratings are cut into ceil(d / (split_degree / 2))
@@ -281,6 +288,14 @@ int plan_segments(bpmf_ctx* h, DevSide& d, const std::vector<int32_t>& order)
     if (e != cudaSuccess) return BPMF_ECUDA;
     d.n_segs = nsegs;
     d.n_split = nsplit;
+    // the shortest rows (the bin's tail) with at most rank_one_max ratings, never a split row
+    int64_t nr1 = 0;
+    while (nr1 < d.n_short - nsplit) {
+        const int32_t row = order[(size_t)(d.n_short - 1 - nr1)];
+        if (d.ptr_h[(size_t)row + 1] - d.ptr_h[(size_t)row] > h->rank_one_max) break;
+        ++nr1;
+    }
+    d.n_rank_one = nr1;
     return BPMF_OK;
 }
 
@@ -363,6 +378,7 @@ int phase_rows(bpmf_ctx* h, int s)
     a.means = d.means;
     a.lam = d.lam32;
     a.lam_ct = d.lam32 + (size_t)h->kp * h->kp;
+    a.lamchol_ct = d.lam32 + (size_t)2 * h->kp * h->kp;
     a.lammu = d.lammu32;
     a.ctl = h->ctl;
     a.seed = h->p.seed;
@@ -383,11 +399,12 @@ int phase_rows(bpmf_ctx* h, int s)
     a.nsplit = d.n_split;
     a.part = d.part;
     a.seg_done = d.seg_done;
+    a.nrank_one = d.n_rank_one;
     if (a.nrows > 0) {
-        h->launches += 1;
+        h->launches += rows_warp_launches(a);
         e = launch_rows_warp(a, h->kp, h->row_sms, h->stream);
     }
-    a.nsegs = a.nsplit = 0;
+    a.nsegs = a.nsplit = a.nrank_one = 0;
     a.rows = d.bin_rows + d.n_short;
     a.nrows = d.n_long;
     if (e == cudaSuccess && a.nrows > 0) {
@@ -574,6 +591,7 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
     h->long_min = long_min;
     h->long_shape_degree = prm.long_shape_degree > 0 ? prm.long_shape_degree : kDefaultLongShapeDegree;
     h->split_degree = prm.split_degree > 0 ? prm.split_degree : kDefaultSplitDegree;
+    h->rank_one_max = rank_one_from(prm.rank_one_degree);
     const int64_t* hp[2] = {csr_ptr, device_csc ? nullptr : csc_ptr};
     const int32_t* hi[2] = {csr_col, csc_row};
     const float* hv[2] = {csr_val, csc_val};
@@ -593,7 +611,7 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
         bool ok = alloc_n(h, &d.ptr, d.rows + 1) && alloc_n(h, &d.idx, h->nnz) &&
                   alloc_n(h, &d.val, h->nnz) && alloc_n(h, &d.X, (size_t)d.rows * kp) &&
                   alloc_n(h, &d.bin_rows, d.rows) && alloc_n(h, &d.mu64, K) && alloc_n(h, &d.shift64, kp) &&
-                  alloc_n(h, &d.lam64, (size_t)K * K) && alloc_n(h, &d.lam32, (size_t)2 * kp * kp) &&
+                  alloc_n(h, &d.lam64, (size_t)K * K) && alloc_n(h, &d.lam32, (size_t)3 * kp * kp) &&
                   alloc_n(h, &d.lammu32, kp) &&
                   alloc_n(h, &d.partials, (size_t)d.red_blocks * hyper_partial_doubles(kp)) &&
                   alloc_n(h, &d.sums, hyper_partial_doubles(kp)) &&
@@ -644,7 +662,8 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
         if (e == cudaSuccess) e = cudaMemsetAsync(d.mu64, 0, sizeof(double) * K, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(d.lam64, I.data(), sizeof(double) * K * K, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = launch_hyper_refresh(d.mu64, d.lam64, K, kp, d.lam32, d.lammu32, st);
+        if (e == cudaSuccess)
+            e = launch_hyper_refresh(d.mu64, d.lam64, K, kp, d.lam32, d.lammu32, nullptr, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors go out of scope
         if (e != cudaSuccess) rc = BPMF_ECUDA;
     }
@@ -680,9 +699,10 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
 }
 
 int bpmf_set_tuning(bpmf_handle h, int32_t long_min_degree, int32_t long_shape_degree,
-                    int32_t split_degree)
+                    int32_t split_degree, int32_t rank_one_degree)
 {
     if (!h) return BPMF_EINVAL;
+    h->rank_one_max = rank_one_from(rank_one_degree);
     h->long_min = long_min_degree > 0 ? long_min_degree : kDefaultLongMinDegree;
     h->long_shape_degree = long_shape_degree > 0 ? long_shape_degree : kDefaultLongShapeDegree;
     h->split_degree = split_degree > 0 ? split_degree : kDefaultSplitDegree;
@@ -963,7 +983,8 @@ int bpmf_set_state(bpmf_handle h, const float* U, const float* V, const double* 
             if (!rc)
                 rc = cuda_rc(cudaMemcpyAsync(d.lam64, in + K, sizeof(double) * K * K,
                                              cudaMemcpyHostToDevice, st));
-            if (!rc) rc = cuda_rc(launch_hyper_refresh(d.mu64, d.lam64, K, kp, d.lam32, d.lammu32, st));
+            if (!rc)
+                rc = cuda_rc(launch_hyper_refresh(d.mu64, d.lam64, K, kp, d.lam32, d.lammu32, h->ctl, st));
             in += K + K * K;
         }
     }

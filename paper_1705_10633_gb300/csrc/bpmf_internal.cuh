@@ -56,6 +56,9 @@ struct RowArgs {
     const float* lam;      // prior precision, kp x kp, identity beyond K
     const float* lam_ct;   // the same, chunk-transposed: float4 (i, 4c..4c+3) at c * kp + i
     const float* lammu;    // prior precision times prior mean, kp (zero beyond K)
+    const float* lamchol_ct;  // chol(prior precision), lower, chunk-transposed like lam_ct
+    int64_t nrank_one;     // CUDA-core kernel: the last nrank_one rows of the bin (at most
+                           // the rank-one threshold's ratings) take the rank-one route
     Control* ctl;
     uint64_t seed;
     uint32_t c3;           // Philox tag word of this side's row noise
@@ -103,7 +106,8 @@ struct NWArgs {
     double* stats;          // out: mean (K), S (K x K)
     double* mu64;           // out: K    (also the next shift)
     double* lam64;          // out: K x K
-    float* lam32;           // out: kp x kp, identity beyond K, then its chunk-transposed copy
+    float* lam32;           // out: kp x kp, identity beyond K, then its chunk-transposed copy,
+                            // then the chunk-transposed lower Cholesky factor (identity beyond K)
     float* lammu32;         // out: kp
 };
 cudaError_t launch_nw_sample(const NWArgs& a, cudaStream_t s);
@@ -115,10 +119,12 @@ __host__ __device__ inline int chunk_t_index(int i, int j, int kp)
 }
 // FP32 copies of a hyper state given in FP64 (after bpmf_set_state).
 cudaError_t launch_hyper_refresh(const double* mu64, const double* lam64, int K, int kp,
-                                 float* lam32, float* lammu32, cudaStream_t s);
+                                 float* lam32, float* lammu32, Control* ctl, cudaStream_t s);
 
 // Row updates on CUDA cores: one warp per row (any degree).
 cudaError_t launch_rows_warp(const RowArgs& a, int kp, int num_sms, cudaStream_t s);
+// Kernel launches launch_rows_warp makes for `a` (0 to 2).
+int rows_warp_launches(const RowArgs& a);
 // Floats of one segment's partial in `part` (Gram rows owned by a lane, and the
 // right-hand side, lane-interleaved).
 int warp_partial_floats(int kp);

@@ -308,14 +308,17 @@ __global__ void __launch_bounds__(kNWThreads) nw_sample_kernel(NWArgs a)
         M1[e] = s;
     }
     __syncthreads();
-    // ---- mu = mu* + chol(beta* Lambda)^{-T} z ----
-    for (int e = t; e < KK; e += blockDim.x) M2[e] = beta_s * M1[e];
+    // ---- C = chol(Lambda) by the same routine that bpmf_set_state's refresh uses on the
+    // stored Lambda (so a resumed chain's rank-one route sees identical factors), and
+    // mu = mu* + chol(beta* Lambda)^{-T} z = mu* + C^{-T} z / sqrt(beta*) ----
+    for (int e = t; e < KK; e += blockDim.x) M2[e] = M1[e];
     for (int k = t; k < K; k += blockDim.x) z[k] = normal_f64(a.seed, (uint32_t)k, 1u, sweep, a.c3_normal);
     __syncthreads();
     nw_cholesky(M2, K, &bad);
     if (t == 0) {
+        const double rb = 1.0 / sqrt(beta_s);
         for (int i = K - 1; i >= 0; --i) {
-            double s = z[i];
+            double s = z[i] * rb;
             for (int k = i + 1; k < K; ++k) s -= M2[k * K + i] * w[k];
             w[i] = s / M2[i * K + i];
         }
@@ -327,9 +330,13 @@ __global__ void __launch_bounds__(kNWThreads) nw_sample_kernel(NWArgs a)
     const int kp = a.kp;
     for (int e = t; e < kp * kp; e += blockDim.x) {
         const int i = e / kp, j = e % kp;
-        const float v = (i < K && j < K) ? (float)M1[i * K + j] : (i == j ? 1.f : 0.f);
+        const bool in = i < K && j < K;
+        const float v = in ? (float)M1[i * K + j] : (i == j ? 1.f : 0.f);
         a.lam32[e] = v;
         a.lam32[kp * kp + chunk_t_index(i, j, kp)] = v;
+        // chol(Lambda) for the rank-one route
+        const float c = in ? (float)M2[i * K + j] : (i == j ? 1.f : 0.f);
+        a.lam32[2 * kp * kp + chunk_t_index(i, j, kp)] = c;
     }
     for (int i = t; i < kp; i += blockDim.x) {
         double s = 0.0;
@@ -361,14 +368,24 @@ cudaError_t launch_nw_sample(const NWArgs& a, cudaStream_t s)
 }
 
 __global__ void hyper_refresh_kernel(const double* mu64, const double* lam64, int K, int kp,
-                                     float* lam32, float* lammu32)
+                                     float* lam32, float* lammu32, Control* ctl)
 {
+    extern __shared__ double rf_sm[];  // K x K: chol(Lambda) for the rank-one route
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    for (int e = threadIdx.x; e < K * K; e += blockDim.x) rf_sm[e] = lam64[e];
+    __syncthreads();
+    nw_cholesky(rf_sm, K, &bad);
     for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) {
         const int i = e / kp, j = e % kp;
-        const float v = (i < K && j < K) ? (float)lam64[i * K + j] : (i == j ? 1.f : 0.f);
+        const bool in = i < K && j < K;
+        const float v = in ? (float)lam64[i * K + j] : (i == j ? 1.f : 0.f);
         lam32[e] = v;
         lam32[kp * kp + chunk_t_index(i, j, kp)] = v;
+        const float c = in ? (float)rf_sm[i * K + j] : (i == j ? 1.f : 0.f);
+        lam32[2 * kp * kp + chunk_t_index(i, j, kp)] = c;
     }
+    if (threadIdx.x == 0 && bad && ctl) atomicOr(&ctl->status, kStatusNotPD);
     for (int i = threadIdx.x; i < kp; i += blockDim.x) {
         double s = 0.0;
         if (i < K)
@@ -378,9 +395,10 @@ __global__ void hyper_refresh_kernel(const double* mu64, const double* lam64, in
 }
 
 cudaError_t launch_hyper_refresh(const double* mu64, const double* lam64, int K, int kp,
-                                 float* lam32, float* lammu32, cudaStream_t s)
+                                 float* lam32, float* lammu32, Control* ctl, cudaStream_t s)
 {
-    hyper_refresh_kernel<<<1, 256, 0, s>>>(mu64, lam64, K, kp, lam32, lammu32);
+    hyper_refresh_kernel<<<1, 256, sizeof(double) * K * K, s>>>(mu64, lam64, K, kp, lam32,
+                                                                 lammu32, ctl);
     return cudaGetLastError();
 }
 

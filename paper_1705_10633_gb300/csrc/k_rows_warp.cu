@@ -52,6 +52,34 @@ struct WarpLayout {
     static constexpr int PART = (NR1 + NA + 2) * 32;
 };
 
+// One chunk of up to 32 ratings starting at `base`: index and value loads, the
+// gathered rows of Y into the stage (rows >= cnt zero), values into rb.
+template <int KT>
+__device__ __forceinline__ void gather_chunk(const RowArgs& a, int64_t base, int cnt, float* stage,
+                                             float* rb, int lane)
+{
+    using W = WarpLayout<KT>;
+    int c = 0;
+    float r = 0.f;
+    if (lane < cnt) {
+        c = __ldg(a.idx + base + lane);
+        r = __ldg(a.val + base + lane);
+    }
+    rb[lane] = r;
+    const int f = lane % W::F4, sub = lane / W::F4;
+#pragma unroll 4
+    for (int it = 0; it < kChunk / W::RPI; ++it) {
+        const int qq = it * W::RPI + sub;
+        const int cq = __shfl_sync(kFullMask, c, qq & 31);
+        if (sub < W::RPI) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (qq < cnt) v = __ldg(reinterpret_cast<const float4*>(a.Y + (int64_t)cq * a.ldy) + f);
+            reinterpret_cast<float4*>(stage + qq * KT)[f] = v;
+        }
+    }
+    __syncwarp();
+}
+
 // Gram rows i1, i2 and right-hand side entries of ratings [p0, p1), added to the
 // registers (the stage holds 32 gathered rows of Y at a time).
 template <int KT>
@@ -65,27 +93,7 @@ __device__ __forceinline__ void accumulate_ratings(const RowArgs& a, int64_t p0,
     const int i1 = lane, i2 = 63 - lane;
     for (int64_t base = p0; base < p1; base += kChunk) {
         const int cnt = (int)min((int64_t)kChunk, p1 - base);
-        int c = 0;
-        float r = 0.f;
-        if (lane < cnt) {
-            c = __ldg(a.idx + base + lane);
-            r = __ldg(a.val + base + lane);
-        }
-        rb[lane] = r;
-        // gather the chunk's rows of Y into the stage (rows >= cnt are zero)
-        const int f = lane % W::F4, sub = lane / W::F4;
-#pragma unroll 4
-        for (int it = 0; it < kChunk / W::RPI; ++it) {
-            const int qq = it * W::RPI + sub;
-            const int cq = __shfl_sync(kFullMask, c, qq & 31);
-            if (sub < W::RPI) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (qq < cnt)
-                    v = __ldg(reinterpret_cast<const float4*>(a.Y + (int64_t)cq * a.ldy) + f);
-                reinterpret_cast<float4*>(stage + qq * KT)[f] = v;
-            }
-        }
-        __syncwarp();
+        gather_chunk<KT>(a, base, cnt, stage, rb, lane);
         // one rating at a time: row i of the Gram += y[i] * y (lower part used)
 #pragma unroll 2
         for (int qq = 0; qq < cnt; ++qq) {
@@ -106,6 +114,36 @@ __device__ __forceinline__ void accumulate_ratings(const RowArgs& a, int64_t p0,
                     if (W::TWO) a2[W::TWO ? j : 0] = fmaf(x2, yv[u], a2[W::TWO ? j : 0]);
                 }
             }
+        }
+        __syncwarp();
+    }
+}
+
+// Rank-one route (Sec. 3.1, Sec. 3.2: cheaper for items with few ratings): a1 / a2
+// start as the lane's rows of chol(Lambda_X) and take one rank-one update with
+// sqrt(alpha) y per rating of [p0, p1); the right-hand side accumulates as on the
+// Gram route.
+template <int KT>
+__device__ __forceinline__ void rank_one_ratings(const RowArgs& a, int64_t p0, int64_t p1,
+                                                 float* stage, float* rb, int lane, bool v1,
+                                                 bool v2, float (&a1)[RowRegs<KT>::NR1],
+                                                 float (&a2)[RowRegs<KT>::NA2], float& rhs1,
+                                                 float& rhs2, bool& bad)
+{
+    const int i1 = lane, i2 = 63 - lane;
+    const float sqa = sqrtf(a.alpha);
+    for (int64_t base = p0; base < p1; base += kChunk) {
+        const int cnt = (int)min((int64_t)kChunk, p1 - base);
+        gather_chunk<KT>(a, base, cnt, stage, rb, lane);
+#pragma unroll 1
+        for (int qq = 0; qq < cnt; ++qq) {
+            const float* srow = stage + qq * KT;
+            const float rq = rb[qq];
+            const float y1 = v1 ? srow[i1] : 0.f;
+            const float y2 = v2 ? srow[i2] : 0.f;
+            rhs1 = fmaf(rq, y1, rhs1);
+            rhs2 = fmaf(rq, y2, rhs2);
+            warp_rank_one<KT>(a1, a2, sqa * y1, sqa * y2, lane, bad);
         }
         __syncwarp();
     }
@@ -139,7 +177,10 @@ __device__ __forceinline__ void add_partial(const float* pp, int lane, float (&a
     rhs2 += __ldcg(pp + (W::NR1 + W::NA + 1) * 32 + lane);
 }
 
-template <int KT>
+// kR1 = false: the segments of the split rows, then rows nsplit .. nrows - nrank_one - 1
+// of the bin on the Gram route; kR1 = true: the last nrank_one rows (the shortest) on
+// the rank-one route.  Two instantiations keep each route's register budget its own.
+template <int KT, bool kR1>
 __global__ void __launch_bounds__(kWarpsPerCta * 32) rows_warp_kernel(RowArgs a)
 {
     using W = WarpLayout<KT>;
@@ -162,7 +203,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) rows_warp_kernel(RowArgs a)
     const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerCta;
     bool bad = false;
 
-    const int64_t nitems = a.nsegs + a.nrows - a.nsplit;
+    const int64_t nitems = kR1 ? a.nrank_one : a.nsegs + a.nrows - a.nsplit - a.nrank_one;
     for (int64_t q = (int64_t)blockIdx.x * kWarpsPerCta + wib; q < nitems; q += nwarps) {
         // Gram rows i1, i2 accumulate in the registers the Cholesky works on
         float a1[RowRegs<KT>::NR1];
@@ -172,18 +213,43 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) rows_warp_kernel(RowArgs a)
 #pragma unroll
         for (int j = 0; j < (W::TWO ? KT : 1); ++j) a2[j] = 0.f;
         float rhs1 = 0.f, rhs2 = 0.f;
-        const bool is_seg = q < a.nsegs;
+        const bool is_seg = !kR1 && q < a.nsegs;
         int row = 0;
         int64_t p0, p1;
         if (is_seg) {
             p0 = __ldg(&a.segs[q].lo);
             p1 = __ldg(&a.segs[q].hi);
         } else {
-            row = a.rows[a.nsplit + (q - a.nsegs)];
+            row = kR1 ? a.rows[a.nrows - a.nrank_one + q] : a.rows[a.nsplit + (q - a.nsegs)];
             p0 = a.ptr[row];
             p1 = a.ptr[row + 1];
         }
-        accumulate_ratings<KT>(a, p0, p1, stage, rb, lane, v1, v2, a1, a2, rhs1, rhs2);
+        constexpr bool rank_one = kR1;
+        const float4* lct = reinterpret_cast<const float4*>(rank_one ? a.lamchol_ct : a.lam_ct);
+        if constexpr (rank_one) {
+            // the lane's rows of chol(Lambda_X) (chunk-transposed: coalesced float4 loads)
+#pragma unroll
+            for (int c = 0; c < W::NR1 / 4; ++c) {
+                const float4 l4 = v1 ? __ldg(lct + c * KT + (v1 ? i1 : 0)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                a1[4 * c + 0] = v1 ? l4.x : (4 * c == 0 ? 1.f : 0.f);
+                a1[4 * c + 1] = l4.y;
+                a1[4 * c + 2] = l4.z;
+                a1[4 * c + 3] = l4.w;
+            }
+            if (W::TWO) {
+#pragma unroll
+                for (int c = 0; c < KT / 4; ++c) {
+                    const float4 l4 =
+                        v2 ? __ldg(lct + c * KT + (v2 ? i2 : 0)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) a2[W::TWO ? 4 * c + u : 0] = lv[u];
+                }
+            }
+            rank_one_ratings<KT>(a, p0, p1, stage, rb, lane, v1, v2, a1, a2, rhs1, rhs2, bad);
+        } else {
+            accumulate_ratings<KT>(a, p0, p1, stage, rb, lane, v1, v2, a1, a2, rhs1, rhs2);
+        }
         if (is_seg) {
             store_partial<KT>(a.part + q * W::PART, lane, a1, a2, rhs1, rhs2);
             const Segment* sg = a.segs + q;
@@ -205,47 +271,69 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) rows_warp_kernel(RowArgs a)
             if (lane == 0) a.seg_done[slot] = 0u;  // ready for the next launch
             row = __ldg(&sg->row);
         }
-        // Lambda_i rows = Lambda_X rows + alpha * Gram rows; b = alpha * rhs + Lambda_X mu_X
+        // Gram route: Lambda_i rows = Lambda_X rows + alpha * Gram rows.  Lambda_X comes
+        // from its chunk-transposed copy (float4 (i, 4c..4c+3) at c * KT + i): the lanes'
+        // loads of one chunk are consecutive 16-B words, not 32 rows apart.
+        if constexpr (!rank_one) {
 #pragma unroll
-        for (int j = 0; j < W::NR1; ++j)
-            a1[j] = v1 ? fmaf(a.alpha, a1[j], __ldg(a.lam + i1 * KT + j)) : (j == 0 ? 1.f : 0.f);
-        if (W::TWO) {
+            for (int c = 0; c < W::NR1 / 4; ++c) {
+                const float4 l4 = v1 ? __ldg(lct + c * KT + (v1 ? i1 : 0)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
-            for (int j = 0; j < KT; ++j)
-                a2[W::TWO ? j : 0] = v2 ? fmaf(a.alpha, a2[W::TWO ? j : 0], __ldg(a.lam + i2 * KT + j))
-                                        : 0.f;
+                for (int u = 0; u < 4; ++u) {
+                    const int j = 4 * c + u;
+                    a1[j] = v1 ? fmaf(a.alpha, a1[j], lv[u]) : (j == 0 ? 1.f : 0.f);
+                }
+            }
+            if (W::TWO) {
+#pragma unroll
+                for (int c = 0; c < KT / 4; ++c) {
+                    const float4 l4 =
+                        v2 ? __ldg(lct + c * KT + (v2 ? i2 : 0)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = W::TWO ? 4 * c + u : 0;
+                        a2[j] = v2 ? fmaf(a.alpha, a2[j], lv[u]) : 0.f;
+                    }
+                }
+            }
         }
+        // b = alpha * rhs + Lambda_X mu_X
         float b1 = v1 ? fmaf(a.alpha, rhs1, __ldg(a.lammu + i1)) : 0.f;
         float b2 = v2 ? fmaf(a.alpha, rhs2, __ldg(a.lammu + i2)) : 0.f;
 
+        if constexpr (rank_one) warp_forward<KT>(a1, a2, b1, b2, dinv, lane);
+        else warp_factor<KT>(a1, a2, b1, b2, colbuf, dinv, lane, bad);
         float x1, x2, m1, m2;
-        factor_solve_sample<KT>(a1, a2, b1, b2, colbuf, dinv, zb, sq, lane, a.K, a.seed,
-                                (uint32_t)row, sweep, a.c3, a.means != nullptr, x1, x2, m1, m2, bad);
+        warp_sample_tail<KT>(a1, a2, b1, b2, dinv, zb, sq, lane, a.K, a.seed, (uint32_t)row, sweep,
+                             a.c3, a.means != nullptr, x1, x2, m1, m2);
         store_row<KT>(a, row, lane, x1, x2, m1, m2);
         __syncwarp();
     }
     if (bad && lane == 0) atomicOr(&a.ctl->status, kStatusNotPD);
 }
 
-template <int KT>
-static cudaError_t launch_kt(const RowArgs& a, int num_sms, cudaStream_t s)
+template <int KT, bool kR1>
+static cudaError_t launch_route(const RowArgs& a, int num_sms, cudaStream_t s)
 {
     using W = WarpLayout<KT>;
+    const int64_t nitems = kR1 ? a.nrank_one : a.nsegs + a.nrows - a.nsplit - a.nrank_one;
+    if (nitems <= 0) return cudaSuccess;
     const size_t smem = sizeof(float) * (size_t)W::PER_WARP_ALIGNED * kWarpsPerCta;
-    cudaError_t e = cudaFuncSetAttribute(rows_warp_kernel<KT>,
+    cudaError_t e = cudaFuncSetAttribute(rows_warp_kernel<KT, kR1>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_warp_kernel<KT>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_warp_kernel<KT, kR1>,
                                                       kWarpsPerCta * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    const int64_t nitems = a.nsegs + a.nrows - a.nsplit;
     int64_t need = (nitems + kWarpsPerCta - 1) / kWarpsPerCta;
     int64_t grid = (int64_t)num_sms * per_sm;
     if (need < grid) grid = need;
     if (grid < 1) return cudaSuccess;
-    rows_warp_kernel<KT><<<(unsigned)grid, kWarpsPerCta * 32, smem, s>>>(a);
+    rows_warp_kernel<KT, kR1><<<(unsigned)grid, kWarpsPerCta * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -259,9 +347,17 @@ int warp_partial_floats(int kp)
     }
 }
 
+// The Gram-route launch, then the rank-one launch (each skipped when it has no work).
+template <int KT>
+static cudaError_t launch_kt(const RowArgs& a, int num_sms, cudaStream_t s)
+{
+    cudaError_t e = launch_route<KT, false>(a, num_sms, s);
+    if (e == cudaSuccess) e = launch_route<KT, true>(a, num_sms, s);
+    return e;
+}
+
 cudaError_t launch_rows_warp(const RowArgs& a, int kp, int num_sms, cudaStream_t s)
 {
-    if (a.nsegs + a.nrows - a.nsplit <= 0) return cudaSuccess;
     switch (kp) {
     case 16: return launch_kt<16>(a, num_sms, s);
     case 32: return launch_kt<32>(a, num_sms, s);
@@ -269,6 +365,11 @@ cudaError_t launch_rows_warp(const RowArgs& a, int kp, int num_sms, cudaStream_t
     case 64: return launch_kt<64>(a, num_sms, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+int rows_warp_launches(const RowArgs& a)
+{
+    return (a.nsegs + a.nrows - a.nsplit - a.nrank_one > 0 ? 1 : 0) + (a.nrank_one > 0 ? 1 : 0);
 }
 
 }  // namespace bpmf

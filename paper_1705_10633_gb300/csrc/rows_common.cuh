@@ -46,82 +46,186 @@ struct RowRegs {
     static constexpr int LD = KT + 1;              // row stride of the square buffer
 };
 
-// colbuf: 2*KT floats, dinv: KT, zb: KT, sq: KT x LD (L is written here for the back solve).
+// Pivot work of column k (a compile-time index once the caller's loop is unrolled)
+// for the warp layout (rows i1 = lane, i2 = 63 - lane): scales the lane's entries of
+// column k into L[r][k] (the diagonal owner gets L[k][k]), returns them in l1 / l2
+// (zero above the diagonal), applies y_k to the right-hand side (forward solve
+// fused: b_k becomes y_k, rows below lose L[r][k] y_k), writes 1 / L[k][k] to dinv
+// and publishes the column in the buffer of k's parity.  Selects, not branches.
 template <int KT>
-__device__ __forceinline__ void factor_solve_sample(float (&a1)[RowRegs<KT>::NR1],
-                                                    float (&a2)[RowRegs<KT>::NA2], float b1,
-                                                    float b2, float* colbuf, float* dinv,
-                                                    float* zb, float* sq, int lane, int K,
-                                                    uint64_t seed, uint32_t row, uint32_t sweep,
-                                                    uint32_t c3, bool want_means, float& x1,
-                                                    float& x2, float& m1, float& m2, bool& bad)
+__device__ __forceinline__ void warp_pivot(int k, float (&a1)[RowRegs<KT>::NR1],
+                                           float (&a2)[RowRegs<KT>::NA2], float& b1, float& b2,
+                                           float& l1, float& l2, float* colbuf, float* dinv,
+                                           int lane, bool v1, bool v2, bool& bad)
 {
     using R = RowRegs<KT>;
     const int i1 = lane, i2 = 63 - lane;
-    const bool v1 = i1 < KT;
-    const bool v2 = R::TWO && i2 < KT;
+    float* cb = colbuf + (k & 1) * KT;
+    const int owner = k < 32 ? k : 63 - k;
+    const float pv = k < R::NR1 ? a1[k < R::NR1 ? k : 0] : a2[R::TWO ? k : 0];
+    float piv = __shfl_sync(kFullMask, pv, owner);
+    const float bk = __shfl_sync(kFullMask, k < 32 ? b1 : b2, owner);
+    if (!(piv > 0.f && piv < INFINITY)) {  // also catches NaN
+        bad = true;
+        piv = 1.f;
+    }
+    const float rinv = rsqrtf(piv);
+    const float yk = bk * rinv;
+    if (lane == 0) dinv[k] = rinv;
+    l1 = l2 = 0.f;
+    if (k < R::NR1) {
+        const int kk = k < R::NR1 ? k : 0;
+        const bool below = i1 > k;
+        a1[kk] = below ? a1[kk] * rinv : (i1 == k ? piv * rinv : a1[kk]);
+        l1 = below ? a1[kk] : 0.f;
+        b1 = below ? fmaf(-l1, yk, b1) : (i1 == k ? yk : b1);
+        if (below && v1) cb[i1] = l1;
+    }
+    if (R::TWO) {
+        const int kk = R::TWO ? k : 0;
+        const bool below = i2 > k;
+        a2[kk] = below ? a2[kk] * rinv : (i2 == k ? piv * rinv : a2[kk]);
+        l2 = below ? a2[kk] : 0.f;
+        b2 = below ? fmaf(-l2, yk, b2) : (i2 == k ? yk : b2);
+        if (below && v2) cb[i2] = l2;
+    }
+}
 
-    // ---- right-looking Cholesky; column k is published through shared memory
+// Right-looking Cholesky of the lane's two register rows (rows i1 = lane, i2 = 63 -
+// lane of Lambda_i) with the forward solve fused: on return a1 / a2 hold the rows of
+// L, b1 / b2 the entries of y = L^{-1} b, dinv the inverse diagonal.  Step k first
+// updates column k + 1 and does its pivot work, then the rest of its update (the
+// next pivot's latency overlaps this step's FMAs).  colbuf: 2*KT floats.
+template <int KT>
+__device__ __forceinline__ void warp_factor(float (&a1)[RowRegs<KT>::NR1],
+                                            float (&a2)[RowRegs<KT>::NA2], float& b1, float& b2,
+                                            float* colbuf, float* dinv, int lane, bool& bad)
+{
+    using R = RowRegs<KT>;
+    const bool v1 = lane < KT;
+    const bool v2 = R::TWO && 63 - lane < KT;
+    float l1, l2;
+    warp_pivot<KT>(0, a1, a2, b1, b2, l1, l2, colbuf, dinv, lane, v1, v2, bad);
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
-        float* cb = colbuf + (k & 1) * KT;
-        const int owner = k < 32 ? k : 63 - k;
-        float pv;
-        if (k < R::NR1) pv = a1[k < R::NR1 ? k : 0];
-        else pv = a2[R::TWO ? k : 0];
-        float piv = __shfl_sync(kFullMask, pv, owner);
-        if (!(piv > 0.f && piv < INFINITY)) {  // also catches NaN
-            bad = true;
-            piv = 1.f;
+        __syncwarp();  // column k of L is in its buffer
+        const float* cb = colbuf + (k & 1) * KT;
+        float nl1 = 0.f, nl2 = 0.f;
+        if (k + 1 < KT) {
+            const int j = k + 1;
+            const float c = cb[j];
+            if (j < R::NR1) a1[j < R::NR1 ? j : 0] = fmaf(-l1, c, a1[j < R::NR1 ? j : 0]);
+            if (R::TWO) a2[R::TWO ? j : 0] = fmaf(-l2, c, a2[R::TWO ? j : 0]);
+            warp_pivot<KT>(j, a1, a2, b1, b2, nl1, nl2, colbuf, dinv, lane, v1, v2, bad);
         }
-        const float rinv = rsqrtf(piv);
-        if (lane == 0) dinv[k] = rinv;
-        float l1 = 0.f, l2 = 0.f;
-        if (k < R::NR1) {
-            const int kk = k < R::NR1 ? k : 0;
-            if (i1 > k) a1[kk] *= rinv;
-            else if (i1 == k) a1[kk] = piv * rinv;
-            l1 = a1[kk];
-            if (i1 > k && v1) cb[i1] = l1;
-        }
-        if (R::TWO) {
-            const int kk = R::TWO ? k : 0;
-            if (i2 > k) a2[kk] *= rinv;
-            else if (i2 == k) a2[kk] = piv * rinv;
-            l2 = a2[kk];
-            if (i2 > k && v2) cb[i2] = l2;
-        }
-        __syncwarp();
 #pragma unroll
-        for (int j4 = ((k + 1) / 4) * 4; j4 < KT; j4 += 4) {
+        for (int j4 = ((k + 2) / 4) * 4; j4 < KT; j4 += 4) {
             const float4 cv = *reinterpret_cast<const float4*>(cb + j4);
             const float cj[4] = {cv.x, cv.y, cv.z, cv.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int j = j4 + u;
-                if (j > k) {
+                if (j > k + 1) {
                     if (j < R::NR1) a1[j < R::NR1 ? j : 0] = fmaf(-l1, cj[u], a1[j < R::NR1 ? j : 0]);
                     if (R::TWO) a2[R::TWO ? j : 0] = fmaf(-l2, cj[u], a2[R::TWO ? j : 0]);
                 }
             }
         }
+        l1 = nl1;
+        l2 = nl2;
     }
 
-    // ---- forward substitution y = L^{-1} b (in place in b1, b2)
+}
+
+// Rank-one update (Sec. 3.1: for few ratings the factor of the prior precision is
+// updated instead of factoring the Gram): L L^T + x x^T = L' L'^T for lower L with a
+// positive diagonal, one Givens rotation per column (the classical LINPACK-style
+// update): r = sqrt(L_kk^2 + x_k^2), c = L_kk / r, s = x_k / r, L'_kk = r and for rows
+// i > k  L'_ik = c L_ik + s x_i,  x_i <- c x_i - s L_ik.  Rows as in warp_factor; x1 / x2
+// are the lane's entries of x (consumed).
+template <int KT>
+__device__ __forceinline__ void warp_rank_one(float (&a1)[RowRegs<KT>::NR1],
+                                              float (&a2)[RowRegs<KT>::NA2], float x1, float x2,
+                                              int lane, bool& bad)
+{
+    using R = RowRegs<KT>;
+    const int i1 = lane, i2 = 63 - lane;
 #pragma unroll
     for (int k = 0; k < KT; ++k) {
         const int owner = k < 32 ? k : 63 - k;
-        const float bk = __shfl_sync(kFullMask, k < 32 ? b1 : b2, owner);
-        const float yk = bk * dinv[k];
+        const float lk = k < R::NR1 ? a1[k < R::NR1 ? k : 0] : a2[R::TWO ? k : 0];
+        float lkk = __shfl_sync(kFullMask, lk, owner);
+        const float xk = __shfl_sync(kFullMask, k < 32 ? x1 : x2, owner);
+        if (!(lkk > 0.f && lkk < INFINITY)) {  // also catches NaN
+            bad = true;
+            lkk = 1.f;
+        }
+        const float q = fmaf(lkk, lkk, xk * xk);
+        const float rinv = rsqrtf(q);
+        const float c = lkk * rinv, sn = xk * rinv, r = q * rinv;
         if (k < R::NR1) {
-            if (i1 == k) b1 = yk;
-            else if (i1 > k) b1 = fmaf(-a1[k < R::NR1 ? k : 0], yk, b1);
+            const int kk = k < R::NR1 ? k : 0;
+            const float t = a1[kk];
+            const bool below = i1 > k;
+            a1[kk] = below ? fmaf(c, t, sn * x1) : (i1 == k ? r : t);
+            x1 = below ? fmaf(c, x1, -sn * t) : x1;
         }
         if (R::TWO) {
-            if (i2 == k) b2 = yk;
-            else if (i2 > k) b2 = fmaf(-a2[R::TWO ? k : 0], yk, b2);
+            const int kk = R::TWO ? k : 0;
+            const float t = a2[kk];
+            const bool below = i2 > k;
+            a2[kk] = below ? fmaf(c, t, sn * x2) : (i2 == k ? r : t);
+            x2 = below ? fmaf(c, x2, -sn * t) : x2;
         }
     }
+}
+
+// Forward solve y = L^{-1} b on the lane's register rows of L (b1 / b2 become y),
+// writing the inverse diagonal to dinv.
+template <int KT>
+__device__ __forceinline__ void warp_forward(const float (&a1)[RowRegs<KT>::NR1],
+                                             const float (&a2)[RowRegs<KT>::NA2], float& b1,
+                                             float& b2, float* dinv, int lane)
+{
+    using R = RowRegs<KT>;
+    const int i1 = lane, i2 = 63 - lane;
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+        const int owner = k < 32 ? k : 63 - k;
+        const float lk = k < R::NR1 ? a1[k < R::NR1 ? k : 0] : a2[R::TWO ? k : 0];
+        const float lkk = __shfl_sync(kFullMask, lk, owner);
+        const float bk = __shfl_sync(kFullMask, k < 32 ? b1 : b2, owner);
+        const float rinv = __frcp_rn(lkk);
+        const float yk = bk * rinv;
+        if (lane == 0) dinv[k] = rinv;
+        if (k < R::NR1) {
+            const float l = a1[k < R::NR1 ? k : 0];
+            b1 = i1 > k ? fmaf(-l, yk, b1) : (i1 == k ? yk : b1);
+        }
+        if (R::TWO) {
+            const float l = a2[R::TWO ? k : 0];
+            b2 = i2 > k ? fmaf(-l, yk, b2) : (i2 == k ? yk : b2);
+        }
+    }
+}
+
+// After the factor and forward solve (a1 / a2 = rows of L, b1 / b2 = y, dinv):
+// x = L^{-T} (y + z) with z ~ N(0, I) from the row's Philox stream, and the
+// conditional mean L^{-T} y.  zb: KT floats, sq: KT x LD (L is written here for the
+// back solve).
+template <int KT>
+__device__ __forceinline__ void warp_sample_tail(const float (&a1)[RowRegs<KT>::NR1],
+                                                 const float (&a2)[RowRegs<KT>::NA2], float b1,
+                                                 float b2, const float* dinv, float* zb,
+                                                 float* sq, int lane, int K, uint64_t seed,
+                                                 uint32_t row, uint32_t sweep, uint32_t c3,
+                                                 bool want_means, float& x1, float& x2,
+                                                 float& m1, float& m2)
+{
+    using R = RowRegs<KT>;
+    const int i1 = lane, i2 = 63 - lane;
+    const bool v1 = i1 < KT;
+    const bool v2 = R::TWO && i2 < KT;
     // ---- noise z (zero beyond K) and L into the square buffer for the back solve
     if (lane < KT / 4) {
         const float4 z4 = normals4_f32(seed, (uint32_t)lane, row, sweep, c3);
@@ -145,38 +249,52 @@ __device__ __forceinline__ void factor_solve_sample(float (&a1)[RowRegs<KT>::NR1
     float n1 = b1, n2 = b2;
 
     // ---- back substitution x = L^{-T} t (and the mean from y alone); no register
-    // indexing here, so the loop is only partly unrolled (keeps register pressure low)
+    // indexing here, so the loop is only partly unrolled (keeps register pressure low).
+    // Selects, not branches: the update of a row on or below i is computed and
+    // dropped (its L entry is read from a clamped in-range index).
+    const bool u1 = v1, u2 = v2;
 #pragma unroll 4
     for (int i = KT - 1; i >= 0; --i) {
         const int owner = i < 32 ? i : 63 - i;
         const float di = dinv[i];
         const float ui = __shfl_sync(kFullMask, i < 32 ? t1 : t2, owner) * di;
-        float mi = 0.f;
-        if (want_means) mi = __shfl_sync(kFullMask, i < 32 ? n1 : n2, owner) * di;
         const float* Lrow = sq + i * R::LD;
-        if (i1 == i) {
-            t1 = ui;
-            n1 = mi;
-        } else if (i1 < i && v1) {
-            const float l = Lrow[i1];
-            t1 = fmaf(-l, ui, t1);
-            n1 = fmaf(-l, mi, n1);
-        }
+        const bool lo1 = u1 && i1 < i;
+        const float la = Lrow[lo1 ? i1 : 0];
+        t1 = i1 == i ? ui : (lo1 ? fmaf(-la, ui, t1) : t1);
+        float lb = 0.f;
+        bool lo2 = false;
         if (R::TWO) {
-            if (i2 == i) {
-                t2 = ui;
-                n2 = mi;
-            } else if (i2 < i && v2) {
-                const float l = Lrow[i2];
-                t2 = fmaf(-l, ui, t2);
-                n2 = fmaf(-l, mi, n2);
-            }
+            lo2 = u2 && i2 < i;
+            lb = Lrow[lo2 ? i2 : 0];
+            t2 = i2 == i ? ui : (lo2 ? fmaf(-lb, ui, t2) : t2);
+        }
+        if (want_means) {
+            const float mi = __shfl_sync(kFullMask, i < 32 ? n1 : n2, owner) * di;
+            n1 = i1 == i ? mi : (lo1 ? fmaf(-la, mi, n1) : n1);
+            if (R::TWO) n2 = i2 == i ? mi : (lo2 ? fmaf(-lb, mi, n2) : n2);
         }
     }
     x1 = t1;
     x2 = t2;
     m1 = n1;
     m2 = n2;
+}
+
+// Factor, forward solve and sample (the Gram route): colbuf 2*KT floats, dinv KT,
+// zb KT, sq KT x LD.
+template <int KT>
+__device__ __forceinline__ void factor_solve_sample(float (&a1)[RowRegs<KT>::NR1],
+                                                    float (&a2)[RowRegs<KT>::NA2], float b1,
+                                                    float b2, float* colbuf, float* dinv,
+                                                    float* zb, float* sq, int lane, int K,
+                                                    uint64_t seed, uint32_t row, uint32_t sweep,
+                                                    uint32_t c3, bool want_means, float& x1,
+                                                    float& x2, float& m1, float& m2, bool& bad)
+{
+    warp_factor<KT>(a1, a2, b1, b2, colbuf, dinv, lane, bad);
+    warp_sample_tail<KT>(a1, a2, b1, b2, dinv, zb, sq, lane, K, seed, row, sweep, c3, want_means,
+                         x1, x2, m1, m2);
 }
 
 // ---------------------------------------------------------------------------
@@ -200,69 +318,96 @@ __device__ __forceinline__ float4 ld_chunk(const float* M, int i, int c)
     return *reinterpret_cast<const float4*>(M + i * 64 + ((c ^ (i & 7)) << 2));
 }
 
-// Column steps k0 .. k1 - 1 of a right-looking Cholesky with the forward solve
-// fused, for K = 64 with lane l owning rows r1 = l and r2 = 32 + l.  The rows are
-// kept in registers "shifted": a1[t] = A[r1][k + t] and a2[t] = A[r2][k + t] at step
-// k, so the update  A[r][k+1+t] -= L[r][k] L[k+1+t][k]  also slides each row by
-// one (a[t] = a[t+1] - l c[t]) and every register index stays static in a rolled
-// loop.  N1 / N2: entries of a1 / a2 still inside the matrix (N1 = 0 once the
-// rows r1 are finished).  The strictly lower part of L is written transposed into
-// M (row k of M receives column k of L: a conflict-free row store), the inverse
-// diagonal into dinv; the pivot column is broadcast through cbuf (two 64-float
-// buffers, by step parity).
+
+// Pivot work of column j of a right-looking Cholesky with the forward solve fused,
+// for K = 64 with lane l owning rows r1 = l and r2 = 32 + l; p1 / p2 are the lane's
+// entries A[r1][j] / A[r2][j] after the updates of columns 0 .. j-1.  Gives the
+// lane's L[r][j] in l1 / l2 (zero on and above the diagonal), applies y_j to the
+// right-hand side (b_j becomes y_j = b_j / L[j][j], rows below lose L[r][j] y_j),
+// writes 1 / L[j][j] to dinv, column j of L transposed into row j of M (a
+// conflict-free row store) and into the column buffer of j's parity.  Branch-free
+// apart from the predicated stores.  HAS1 = false once the rows r1 are finished.
+template <bool HAS1>
+__device__ __forceinline__ void chol_pivot(int j, float p1, float p2, float& b1, float& b2,
+                                           float& l1, float& l2, float* M, float* cbuf,
+                                           float* dinv, int lane, bool& bad)
+{
+    const int r1 = lane, r2 = 32 + lane;
+    const int owner = j & 31;
+    float piv = __shfl_sync(kFullMask, (HAS1 && j < 32) ? p1 : p2, owner);
+    const float bk = __shfl_sync(kFullMask, (HAS1 && j < 32) ? b1 : b2, owner);
+    if (!(piv > 0.f && piv < INFINITY)) {  // also catches NaN
+        bad = true;
+        piv = 1.f;
+    }
+    const float rinv = rsqrtf(piv);
+    const float yk = bk * rinv;
+    if (lane == 0) dinv[j] = rinv;
+    float* cb = cbuf + (j & 1) * 64;
+    l1 = 0.f;
+    if (HAS1) {
+        const bool below = r1 > j;
+        l1 = below ? p1 * rinv : 0.f;
+        b1 = below ? fmaf(-l1, yk, b1) : (r1 == j ? yk : b1);
+        if (below) {
+            M[sw64(j, r1)] = l1;
+            cb[r1 - j - 1] = l1;
+        }
+    }
+    const bool below2 = r2 > j;
+    l2 = below2 ? p2 * rinv : 0.f;
+    b2 = below2 ? fmaf(-l2, yk, b2) : (r2 == j ? yk : b2);
+    if (below2) {
+        M[sw64(j, r2)] = l2;
+        cb[r2 - j - 1] = l2;
+    }
+}
+
+// Column steps k0 .. k1 - 1 (the pivot work of column k0 already done: l1 / l2 hold
+// the lane's L[r][k0] and cbuf its column).  The rows are kept in registers
+// "shifted": a1[t] = A[r1][k + t] and a2[t] = A[r2][k + t] at step k, so the update
+// A[r][k+1+t] -= L[r][k] L[k+1+t][k]  also slides each row by one
+// (a[t] = a[t+1] - l c[t]) and every register index stays static in a rolled loop.
+// Lookahead: step k first updates the entries of column k + 1 and does that
+// column's pivot work, then the rest of its update, so the pivot's shuffle /
+// rsqrt / store / sync latency overlaps the bulk of the step's FMAs (same
+// arithmetic, same results).  The column buffer is double-buffered by parity.
+// N1 / N2: entries of a1 / a2 still inside the matrix (N1 = 0 once the rows r1 are
+// finished); entries past the matrix are stale and only ever reach register
+// entries past the matrix.
 template <int N1, int N2>
 __device__ __forceinline__ void chol_shifted_steps(float (&a1)[32], float (&a2)[64], float& b1,
-                                                   float& b2, int k0, int k1, float* M,
-                                                   float* cbuf, float* dinv, int lane, bool& bad)
+                                                   float& b2, float& l1, float& l2, int k0,
+                                                   int k1, float* M, float* cbuf, float* dinv,
+                                                   int lane, bool& bad)
 {
     static_assert(N1 % 4 == 0 && N2 % 4 == 0 && N2 > 0, "step shape");
-    const int r1 = lane, r2 = 32 + lane;
 #pragma unroll 1
     for (int k = k0; k < k1; ++k) {
-        const int owner = k & 31;
-        float piv = __shfl_sync(kFullMask, N1 > 0 ? a1[0] : a2[0], owner);
-        const float bk = __shfl_sync(kFullMask, N1 > 0 ? b1 : b2, owner);
-        if (!(piv > 0.f && piv < INFINITY)) {  // also catches NaN
-            bad = true;
-            piv = 1.f;
-        }
-        const float rinv = rsqrtf(piv);
-        const float yk = bk * rinv;
-        if (lane == 0) dinv[k] = rinv;
-        float* cb = cbuf + (k & 1) * 64;
-        float l1 = 0.f, l2 = 0.f;
-        if (N1 > 0) {
-            if (r1 == k) {
-                b1 = yk;
-            } else if (r1 > k) {
-                l1 = a1[0] * rinv;
-                M[sw64(k, r1)] = l1;
-                b1 = fmaf(-l1, yk, b1);
-                cb[r1 - k - 1] = l1;
-            }
-        }
-        if (r2 == k) {
-            b2 = yk;
-        } else if (r2 > k) {
-            l2 = a2[0] * rinv;
-            M[sw64(k, r2)] = l2;
-            b2 = fmaf(-l2, yk, b2);
-            cb[r2 - k - 1] = l2;
-        }
-        __syncwarp();
-        // cb[t] = L[k + 1 + t][k]; entries past the matrix are stale and only ever
-        // reach register entries past the matrix
+        __syncwarp();  // column k of L is in its buffer
+        const float* cb = cbuf + (k & 1) * 64;
+        const float4 c0 = *reinterpret_cast<const float4*>(cb);
+        const float n1 = N1 > 1 ? fmaf(-l1, c0.x, a1[1]) : 0.f;
+        const float n2 = fmaf(-l2, c0.x, a2[1]);
+        float nl1 = 0.f, nl2 = 0.f;
 #pragma unroll
         for (int t4 = 0; t4 < N2; t4 += 4) {
-            const float4 c = *reinterpret_cast<const float4*>(cb + t4);
+            const float4 c = t4 == 0 ? c0 : *reinterpret_cast<const float4*>(cb + t4);
             const float cv[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int t = t4 + u;
+                if (t == 0) continue;
                 if (t + 1 < N2) a2[t] = fmaf(-l2, cv[u], a2[t + 1]);
                 if (t + 1 < N1) a1[t] = fmaf(-l1, cv[u], a1[t + 1]);
             }
+            if ((t4 == 4 || (t4 == 0 && N2 == 4)) && k + 1 < 64)
+                chol_pivot<(N1 > 1)>(k + 1, n1, n2, b1, b2, nl1, nl2, M, cbuf, dinv, lane, bad);
         }
+        if (N1 > 1) a1[0] = n1;
+        a2[0] = n2;
+        l1 = nl1;
+        l2 = nl2;
     }
 }
 
@@ -283,7 +428,9 @@ __device__ __forceinline__ void fill_lower_sw64(float* M, const float4* src_ct, 
 // triangle valid, the rest scratch; overwritten with the strictly lower part of L,
 // transposed), b_i in bv.  Lane l owns
 // rows r1 = l and r2 = 32 + l; the factorization runs in four spans of 16 columns
-// so the register rows shrink as they finish, then x = L^{-T}(y + z).
+// so the register rows shrink as they finish (eight spans of 8 cut the FMAs by a
+// tenth but, as more code beside the kernel's other roles, ran slower in the kernel),
+// then x = L^{-T}(y + z).
 __device__ __forceinline__ void factor_solve_sample_rl64(float* M, const float* bv, float* cbuf,
                                                          float* dinv, float* zb, int lane, int K,
                                                          uint64_t seed, uint32_t row,
@@ -306,10 +453,12 @@ __device__ __forceinline__ void factor_solve_sample_rl64(float* M, const float* 
     float b1 = bv[r1];
     float b2 = bv[r2];
     __syncwarp();  // every lane has its rows before L overwrites them
-    chol_shifted_steps<32, 64>(a1, a2, b1, b2, 0, 16, M, cbuf, dinv, lane, bad);
-    chol_shifted_steps<16, 48>(a1, a2, b1, b2, 16, 32, M, cbuf, dinv, lane, bad);
-    chol_shifted_steps<0, 32>(a1, a2, b1, b2, 32, 48, M, cbuf, dinv, lane, bad);
-    chol_shifted_steps<0, 16>(a1, a2, b1, b2, 48, 64, M, cbuf, dinv, lane, bad);
+    float l1, l2;
+    chol_pivot<true>(0, a1[0], a2[0], b1, b2, l1, l2, M, cbuf, dinv, lane, bad);
+    chol_shifted_steps<32, 64>(a1, a2, b1, b2, l1, l2, 0, 16, M, cbuf, dinv, lane, bad);
+    chol_shifted_steps<16, 48>(a1, a2, b1, b2, l1, l2, 16, 32, M, cbuf, dinv, lane, bad);
+    chol_shifted_steps<0, 32>(a1, a2, b1, b2, l1, l2, 32, 48, M, cbuf, dinv, lane, bad);
+    chol_shifted_steps<0, 16>(a1, a2, b1, b2, l1, l2, 48, 64, M, cbuf, dinv, lane, bad);
     // ---- noise z (zero beyond K)
     if (lane < 16) {
         const float4 z4 = normals4_f32(seed, (uint32_t)lane, row, sweep, c3);
@@ -325,7 +474,8 @@ __device__ __forceinline__ void factor_solve_sample_rl64(float* M, const float* 
     float n1 = b1, n2 = b2;
     // ---- back substitution x = L^{-T} t: step i broadcasts x_i and every lane
     // updates its rows r < i with L[i][r], which sits in row r of M (L^T); one
-    // float4 of that row serves four steps
+    // float4 of that row serves four steps.  Selects, not branches: the update of
+    // a row on or below i is computed and dropped.
 #pragma unroll 1
     for (int g = 15; g >= 0; --g) {
         const float4 A1 = ld_chunk(M, r1, g), A2 = ld_chunk(M, r2, g);
@@ -338,21 +488,14 @@ __device__ __forceinline__ void factor_solve_sample_rl64(float* M, const float* 
             const int i = 4 * g + u;
             const int owner = i & 31;
             const float ui = __shfl_sync(kFullMask, i < 32 ? t1 : t2, owner) * dv[u];
-            float mi = 0.f;
-            if (want_means) mi = __shfl_sync(kFullMask, i < 32 ? n1 : n2, owner) * dv[u];
-            if (r1 == i) {
-                t1 = ui;
-                n1 = mi;
-            } else if (r1 < i) {
-                t1 = fmaf(-l1v[u], ui, t1);
-                n1 = fmaf(-l1v[u], mi, n1);
-            }
-            if (r2 == i) {
-                t2 = ui;
-                n2 = mi;
-            } else if (r2 < i) {
-                t2 = fmaf(-l2v[u], ui, t2);
-                n2 = fmaf(-l2v[u], mi, n2);
+            const float f1 = fmaf(-l1v[u], ui, t1), f2 = fmaf(-l2v[u], ui, t2);
+            t1 = r1 == i ? ui : (r1 < i ? f1 : t1);
+            t2 = r2 == i ? ui : (r2 < i ? f2 : t2);
+            if (want_means) {
+                const float mi = __shfl_sync(kFullMask, i < 32 ? n1 : n2, owner) * dv[u];
+                const float g1 = fmaf(-l1v[u], mi, n1), g2 = fmaf(-l2v[u], mi, n2);
+                n1 = r1 == i ? mi : (r1 < i ? g1 : n1);
+                n2 = r2 == i ? mi : (r2 < i ? g2 : n2);
             }
         }
     }

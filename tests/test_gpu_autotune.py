@@ -63,7 +63,7 @@ def test_autotune_restores_state_and_applies_a_grid_pair(bp):
         best, times = autotune(h, prob.M, prob.N, prob.K, st.cuda_stream, long_min=(1, 60),
                                shape=(50, 1024))
         assert best in times and len(times) == 4 and all(t > 0 for t in times.values())
-        assert best[2] == 0
+        assert best[2:] == (0, 0)
         after = bp.bpmf_get_state(h, prob.M, prob.N, prob.K)
         for x, y in zip(before, after):
             np.testing.assert_array_equal(x, y)
@@ -84,8 +84,11 @@ def test_autotune_split_degree_below_k64(bp):
     try:
         bp.bpmf_sweep(h, 1)
         before = bp.bpmf_get_state(h, prob.M, prob.N, prob.K)
-        best, times = autotune(h, prob.M, prob.N, prob.K, st.cuda_stream, split=(32, 1 << 30))
-        assert sorted(times) == [(0, 0, 32), (0, 0, 1 << 30)] and best in times
+        best, times = autotune(h, prob.M, prob.N, prob.K, st.cuda_stream, split=(32, 1 << 30),
+                               rank_one=(-1, 3))
+        sp = min(((0, 0, 32, 0), (0, 0, 1 << 30, 0)), key=times.get)[2]
+        assert sorted(times) == sorted([(0, 0, 32, 0), (0, 0, 1 << 30, 0), (0, 0, sp, -1),
+                                        (0, 0, sp, 3)]) and best in times
         after = bp.bpmf_get_state(h, prob.M, prob.N, prob.K)
         for x, y in zip(before, after):
             np.testing.assert_array_equal(x, y)
