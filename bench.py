@@ -157,10 +157,9 @@ def row_gather_bytes(nnz, rows, K, split=True):
     return nnz * (8 + 4 * K) + rows * (16 + 8 * K)
 
 
-# DRAM bytes (read + write) per launch of the row kernel on the 480k x 18k, 1e8-rating,
-# K = 64 workload, from one ncu capture of this kernel version (null once the kernel
-# changes).
-TRAFFIC = {"rows_user": 934e6}
+# DRAM bytes (read + write) per launch of the dominant row kernel, per workload and
+# phase, from one ncu capture of this kernel version (null once the kernel changes).
+TRAFFIC = {}
 
 
 def finite_or_none(x):
@@ -290,14 +289,16 @@ def run_native(args):
     value = aggregate_rows_per_s((prob.M + prob.N) * world, args.steps, max_ms)
     ms_per_step = max_ms / args.steps
 
-    # dominant kernel: the tensor-core row kernel of the slower row phase (with every
-    # rated row in the long bin the phase is that one launch plus the FP16 split of
-    # the new rows)
+    # dominant kernel: the row kernel of the slower row phase -- the tensor-core kernel
+    # when K pads to 64 (with every rated row in its bin the phase is that one launch
+    # plus the FP16 split of the new rows), else the CUDA-core kernel, whose FP32 work
+    # includes the Gram
     nnz = prob.nnz
+    tc_path = (K + 15) // 16 * 16 == 64
     dom = max(("rows_movie", "rows_user"), key=lambda n: phase_ms[n])
     dom_rows = prob.N if dom == "rows_movie" else prob.M
     t_dom = phase_ms[dom] / 1e3
-    alu = row_alu_flops(dom_rows, K)
+    alu = row_alu_flops(dom_rows, K) + (0.0 if tc_path else row_gram_flops(nnz, K))
     achieved = alu / t_dom / 1e12
     peaks = load_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
@@ -309,16 +310,14 @@ def run_native(args):
     other = "rows_movie" if dom == "rows_user" else "rows_user"
     other_rows = prob.N if other == "rows_movie" else prob.M
     gather = row_gather_bytes(nnz, other_rows, K)
-    roofline = {"bound": "alu", "kernel": "rows_tc_kernel (%s)" % dom,
+    roofline = {"bound": "alu",
+                "kernel": "%s (%s)" % ("rows_tc_kernel" if tc_path else "rows_warp_kernel", dom),
                 "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak, 4), "traffic": TRAFFIC.get(dom),
+                "frac": round(achieved / fp32_peak, 4),
+                "traffic": TRAFFIC.get(prob.name, {}).get(dom),
                 "peak_source": "FP32 CUDA-core peak derived from %d SMs x 128 lanes x 2 x %.0f MHz"
                                % (n_sm, sm_max),
                 "algorithmic_tflop_per_launch": round(alu / 1e12, 4),
-                "tensor": {"achieved": round(gram / t_dom / 1e12, 2), "peak": tc_peak,
-                           "frac": round(gram / t_dom / 1e12 / tc_peak, 4),
-                           "note": "Gram tiles on tcgen05 in the same launch (of measured "
-                                   "sustained bf16; FP16 runs at the bf16 rate)"},
                 "gather": {"phase": other,
                            "achieved_gbs": round(gather / (phase_ms[other] / 1e3) / 1e9, 1),
                            "peak_gbs": hbm_peak,
@@ -326,6 +325,11 @@ def run_native(args):
                            "note": "algorithmic bytes incl. gathered factor rows (mostly L2 "
                                    "hits) over the other row phase, of measured HBM copy"},
                 "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()},
+                **({"tensor": {"achieved": round(gram / t_dom / 1e12, 2), "peak": tc_peak,
+                               "frac": round(gram / t_dom / 1e12 / tc_peak, 4),
+                               "note": "Gram tiles on tcgen05 in the same launch (of measured "
+                                       "sustained bf16; FP16 runs at the bf16 rate)"}}
+                   if tc_path else {}),
                 "phase_note": "phases timed one by one (hyper steps not overlapped, all SMs to "
                               "the row kernel); %.2f ms per sweep that way" % phase_sweep_ms}
 
@@ -362,14 +366,17 @@ def run_e2e(args, prob, bp, torch, dev, stream, world, local):
     `steps` sweeps each returning its RMSE to the host."""
     h2d = (prob.csr_ptr.nbytes + prob.csr_col.nbytes + prob.csr_val.nbytes + prob.test_i.nbytes
            + prob.test_j.nbytes + prob.test_r.nbytes)
+    # the job's host buffers live in pinned memory (filled before the timed region)
+    ptr, col, val, ti, tj, tr = (torch.from_numpy(x).pin_memory().numpy() for x in
+                                 (prob.csr_ptr, prob.csr_col, prob.csr_val, prob.test_i,
+                                  prob.test_j, prob.test_r))
     barrier(world, local)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     params = bp.bpmf_default_params(alpha=prob.alpha, seed=prob.seed, burn_in=prob.burn_in,
                                     flags=bp.BPMF_BF16_GRAM if args.bf16 else 0)
-    h = bp.bpmf_create(prob.M, prob.N, prob.K, prob.csr_ptr, prob.csr_col, prob.csr_val,
-                       test_i=prob.test_i, test_j=prob.test_j, test_r=prob.test_r, params=params,
-                       stream=stream.cuda_stream)
+    h = bp.bpmf_create(prob.M, prob.N, prob.K, ptr, col, val, test_i=ti, test_j=tj, test_r=tr,
+                       params=params, stream=stream.cuda_stream)
     try:
         for _ in range(args.steps):
             bp.bpmf_sweep(h, 1)  # RMSE of the step read back to the host
@@ -381,8 +388,8 @@ def run_e2e(args, prob, bp, torch, dev, stream, world, local):
     return {"value": round(aggregate_rows_per_s((prob.M + prob.N) * world, args.steps, ms), 1),
             "unit": UNIT, "h2d_bytes_per_step": int(h2d / args.steps),
             "d2h_bytes_per_step": 16,
-            "note": "wall clock of bpmf_create from host arrays + %d x bpmf_sweep with RMSE "
-                    "read back" % args.steps}
+            "note": "wall clock of bpmf_create from pinned host arrays + %d x bpmf_sweep with "
+                    "RMSE read back" % args.steps}
 
 
 def run_reference(args):

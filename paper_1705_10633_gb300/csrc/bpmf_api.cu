@@ -187,11 +187,17 @@ bool host_spd_inverse(int K, const double* A, std::vector<double>& inv)
     return true;
 }
 
-bool valid_csr(int64_t rows, int64_t cols, const int64_t* ptr, const int32_t* idx)
+bool valid_ptr(int64_t rows, const int64_t* ptr)
 {
     if (ptr[0] != 0) return false;
     for (int64_t r = 0; r < rows; ++r)
         if (ptr[r + 1] < ptr[r]) return false;
+    return true;
+}
+
+bool valid_csr(int64_t rows, int64_t cols, const int64_t* ptr, const int32_t* idx)
+{
+    if (!valid_ptr(rows, ptr)) return false;
     const int64_t nnz = ptr[rows];
     for (int64_t t = 0; t < nnz; ++t)
         if (idx[t] < 0 || (int64_t)idx[t] >= cols) return false;
@@ -223,20 +229,28 @@ void build_csc(int64_t M, int64_t N, const int64_t* rp, const int32_t* ci, const
 void bin_rows(int64_t rows, const int64_t* ptr, int64_t long_min, std::vector<int32_t>& order,
               int64_t* n_short, int64_t* n_long, int64_t* long_ratings)
 {
-    order.resize((size_t)rows);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        const int64_t da = ptr[a + 1] - ptr[a], db = ptr[b + 1] - ptr[b];
-        const bool la = da >= long_min, lb = db >= long_min;
-        if (la != lb) return lb;  // short bin first
-        return da > db;
-    });
-    int64_t ns = 0, nl_ratings = 0;
-    for (int64_t r = 0; r < rows; ++r) {
-        const int64_t d = ptr[r + 1] - ptr[r];
-        if (d < long_min) ++ns;
-        else nl_ratings += d;
+    // counting sort by degree (stable: equal degrees keep ascending row order)
+    int64_t dmax = 0;
+    for (int64_t r = 0; r < rows; ++r) dmax = std::max(dmax, ptr[r + 1] - ptr[r]);
+    std::vector<int64_t> start((size_t)dmax + 2, 0);
+    for (int64_t r = 0; r < rows; ++r) ++start[(size_t)(ptr[r + 1] - ptr[r])];
+    // bucket offsets: short-bin degrees (below long_min) first, each bin from its
+    // largest degree down
+    const int64_t split = std::min(long_min, dmax + 1);  // degrees >= split are long
+    int64_t off = 0, ns = 0, nl_ratings = 0;
+    std::vector<int64_t> pos((size_t)dmax + 1, 0);
+    for (int64_t d = split - 1; d >= 0; --d) {
+        pos[(size_t)d] = off;
+        off += start[(size_t)d];
     }
+    ns = off;
+    for (int64_t d = dmax; d >= split; --d) {
+        pos[(size_t)d] = off;
+        off += start[(size_t)d];
+        nl_ratings += d * start[(size_t)d];
+    }
+    order.resize((size_t)rows);
+    for (int64_t r = 0; r < rows; ++r) order[(size_t)pos[(size_t)(ptr[r + 1] - ptr[r])]++] = (int32_t)r;
     *n_short = ns;
     *n_long = rows - ns;
     *long_ratings = nl_ratings;
@@ -521,7 +535,11 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
     if (prm.nu0 == 0.0) prm.nu0 = (double)K;
     if (!(prm.alpha > 0.0) || !(prm.beta0 > 0.0) || !(prm.nu0 >= (double)K)) return BPMF_EINVAL;
     if (prm.order != 0 && prm.order != 1) return BPMF_EINVAL;
-    if (!valid_csr(M, N, csr_ptr, csr_col)) return BPMF_EINVAL;
+    // the column indices of the row view are checked on the device when it also builds
+    // the column view there (one pass over the uploaded ratings, with the mean)
+    if (!valid_ptr(M, csr_ptr)) return BPMF_EINVAL;
+    const bool device_csc = !have_csc && csr_ptr[M] > 0 && csr_ptr[M] < INT32_MAX;
+    if (!device_csc && !valid_csr(M, N, csr_ptr, csr_col)) return BPMF_EINVAL;
     if (have_csc) {
         if (!valid_csr(N, M, csc_ptr, csc_row) || csc_ptr[N] != csr_ptr[M]) return BPMF_EINVAL;
     }
@@ -570,17 +588,11 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
             return BPMF_ECUDA;
         }
     }
-    // training mean in index order (FP64)
-    double total = 0.0;
-    for (int64_t t = 0; t < h->nnz; ++t) total += (double)csr_val[t];
-    h->rbar = ((prm.flags & BPMF_NO_CENTER) || h->nnz == 0) ? 0.0 : total / (double)h->nnz;
-
     std::vector<int64_t> cp;
     std::vector<int32_t> ri;
     std::vector<float> cv;
     // without a caller-supplied CSC the column view is built on the device from the
     // uploaded CSR (same order as the host counting sort, which serves the rest)
-    const bool device_csc = !have_csc && h->nnz > 0 && h->nnz < INT32_MAX;
     if (!have_csc && !device_csc) {
         build_csc(M, N, csr_ptr, csr_col, csr_val, cp, ri, cv);
         csc_ptr = cp.data();
@@ -648,6 +660,32 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
         if (e != cudaSuccess) {
             rc = BPMF_ECUDA;
             break;
+        }
+        if (s == 0) {
+            // training mean (FP64, fixed summation order) and the column range check
+            double* scratch = nullptr;
+            unsigned int* bad = nullptr;
+            double sum = 0.0;
+            unsigned int bad_h = 0;
+            if (!alloc_n(h, &scratch, 1 + (size_t)kCheckSumBlocks) || !alloc_n(h, &bad, 1)) {
+                rc = BPMF_ENOMEM;
+                break;
+            }
+            e = launch_check_sum(d.idx, d.val, h->nnz, (int32_t)N, scratch, bad, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&sum, scratch, sizeof(double), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&bad_h, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                rc = BPMF_ECUDA;
+                break;
+            }
+            if (bad_h) {
+                rc = BPMF_EINVAL;
+                break;
+            }
+            h->rbar = ((prm.flags & BPMF_NO_CENTER) || h->nnz == 0) ? 0.0 : sum / (double)h->nnz;
         }
         d.ptr_h.assign(hp[s], hp[s] + d.rows + 1);
         rc = bin_side(h, d, order);

@@ -74,6 +74,11 @@ struct RowArgs {
 cudaError_t launch_init_factors(float* X, int64_t rows, int K, int ld, uint64_t seed, uint32_t c3,
                                 cudaStream_t s);
 cudaError_t launch_center_values(float* val, int64_t n, double rbar, cudaStream_t s);
+// Column range check and fixed-order FP64 sum of n ratings: scratch[0] = sum (scratch
+// holds 1 + kCheckSumBlocks doubles), *bad = 1 if an index is outside [0, ncols).
+constexpr int kCheckSumBlocks = 512;
+cudaError_t launch_check_sum(const int32_t* col, const float* val, int64_t n, int32_t ncols,
+                             double* scratch, unsigned int* bad, cudaStream_t s);
 
 // Hyper step, part 0: the shift (FP64 mean of the first rows, kp entries, zero
 // beyond K) that parts 1 and 2 subtract.

@@ -39,6 +39,67 @@ cudaError_t launch_init_factors(float* X, int64_t rows, int K, int ld, uint64_t 
     return cudaGetLastError();
 }
 
+// Ratings check and FP64 sum in a fixed order (the result does not depend on timing):
+// block b takes the contiguous range [b n / B, (b + 1) n / B), thread t its elements
+// t, t + 256, ... in order, then a fixed tree; the finishing block adds the B partials
+// the same way.  Column indices outside [0, ncols) set *bad.
+constexpr int kSumThreads = 256;
+
+__device__ double block_tree_sum(double v, double* sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = kSumThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    return sh[0];
+}
+
+__global__ void __launch_bounds__(kSumThreads) check_sum_kernel(const int32_t* __restrict__ col,
+                                                               const float* __restrict__ val,
+                                                               int64_t n, int32_t ncols,
+                                                               double* __restrict__ partials,
+                                                               unsigned int* bad)
+{
+    __shared__ double sh[kSumThreads];
+    const int64_t lo = n * blockIdx.x / gridDim.x, hi = n * (blockIdx.x + 1) / gridDim.x;
+    double acc = 0.0;
+    bool ok = true;
+    for (int64_t e = lo + threadIdx.x; e < hi; e += kSumThreads) {
+        const int32_t c = col[e];
+        ok &= c >= 0 && c < ncols;
+        acc += (double)val[e];
+    }
+    if (!ok) atomicOr(bad, 1u);
+    const double t = block_tree_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kSumThreads) sum_finish_kernel(const double* __restrict__ partials,
+                                                                int nparts, double* out)
+{
+    __shared__ double sh[kSumThreads];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += kSumThreads) acc += partials[b];
+    const double t = block_tree_sum(acc, sh);
+    if (threadIdx.x == 0) *out = t;
+}
+
+cudaError_t launch_check_sum(const int32_t* col, const float* val, int64_t n, int32_t ncols,
+                             double* scratch, unsigned int* bad, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        check_sum_kernel<<<kCheckSumBlocks, kSumThreads, 0, s>>>(col, val, n, ncols, scratch + 1, bad);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        sum_finish_kernel<<<1, kSumThreads, 0, s>>>(scratch + 1, kCheckSumBlocks, scratch);
+        return cudaGetLastError();
+    }
+    return cudaMemsetAsync(scratch, 0, sizeof(double), s);
+}
+
 __global__ void center_values_kernel(float* val, int64_t n, double rbar)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
