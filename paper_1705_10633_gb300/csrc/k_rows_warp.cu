@@ -323,6 +323,11 @@ static cudaError_t launch_route(const RowArgs& a, int num_sms, cudaStream_t s)
     const size_t smem = sizeof(float) * (size_t)W::PER_WARP_ALIGNED * kWarpsPerCta;
     cudaError_t e = cudaFuncSetAttribute(rows_warp_kernel<KT, kR1>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // all of the unified L1 / shared memory as shared, so residency is set by registers
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(rows_warp_kernel<KT, kR1>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_warp_kernel<KT, kR1>,
