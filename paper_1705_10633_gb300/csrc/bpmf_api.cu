@@ -47,6 +47,7 @@ struct DevSide {
     double* mu64 = nullptr;
     double* shift64 = nullptr;  // kp: shift of the hyper statistics
     double* lam64 = nullptr;
+    double* nw_draws = nullptr;  // the hyper step's random draws (scratch)
     float* lam32 = nullptr;
     float* lammu32 = nullptr;
     double* partials = nullptr;
@@ -368,7 +369,8 @@ int phase_hyper(bpmf_ctx* h, int s, cudaStream_t st, uint32_t sweep_offset)
     a.lam64 = d.lam64;
     a.lam32 = d.lam32;
     a.lammu32 = d.lammu32;
-    h->launches += 4;
+    a.draws = d.nw_draws;
+    h->launches += 5;
     return cuda_rc(launch_nw_sample(a, st));
 }
 
@@ -623,7 +625,8 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
         bool ok = alloc_n(h, &d.ptr, d.rows + 1) && alloc_n(h, &d.idx, h->nnz) &&
                   alloc_n(h, &d.val, h->nnz) && alloc_n(h, &d.X, (size_t)d.rows * kp) &&
                   alloc_n(h, &d.bin_rows, d.rows) && alloc_n(h, &d.mu64, K) && alloc_n(h, &d.shift64, kp) &&
-                  alloc_n(h, &d.lam64, (size_t)K * K) && alloc_n(h, &d.lam32, (size_t)3 * kp * kp) &&
+                  alloc_n(h, &d.lam64, (size_t)K * K) && alloc_n(h, &d.nw_draws, nw_draws_doubles(K)) &&
+                  alloc_n(h, &d.lam32, (size_t)3 * kp * kp) &&
                   alloc_n(h, &d.lammu32, kp) &&
                   alloc_n(h, &d.partials, (size_t)d.red_blocks * hyper_partial_doubles(kp)) &&
                   alloc_n(h, &d.sums, hyper_partial_doubles(kp)) &&

@@ -114,7 +114,11 @@ struct NWArgs {
     float* lam32;           // out: kp x kp, identity beyond K, then its chunk-transposed copy,
                             // then the chunk-transposed lower Cholesky factor (identity beyond K)
     float* lammu32;         // out: kp
+    double* draws;          // K(K-1)/2 + 2K scratch: the step's random draws
 };
+// Doubles of NWArgs::draws for K.
+inline size_t nw_draws_doubles(int K) { return (size_t)K * (K - 1) / 2 + 2 * (size_t)K; }
+// The draws kernel (many CTAs) then the one-CTA draw: two launches.
 cudaError_t launch_nw_sample(const NWArgs& a, cudaStream_t s);
 // Index of (i, j) in the chunk-transposed copy of a kp x kp matrix (kp a multiple
 // of 4): float4 (i, 4c .. 4c + 3) sits at float4 index c * kp + i.

@@ -2,13 +2,15 @@
 // movies/users based on V/U", Sec. 2): sufficient statistics of a factor matrix
 // and the Normal-Wishart draw of (mu, Lambda).
 //
+//   shift  : s = FP64 mean of the first rows (fixed order).
 //   reduce : every block streams a contiguous slab of rows once (HBM bound),
 //            accumulating (x - s) and (x - s)(x - s)^T in FP32 registers over
-//            64-row chunks and folding each chunk into FP64 accumulators; s is
-//            the side's current hyper mean, so the sums stay small.
+//            64-row chunks and folding each chunk into FP64 accumulators, so the
+//            sums stay small.
 //   combine: fixed-order FP64 sum of the block partials (deterministic).
-//   nw     : one CTA in FP64 -- posterior parameters, Cholesky, inverse,
-//            Bartlett Wishart draw with Marsaglia-Tsang gammas, mean draw.
+//   nw     : one CTA in FP64 -- posterior parameters, chol(W*) through the
+//            reversed factorisation of its inverse, Bartlett Wishart draw with
+//            Marsaglia-Tsang gammas, chol(Lambda), mean draw.
 #include "bpmf_internal.cuh"
 #include "philox.cuh"
 
@@ -109,22 +111,30 @@ __global__ void __launch_bounds__(kRedThreads) hyper_reduce_kernel(const float* 
 // side has few rows) and computed in a fixed order keeps resumed chains bit-identical.
 constexpr int64_t kShiftRows = 256;
 
-__global__ void hyper_shift_kernel(const float* __restrict__ X, int64_t rows, int K, int kp,
-                                   double* __restrict__ shift64)
+// 256 threads: column c = t mod 64 of rows r = t / 64 (mod 4), four partial sums added
+// in a fixed order (a quarter of the dependent chain of one thread per column).
+__global__ void __launch_bounds__(256) hyper_shift_kernel(const float* __restrict__ X,
+                                                          int64_t rows, int K, int kp,
+                                                          double* __restrict__ shift64)
 {
-    const int t = threadIdx.x;
-    if (t >= kp) return;
+    __shared__ double part[4][64];
+    const int t = threadIdx.x, c = t & 63, g = t >> 6;
     const int64_t n = rows < kShiftRows ? rows : kShiftRows;
     double s = 0.0;
-    if (t < K)
-        for (int64_t r = 0; r < n; ++r) s += (double)X[r * kp + t];
-    shift64[t] = (t < K && n > 0) ? s / (double)n : 0.0;
+    if (c < K)
+        for (int64_t r = g; r < n; r += 4) s += (double)X[r * kp + c];
+    part[g][c] = s;
+    __syncthreads();
+    if (t < kp) {
+        const double tot = (part[0][t] + part[1][t]) + (part[2][t] + part[3][t]);
+        shift64[t] = (t < K && n > 0) ? tot / (double)n : 0.0;
+    }
 }
 
 cudaError_t launch_hyper_shift(const float* X, int64_t rows, int K, int kp, double* shift64,
                                cudaStream_t s)
 {
-    hyper_shift_kernel<<<1, 64, 0, s>>>(X, rows, K, kp, shift64);
+    hyper_shift_kernel<<<1, 256, 0, s>>>(X, rows, K, kp, shift64);
     return cudaGetLastError();
 }
 
@@ -146,9 +156,17 @@ __global__ void hyper_combine_kernel(const double* __restrict__ partials, int nb
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
-    double acc = 0.0;
-    for (int b = 0; b < nblocks; ++b) acc += partials[(size_t)b * E + e];
-    sums[e] = acc;
+    // four interleaved accumulators (more loads in flight), added in a fixed order
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int b = 0;
+    for (; b + 3 < nblocks; b += 4) {
+        a0 += partials[(size_t)b * E + e];
+        a1 += partials[(size_t)(b + 1) * E + e];
+        a2 += partials[(size_t)(b + 2) * E + e];
+        a3 += partials[(size_t)(b + 3) * E + e];
+    }
+    for (; b < nblocks; ++b) a0 += partials[(size_t)b * E + e];
+    sums[e] = (a0 + a1) + (a2 + a3);
 }
 
 cudaError_t launch_hyper_combine(const double* partials, int nblocks, int kp, double* sums,
@@ -165,33 +183,121 @@ cudaError_t launch_hyper_combine(const double* partials, int nblocks, int kp, do
 constexpr int kNWThreads = 256;
 constexpr int kGammaMaxAttempts = 64;
 
-// In-place right-looking Cholesky of the lower triangle of A (upper set to 0).
-// Returns false (in every thread) if a pivot is not positive.
-__device__ bool nw_cholesky(double* A, int K, int* bad)
+// 1 / sqrt(p) for p > 0 in FP64: an FP32 estimate refined by two steps of Newton's
+// iteration for the reciprocal square root, y <- y (3 - p y^2) / 2, whose relative error
+// squares each step (2^-23 -> 2^-45 -> FP64 rounding).  A handful of FP64 operations
+// instead of a square root and a division (FP64 issues slowly on this GPU, and the
+// factorisations below take one of these per column, serially).  Outside FP32's
+// normal range: the FP64 square root and division.
+__device__ __forceinline__ double rsqrt_newton(double p)
 {
-    const int t = threadIdx.x;
+    if (p > 1e-30 && p < 1e30) {
+        double y = (double)rsqrtf((float)p);
+        y = y * fma(-0.5 * p * y, y, 1.5);
+        y = y * fma(-0.5 * p * y, y, 1.5);
+        return y;
+    }
+    return 1.0 / sqrt(p);
+}
+
+// In-place right-looking Cholesky of the lower triangle of A (K x K row-major in shared
+// memory; the upper triangle is set to 0), by a block of kNWThreads = 256 threads.  Per
+// column: one thread takes the pivot's reciprocal square root, the column is scaled by
+// it, and the trailing lower triangle is updated on a 16 x 16 thread grid.  *bad is set
+// on a non-positive pivot (which is replaced by 1).
+__device__ void nw_cholesky(double* A, int K, int* bad)
+{
+    __shared__ double s_rinv;
+    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
     for (int k = 0; k < K; ++k) {
         if (t == 0) {
-            const double p = A[k * K + k];
-            if (!(p > 0.0)) *bad = 1;
-            A[k * K + k] = sqrt(p > 0.0 ? p : 1.0);
+            double p = A[k * K + k];
+            if (!(p > 0.0)) {
+                *bad = 1;
+                p = 1.0;
+            }
+            const double r = rsqrt_newton(p);
+            s_rinv = r;
+            A[k * K + k] = p * r;
         }
         __syncthreads();
-        const double lkk = A[k * K + k];
-        for (int i = k + 1 + t; i < K; i += blockDim.x) A[i * K + k] /= lkk;
+        const double rinv = s_rinv;
+        for (int i = k + 1 + t; i < K; i += kNWThreads) A[i * K + k] *= rinv;
         __syncthreads();
-        // trailing update of the lower triangle, j in (k, i]
-        const int m = K - k - 1;
-        for (int e = t; e < m * m; e += blockDim.x) {
-            const int i = k + 1 + e / m, j = k + 1 + e % m;
-            if (j <= i) A[i * K + j] -= A[i * K + k] * A[j * K + k];
+        for (int i = k + 1 + ty; i < K; i += 16) {
+            const double lik = A[i * K + k];
+            for (int j = k + 1 + tx; j <= i; j += 16) A[i * K + j] = fma(-lik, A[j * K + k], A[i * K + j]);
         }
         __syncthreads();
     }
-    for (int e = t; e < K * K; e += blockDim.x)
+    for (int e = t; e < K * K; e += kNWThreads)
         if (e % K > e / K) A[e] = 0.0;
     __syncthreads();
-    return *bad == 0;
+}
+
+// Dot product of x[0..n) and y[0..n) (strides sx, sy) with four interleaved FP64
+// accumulators added in a fixed order: a quarter of the dependent chain.
+__device__ __forceinline__ double dot4(const double* x, int sx, const double* y, int sy, int n)
+{
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int k = 0;
+    for (; k + 3 < n; k += 4) {
+        s0 = fma(x[k * sx], y[k * sy], s0);
+        s1 = fma(x[(k + 1) * sx], y[(k + 1) * sy], s1);
+        s2 = fma(x[(k + 2) * sx], y[(k + 2) * sy], s2);
+        s3 = fma(x[(k + 3) * sx], y[(k + 3) * sy], s3);
+    }
+    for (; k < n; ++k) s0 = fma(x[k * sx], y[k * sy], s0);
+    return (s0 + s1) + (s2 + s3);
+}
+
+// The Normal-Wishart step's random numbers, which depend only on (seed, sweep, side)
+// and the posterior degrees of freedom (nu0 + rows, fixed per side): draws[q] for
+// q < K(K-1)/2 the Bartlett factor's off-diagonal normals (stream 0), then K normals of
+// the mean draw (stream 1), then the Bartlett diagonal sqrt(chi^2(nu* - k)) =
+// sqrt(2 Gamma((nu* - k) / 2)) by Marsaglia-Tsang.  One thread per Philox call (four
+// normals) or per gamma, over as many CTAs as that takes: FP64 is slow on this GPU, and
+// spreading these draws over SMs takes them off the one-CTA kernel that uses them.
+__global__ void nw_draws_kernel(NWArgs a, double* __restrict__ draws)
+{
+    const int K = a.K, noff = K * (K - 1) / 2;
+    const int ncall0 = (noff + 3) / 4, ncall1 = (K + 3) / 4;
+    const uint32_t sweep = (uint32_t)a.ctl->sweep + a.sweep_offset;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < ncall0 + ncall1) {
+        const bool mean = q >= ncall0;
+        const uint32_t c = mean ? (uint32_t)(q - ncall0) : (uint32_t)q;
+        const uint4 w = philox_call(a.seed, c, mean ? 1u : 0u, sweep, a.c3_normal);
+        const double2 z0 = box_muller_f64(w.x, w.y), z1 = box_muller_f64(w.z, w.w);
+        const double z[4] = {z0.x, z0.y, z1.x, z1.y};
+        const int base = mean ? noff : 0, lim = mean ? K : noff;
+        for (int u = 0; u < 4; ++u)
+            if ((int)(4 * c) + u < lim) draws[base + 4 * c + u] = z[u];
+    } else if (q < ncall0 + ncall1 + K) {
+        const int k = q - ncall0 - ncall1;
+        const double nu_s = a.nu0 + (double)a.n;
+        const double shape = 0.5 * (nu_s - (double)k);
+        const double d = shape - 1.0 / 3.0;
+        const double c = 1.0 / sqrt(9.0 * d);
+        double g = -1.0;
+        for (int att = 0; att < kGammaMaxAttempts; ++att) {
+            const uint4 wd = philox_call(a.seed, (uint32_t)att, (uint32_t)k, sweep, a.c3_gamma);
+            const double x = box_muller_f64(wd.x, wd.y).x;
+            const double sx = 1.0 + c * x;
+            if (sx <= 0.0) continue;
+            const double v = sx * sx * sx;
+            const double u = (double)((wd.z >> 8) + 1u) * 0x1p-24;
+            if (log(u) < 0.5 * x * x + d - d * v + d * log(v)) {
+                g = d * v;
+                break;
+            }
+        }
+        if (g < 0.0) {
+            atomicOr(&a.ctl->status, kStatusGamma);
+            g = shape;
+        }
+        draws[noff + K + k] = sqrt(2.0 * g);
+    }
 }
 
 __global__ void __launch_bounds__(kNWThreads) nw_sample_kernel(NWArgs a)
@@ -206,10 +312,9 @@ __global__ void __launch_bounds__(kNWThreads) nw_sample_kernel(NWArgs a)
     double* mustar = dvec + K;
     double* w = mustar + K;
     double* z = w + K;
-    __shared__ int bad, gbad;
-    const uint32_t sweep = (uint32_t)a.ctl->sweep + a.sweep_offset;
+    __shared__ int bad;
     const double n = (double)a.n;
-    if (t == 0) { bad = 0; gbad = 0; }
+    if (t == 0) bad = 0;
     // ---- statistics: mean = s + S1/n, S = S2/n - d d^T with d = S1/n ----
     for (int k = t; k < K; k += blockDim.x) {
         const double s = (double)(float)a.shift64[k];
@@ -227,7 +332,7 @@ __global__ void __launch_bounds__(kNWThreads) nw_sample_kernel(NWArgs a)
     for (int k = t; k < K; k += blockDim.x) a.stats[k] = mean[k];
     __syncthreads();
     // ---- posterior parameters ----
-    const double beta_s = a.beta0 + n, nu_s = a.nu0 + n;
+    const double beta_s = a.beta0 + n;
     const double cross = a.beta0 * n / (a.beta0 + n);
     for (int k = t; k < K; k += blockDim.x) mustar[k] = (a.beta0 * a.mu0[k] + n * mean[k]) / (a.beta0 + n);
     for (int e = t; e < KK; e += blockDim.x) {
@@ -235,92 +340,87 @@ __global__ void __launch_bounds__(kNWThreads) nw_sample_kernel(NWArgs a)
         M0[e] = a.W0inv[e] + n * M1[e] + cross * (a.mu0[i] - mean[i]) * (a.mu0[j] - mean[j]);
     }
     __syncthreads();
-    // ---- W* = P^{-1}: chol(P) = L, Linv by forward substitution per column ----
-    nw_cholesky(M0, K, &bad);
-    for (int j = t; j < K; j += blockDim.x) {
-        for (int i = 0; i < K; ++i) {
-            double v;
-            if (i < j) v = 0.0;
-            else {
-                double s = (i == j) ? 1.0 : 0.0;
-                for (int k = j; k < i; ++k) s -= M0[i * K + k] * M1[k * K + j];
-                v = s / M0[i * K + i];
-            }
-            M1[i * K + j] = v;  // column j is private to this thread
-        }
-    }
-    __syncthreads();
-    // W = Linv^T Linv
-    for (int e = t; e < KK; e += blockDim.x) {
+    // ---- L_W = chol(W*), W* = P^{-1}.  With J the reversal (J_ij = [i + j = K - 1]) and
+    // G = chol(J P J):  P^{-1} = J G^{-T} G^{-1} J, and J G^{-T} J is lower with a positive
+    // diagonal, so it is the Cholesky factor of W* (one factorisation and one triangular
+    // inverse instead of inverse, product and a second factorisation) ----
+    for (int e = t; e < KK; e += kNWThreads) {
         const int i = e / K, j = e % K;
-        const int k0 = i > j ? i : j;
-        double s = 0.0;
-        for (int k = k0; k < K; ++k) s += M1[k * K + i] * M1[k * K + j];
-        M2[e] = s;
+        M1[e] = M0[(K - 1 - i) * K + (K - 1 - j)];
     }
     __syncthreads();
-    // L_W = chol(W) in M2
-    nw_cholesky(M2, K, &bad);
-    // ---- Bartlett factor A in M1 ----
-    for (int e = t; e < KK; e += blockDim.x) M1[e] = 0.0;
+    nw_cholesky(M1, K, &bad);  // G
+    for (int k = t; k < K; k += kNWThreads) dvec[k] = 1.0 / M1[k * K + k];
     __syncthreads();
-    for (int k = t; k < K; k += blockDim.x) {
-        const double shape = 0.5 * (nu_s - (double)k);
-        const double d = shape - 1.0 / 3.0;
-        const double c = 1.0 / sqrt(9.0 * d);
-        double g = -1.0;
-        for (int att = 0; att < kGammaMaxAttempts; ++att) {
-            const uint4 wd = philox_call(a.seed, (uint32_t)att, (uint32_t)k, sweep, a.c3_gamma);
-            const double x = box_muller_f64(wd.x, wd.y).x;
-            const double sx = 1.0 + c * x;
-            if (sx <= 0.0) continue;
-            const double v = sx * sx * sx;
-            const double u = (double)((wd.z >> 8) + 1u) * 0x1p-24;
-            if (log(u) < 0.5 * x * x + d - d * v + d * log(v)) { g = d * v; break; }
+    // G^{-1} into M2 by forward substitution, four lanes per column: lane q of column j
+    // sums the terms k = q (mod 4) and writes the rows i = q (mod 4), so it only reads
+    // entries it wrote; the four partial sums meet by butterfly shuffles (every lane of a
+    // warp runs every row, so the shuffles are uniform)
+    {
+        const int j = t >> 2, q = t & 3;
+        const bool col = j < K;
+        if (col && (j & 3) == q) M2[j * K + j] = dvec[j];
+        for (int i = 1; i < K; ++i) {
+            double part = 0.0;
+            if (col && i > j)
+                for (int k = j + ((q - j) & 3); k < i; k += 4) part = fma(M1[i * K + k], M2[k * K + j], part);
+            part += __shfl_xor_sync(0xffffffffu, part, 1);
+            part += __shfl_xor_sync(0xffffffffu, part, 2);
+            if (col && i > j && (i & 3) == q) M2[i * K + j] = -part * dvec[i];
         }
-        if (g < 0.0) { gbad = 1; g = shape; }
-        M1[k * K + k] = sqrt(2.0 * g);
+        if (col)
+            for (int i = q; i < j; i += 4) M2[i * K + j] = 0.0;
     }
+    __syncthreads();
+    // L_W[i][j] = G^{-1}[K-1-j][K-1-i] into M0 (lower)
+    for (int e = t; e < KK; e += kNWThreads) {
+        const int i = e / K, j = e % K;
+        M0[e] = (j <= i) ? M2[(K - 1 - j) * K + (K - 1 - i)] : 0.0;
+    }
+    // ---- Bartlett factor A in M1 (its normals and chi^2 square roots from the draws
+    // kernel) ----
     const int noff = K * (K - 1) / 2;
-    for (int q = t; q < noff; q += blockDim.x) {
-        // q = k(k-1)/2 + l, k > l
-        int k = (int)((1.0 + sqrt(1.0 + 8.0 * (double)q)) * 0.5);
-        while (k * (k - 1) / 2 > q) --k;
-        while ((k + 1) * k / 2 <= q) ++k;
-        const int l = q - k * (k - 1) / 2;
-        M1[k * K + l] = normal_f64(a.seed, (uint32_t)q, 0u, sweep, a.c3_normal);
+    for (int e = t; e < KK; e += kNWThreads) {
+        const int i = e / K, j = e % K;
+        M1[e] = j < i ? a.draws[i * (i - 1) / 2 + j] : (i == j ? a.draws[noff + K + i] : 0.0);
     }
     __syncthreads();
-    // B = L_W A (lower) into M0
-    for (int e = t; e < KK; e += blockDim.x) {
+    // B = L_W A (lower times lower: lower) into M2
+    for (int e = t; e < KK; e += kNWThreads) {
         const int i = e / K, j = e % K;
-        double s = 0.0;
-        for (int k = j; k <= i; ++k) s += M2[i * K + k] * M1[k * K + j];
-        M0[e] = (j <= i) ? s : 0.0;
+        M2[e] = (j <= i) ? dot4(M0 + i * K + j, 1, M1 + j * K + j, K, i - j + 1) : 0.0;
     }
     __syncthreads();
-    // Lambda = B B^T into M1
-    for (int e = t; e < KK; e += blockDim.x) {
+    // Lambda = B B^T into M1: the lower triangle, mirrored (the products are the same
+    // either way round, so the matrix is exactly symmetric)
+    for (int e = t; e < KK; e += kNWThreads) {
         const int i = e / K, j = e % K;
-        const int kmax = i < j ? i : j;
-        double s = 0.0;
-        for (int k = 0; k <= kmax; ++k) s += M0[i * K + k] * M0[j * K + k];
-        M1[e] = s;
+        if (j <= i) {
+            const double v = dot4(M2 + i * K, 1, M2 + j * K, 1, j + 1);
+            M1[i * K + j] = v;
+            M1[j * K + i] = v;
+        }
     }
     __syncthreads();
     // ---- C = chol(Lambda) by the same routine that bpmf_set_state's refresh uses on the
     // stored Lambda (so a resumed chain's rank-one route sees identical factors), and
     // mu = mu* + chol(beta* Lambda)^{-T} z = mu* + C^{-T} z / sqrt(beta*) ----
-    for (int e = t; e < KK; e += blockDim.x) M2[e] = M1[e];
-    for (int k = t; k < K; k += blockDim.x) z[k] = normal_f64(a.seed, (uint32_t)k, 1u, sweep, a.c3_normal);
+    for (int e = t; e < KK; e += kNWThreads) M0[e] = M1[e];
+    for (int k = t; k < K; k += kNWThreads) z[k] = a.draws[noff + k];
     __syncthreads();
-    nw_cholesky(M2, K, &bad);
-    if (t == 0) {
+    nw_cholesky(M0, K, &bad);
+    if (t < 32) {
+        // back substitution C^T w = z / sqrt(beta*) in one warp: lane l keeps the residuals
+        // of rows l and 32 + l; step i takes w_i from its owner and every lane removes
+        // C[i][r] w_i from its rows r < i
         const double rb = 1.0 / sqrt(beta_s);
+        double r1 = t < K ? z[t] * rb : 0.0, r2 = 32 + t < K ? z[32 + t] * rb : 0.0;
         for (int i = K - 1; i >= 0; --i) {
-            double s = z[i] * rb;
-            for (int k = i + 1; k < K; ++k) s -= M2[k * K + i] * w[k];
-            w[i] = s / M2[i * K + i];
+            const double own = i < 32 ? r1 : r2;
+            const double wi = __shfl_sync(0xffffffffu, own, i & 31) / M0[i * K + i];
+            if (t == 0) w[i] = wi;
+            if (t < i) r1 = fma(-M0[i * K + t], wi, r1);
+            if (32 + t < i) r2 = fma(-M0[i * K + 32 + t], wi, r2);
         }
     }
     __syncthreads();
@@ -335,7 +435,7 @@ __global__ void __launch_bounds__(kNWThreads) nw_sample_kernel(NWArgs a)
         a.lam32[e] = v;
         a.lam32[kp * kp + chunk_t_index(i, j, kp)] = v;
         // chol(Lambda) for the rank-one route
-        const float c = in ? (float)M2[i * K + j] : (i == j ? 1.f : 0.f);
+        const float c = in ? (float)M0[i * K + j] : (i == j ? 1.f : 0.f);
         a.lam32[2 * kp * kp + chunk_t_index(i, j, kp)] = c;
     }
     for (int i = t; i < kp; i += blockDim.x) {
@@ -347,7 +447,6 @@ __global__ void __launch_bounds__(kNWThreads) nw_sample_kernel(NWArgs a)
     if (t == 0) {
         unsigned int st = 0;
         if (bad) st |= kStatusNotPD;
-        if (gbad) st |= kStatusGamma;
         if (st) atomicOr(&a.ctl->status, st);
     }
 }
@@ -363,6 +462,11 @@ cudaError_t launch_nw_sample(const NWArgs& a, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
+    const int noff = a.K * (a.K - 1) / 2;
+    const int nthreads = (noff + 3) / 4 + (a.K + 3) / 4 + a.K;
+    nw_draws_kernel<<<(nthreads + 31) / 32, 32, 0, s>>>(a, a.draws);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     nw_sample_kernel<<<1, kNWThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
