@@ -561,6 +561,72 @@ def run_serving(args):
     print(json.dumps(out), flush=True)
 
 
+def run_fig3(args):
+    """Per-row cost against degree for each route of the row update, the GPU analogue of
+    the paper's Fig. 3 (time to update one item against its number of ratings for the
+    rank-one, sequential-Cholesky and parallel-Cholesky methods, Sec. 3.2).  For each
+    degree d and route: microseconds per row of a user phase over many rows of degree d
+    (throughput), and the phase time for a single row (latency of one item)."""
+    import torch
+
+    import paper_1705_10633_gb300 as bp
+    import workloads
+    torch.cuda.set_device(0)
+    degrees = [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096]
+    no = 1 << 30
+    routes = {
+        32: {"gram": dict(rank_one_degree=-1, split_degree=no),
+             "rank_one": lambda d: dict(rank_one_degree=d + 1, split_degree=no),
+             "split": lambda d: dict(rank_one_degree=-1, split_degree=max(2, d // 4))},
+        64: {"gram_cuda_core": dict(flags=bp.BPMF_CUDA_CORE_GRAM, rank_one_degree=-1,
+                                    split_degree=no),
+             "rank_one": lambda d: dict(flags=bp.BPMF_CUDA_CORE_GRAM, rank_one_degree=d + 1,
+                                        split_degree=no),
+             "split_cuda_core": lambda d: dict(flags=bp.BPMF_CUDA_CORE_GRAM, rank_one_degree=-1,
+                                               split_degree=max(2, d // 4)),
+             "tensor_core": dict(rank_one_degree=-1, split_degree=no)},
+    }
+
+    def phase_ms(prob, kw):
+        st = torch.cuda.Stream()
+        params = bp.bpmf_default_params(alpha=prob.alpha, seed=1, **kw)
+        h = bp.bpmf_create(prob.M, prob.N, prob.K, prob.csr_ptr, prob.csr_col, prob.csr_val,
+                           params=params, stream=st.cuda_stream)
+        try:
+            bp.bpmf_step(h, bp.BPMF_PHASE_ROWS_USER)
+            ts = []
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                bp.bpmf_step(h, bp.BPMF_PHASE_ROWS_USER)
+                e1.record(st)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            if bp.bpmf_status(h) != 0:
+                raise bp.BpmfError(bp.bpmf_status(h), "fig3")
+            return float(np.median(ts))
+        finally:
+            bp.bpmf_destroy(h)
+
+    table = {}
+    for K, rs in routes.items():
+        table[K] = {name: {} for name in rs}
+        for d in degrees:
+            M = int(max(256, min(20000, 4_000_000 // d)))
+            N = max(2 * d, 2000)
+            many = workloads.fixed_degree(M, N, K, d, seed=d)
+            one = workloads.fixed_degree(1, N, K, d, seed=d)
+            for name, kw in rs.items():
+                kw = kw(d) if callable(kw) else kw
+                t_many = phase_ms(many, kw)
+                t_one = phase_ms(one, kw)
+                table[K][name][d] = [round(1e3 * t_many / M, 4), round(1e3 * t_one, 2)]
+    out = {"metric": "row update time against degree (us per row over many rows; us for one row)",
+           "data": "synthetic, every row of the phase with the same degree",
+           "degrees": degrees, "table": {str(k): v for k, v in table.items()}}
+    print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -584,6 +650,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-frac", type=float, default=0.1)
     ap.add_argument("--ref-frac", type=float, default=0.01)
+    ap.add_argument("--fig3", action="store_true",
+                    help="row update time against degree for every route (the paper's Fig. 3)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -593,6 +661,8 @@ def main(argv=None):
                           "one-at-a-time forms of this library"}), flush=True)
     elif args.impl == "reference":
         run_reference(args)
+    elif args.fig3:
+        run_fig3(args)
     elif args.config == 4:
         run_batched(args)
     elif args.config == 5:

@@ -304,6 +304,27 @@ def random_small(M, N, K, nnz, seed, n_test=0, empty_rows=0, empty_cols=0, alpha
                      alpha=alpha, seed=seed, burn_in=0, sweeps=4, noise_sd=0.3)
 
 
+def fixed_degree(M: int, N: int, K: int, d: int, seed: int = 0) -> Problem:
+    """Every row with exactly d ratings (columns (o_r + s k) mod N for k < d, with a random
+    offset o_r per row and a stride s coprime to N, so they are distinct), planted values
+    plus noise, no test set.  For per-row cost against degree (the paper's Fig. 3)."""
+    if d > N:
+        raise ValueError("degree above the column count")
+    rng = np.random.default_rng(seed)
+    s = 1 + 2 * int(rng.integers(0, N // 2))
+    while np.gcd(s, N) != 1:
+        s += 2
+    off = rng.integers(0, N, M)
+    cols = (off[:, None] + s * np.arange(d)[None, :]) % N
+    rows = np.repeat(np.arange(M), d)
+    U, V = _planted(rng, M, K), _planted(rng, N, K)
+    vals = _dot_rows(U, V, rows, cols.ravel()) + 0.3 * rng.standard_normal(M * d)
+    empty = np.zeros(0, np.int64)
+    return _assemble("fixed_degree_%d_%dx%d_K%d" % (d, M, N, K), M, N, K,
+                     (rows, cols.ravel(), vals), (empty, empty, np.zeros(0)), alpha=2.0,
+                     seed=seed, burn_in=0, sweeps=1, noise_sd=0.3)
+
+
 def config4(seed: int = 3, n_jobs: int = 256) -> list:
     """Many independent small jobs (batched form): per job M log-uniform in
     [1,000, 100,000], N log-uniform in [500, 10,000], density log-uniform in
