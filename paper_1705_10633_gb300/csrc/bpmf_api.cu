@@ -17,7 +17,7 @@ using namespace bpmf;
 
 namespace {
 
-constexpr int kDefaultLongMinDegree = 1;
+constexpr int kDefaultLongMinDegree = 48;
 constexpr int kDefaultLongShapeDegree = 1024;
 constexpr int kDefaultSplitDegree = 1024;
 constexpr int kDefaultRankOneDegree = 1;
@@ -62,7 +62,7 @@ struct DevSide {
 struct bpmf_ctx {
     int device = 0;
     int num_sms = 1;
-    int64_t long_min = 1;            // binning threshold of the tensor-core kernel
+    int64_t long_min = 48;           // binning threshold of the tensor-core kernel
     int64_t long_shape_degree = 1024;  // mean degree that selects the many-stage CTA shape
     int64_t split_degree = 1024;  // CUDA-core rows with this many ratings are split
     int rank_one_max = 0;  // CUDA-core rows with at most this many ratings: rank-one route

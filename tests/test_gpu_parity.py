@@ -171,8 +171,8 @@ def test_sweep_entry_point_matches_phases(bp, K, order):
     a = bp.create_from_problem(prob, order=order, stream=sa.cuda_stream)
     b = bp.create_from_problem(prob, order=order, stream=sb.cuda_stream)
     try:
-        if K == 64:
-            assert bp.bpmf_info(a, 0)["n_long"] > 0
+        if K == 64:  # movies on the tensor-core kernel, users on the CUDA-core one
+            assert bp.bpmf_info(a, 1)["n_long"] > 0 and bp.bpmf_info(a, 0)["n_short"] > 0
         ra = bp.bpmf_sweep(a, 3)
         seq = (bp.BPMF_PHASE_HYPER_MOVIE, bp.BPMF_PHASE_ROWS_MOVIE, bp.BPMF_PHASE_HYPER_USER,
                bp.BPMF_PHASE_ROWS_USER)
