@@ -159,8 +159,9 @@ def row_gather_bytes(nnz, rows, K, split=True):
 
 # DRAM bytes (read + write) per launch of the dominant row kernel, per workload and
 # phase, from one ncu capture of this kernel version (null once the kernel changes):
-# the user launch of the 480k x 18k K = 64 workload, scaled x 5.0 from its 96k-row slice.
-TRAFFIC = {"config3_480kx18k_K64": {"rows_user": 929e6}}
+# the tensor-core user launch of the 480k x 18k K = 64 workload (its 352,197 rows of 48
+# ratings or more), scaled x 4.99 from its 96k-row slice.
+TRAFFIC = {"config3_480kx18k_K64": {"rows_user": 891e6}}
 
 
 def finite_or_none(x):
@@ -271,13 +272,20 @@ def run_native(args):
         nph = max(2, min(5, args.steps))
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(phases) + 1)]
               for _ in range(nph)]
+        # the library's own events around each row phase's CUDA-core and tensor-core
+        # launches (on the handle's stream)
+        bp.bpmf_set_row_timing(h, True)
+        launch_ms = {"rows_movie": [], "rows_user": []}
         with torch.cuda.stream(stream):
             for s_ in range(nph):
                 for p_, ph in enumerate(phases):
                     ev[s_][p_].record(stream)
                     bp.bpmf_step(h, ph)
+                    if names[p_] in launch_ms:
+                        launch_ms[names[p_]].append(bp.bpmf_row_launch_ms(h))
                 ev[s_][-1].record(stream)
         torch.cuda.synchronize(dev)
+        bp.bpmf_set_row_timing(h, False)
         phase_ms = {n: sum(ev[s_][p_].elapsed_time(ev[s_][p_ + 1]) for s_ in range(nph))
                     / nph for p_, n in enumerate(names)}
         phase_sweep_ms = sum(phase_ms.values())
@@ -298,8 +306,21 @@ def run_native(args):
     tc_path = (K + 15) // 16 * 16 == 64
     dom = max(("rows_movie", "rows_user"), key=lambda n: phase_ms[n])
     dom_rows = prob.N if dom == "rows_movie" else prob.M
-    t_dom = phase_ms[dom] / 1e3
-    alu = row_alu_flops(dom_rows, K) + (0.0 if tc_path else row_gram_flops(nnz, K))
+    # the phase's rows split by kernel: the short bin (n_short smallest degrees) on the
+    # CUDA-core kernel, the rest on the tensor-core kernel when K pads to 64
+    info_d = info_u if dom == "rows_user" else info_v
+    deg = np.sort(np.diff(prob.csr_ptr) if dom == "rows_user" else prob.col_degrees())
+    n_short = int(info_d["n_short"])
+    short_ratings = int(deg[:n_short].sum())
+    n_long, long_ratings = dom_rows - n_short, nnz - short_ratings
+    t_cc = float(np.mean([a for a, _ in launch_ms[dom]])) / 1e3
+    t_tc = float(np.mean([b for _, b in launch_ms[dom]])) / 1e3
+    if tc_path and n_long > 0:
+        kern, t_dom, units = "rows_tc_kernel", t_tc, (n_long, long_ratings)
+        alu = row_alu_flops(n_long, K)
+    else:
+        kern, t_dom, units = "rows_warp_kernel", t_cc, (dom_rows, nnz)
+        alu = row_alu_flops(dom_rows, K) + row_gram_flops(nnz, K)
     achieved = alu / t_dom / 1e12
     peaks = load_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
@@ -307,12 +328,13 @@ def run_native(args):
     fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
     tc_peak = peaks.get("bf16_tflops_sustained", 1700.0)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    gram = row_gram_flops(nnz, K)
+    gram = row_gram_flops(units[1], K)
     other = "rows_movie" if dom == "rows_user" else "rows_user"
     other_rows = prob.N if other == "rows_movie" else prob.M
     gather = row_gather_bytes(nnz, other_rows, K)
     roofline = {"bound": "alu",
-                "kernel": "%s (%s)" % ("rows_tc_kernel" if tc_path else "rows_warp_kernel", dom),
+                "kernel": "%s (%s: %d rows, %d ratings)" % (kern, dom, units[0], units[1]),
+                "launch_ms": round(t_dom * 1e3, 4),
                 "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / fp32_peak, 4),
                 "traffic": TRAFFIC.get(prob.name, {}).get(dom),
@@ -333,6 +355,14 @@ def run_native(args):
                    if tc_path else {}),
                 "phase_note": "phases timed one by one (hyper steps not overlapped, all SMs to "
                               "the row kernel); %.2f ms per sweep that way" % phase_sweep_ms}
+    if tc_path and n_long > 0 and n_short > 0:
+        cc_flops = row_alu_flops(n_short, K) + row_gram_flops(short_ratings, K)
+        roofline["cuda_core_launch"] = {
+            "kernel": "rows_warp_kernel (%s: %d rows below the tensor-core threshold, %d "
+                      "ratings)" % (dom, n_short, short_ratings),
+            "launch_ms": round(t_cc * 1e3, 4),
+            "achieved": round(cc_flops / t_cc / 1e12, 3), "unit": "TFLOP/s",
+            "frac": round(cc_flops / t_cc / 1e12 / fp32_peak, 4)}
 
     e2e = None
     if not args.no_e2e:

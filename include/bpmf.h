@@ -215,6 +215,16 @@ int bpmf_info(bpmf_handle h, int32_t side, int64_t* n_short, int64_t* n_long, in
 int bpmf_launch_count(bpmf_handle h, int64_t* launches);
 
 /*
+ * Launch timing of the row phases run by bpmf_step (not inside bpmf_sweep, whose sweeps
+ * may be a captured CUDA graph).  on != 0: each row phase records CUDA events on the
+ * handle's stream around its CUDA-core launches and its tensor-core launch.
+ * bpmf_row_launch_ms waits for the last timed row phase and returns each part's
+ * milliseconds, -1 for a part that did not launch (or when timing is off).
+ */
+int bpmf_set_row_timing(bpmf_handle h, int32_t on);
+int bpmf_row_launch_ms(bpmf_handle h, float* cuda_core_ms, float* tensor_core_ms);
+
+/*
  * Row statistics of a device matrix, computed without allocating any memory.
  * The paper has no counterpart to this entry point; it exists for callers that
  * cannot allocate device memory when they need the reduction (for example a

@@ -85,6 +85,8 @@ def lib():
     L.bpmf_status.argtypes = [vp]
     L.bpmf_info.argtypes = [vp, i32, P(i64), P(i64), P(i64), P(i64), P(C.c_double), P(i64)]
     L.bpmf_launch_count.argtypes = [vp, P(i64)]
+    L.bpmf_set_row_timing.argtypes = [vp, i32]
+    L.bpmf_row_launch_ms.argtypes = [vp, P(C.c_float), P(C.c_float)]
     L.bpmf_row_stats_noalloc.argtypes = [vp, i64, i32, vp, vp, vp, vp]
     L.bpmf_strerror.argtypes = [C.c_int]
     L.bpmf_strerror.restype = C.c_char_p
@@ -276,6 +278,19 @@ def bpmf_info(h, side):
             "n_segments": nsg.value, "rbar": rb.value, "device_bytes": nb.value}
 
 
+def bpmf_set_row_timing(h, on=True):
+    """Record CUDA events around the row kernels of phases run by bpmf_step."""
+    _check(lib().bpmf_set_row_timing(h, 1 if on else 0), "bpmf_set_row_timing")
+
+
+def bpmf_row_launch_ms(h):
+    """(CUDA-core ms, tensor-core ms) of the last timed row phase; -1 for a part that did
+    not launch."""
+    a, b = C.c_float(), C.c_float()
+    _check(lib().bpmf_row_launch_ms(h, C.byref(a), C.byref(b)), "bpmf_row_launch_ms")
+    return a.value, b.value
+
+
 def bpmf_launch_count(h):
     n = C.c_int64()
     _check(lib().bpmf_launch_count(h, C.byref(n)), "bpmf_launch_count")
@@ -310,6 +325,7 @@ EXPORTED = ["bpmf_default_params", "bpmf_create", "bpmf_sweep", "bpmf_sweep_batc
             "bpmf_predict",
             "bpmf_get_state", "bpmf_set_state", "bpmf_get_accum", "bpmf_set_accum",
             "bpmf_get_stats", "bpmf_debug_means", "bpmf_status", "bpmf_info", "bpmf_launch_count",
+            "bpmf_set_row_timing", "bpmf_row_launch_ms",
             "bpmf_row_stats_noalloc",
             "bpmf_strerror",
             "bpmf_destroy"]

@@ -95,6 +95,10 @@ struct bpmf_ctx {
     std::vector<void*> allocs;
     int64_t bytes = 0;
     int64_t launches = 0;  // kernels launched by the phases
+    // bpmf_set_row_timing: events around the row kernels of phases run by bpmf_step
+    bool row_timing = false;
+    cudaEvent_t tev[3] = {nullptr, nullptr, nullptr};
+    int timed_parts = 0;  // bit 0: CUDA-core launches recorded, bit 1: tensor-core launch
 };
 
 namespace {
@@ -374,7 +378,9 @@ int phase_hyper(bpmf_ctx* h, int s, cudaStream_t st, uint32_t sweep_offset)
     return cuda_rc(launch_nw_sample(a, st));
 }
 
-int phase_rows(bpmf_ctx* h, int s)
+// timed: record events around the CUDA-core and tensor-core launches (bpmf_step only,
+// never inside a captured sweep)
+int phase_rows(bpmf_ctx* h, int s, bool timed = false)
 {
     DevSide& d = h->side[s];
     const DevSide& o = h->side[1 - s];
@@ -416,10 +422,16 @@ int phase_rows(bpmf_ctx* h, int s)
     a.part = d.part;
     a.seg_done = d.seg_done;
     a.nrank_one = d.n_rank_one;
-    if (a.nrows > 0) {
+    timed = timed && h->row_timing;
+    if (timed) {
+        h->timed_parts = (a.nrows > 0 ? 1 : 0) | (d.n_long > 0 ? 2 : 0);
+        e = cudaEventRecord(h->tev[0], h->stream);
+    }
+    if (e == cudaSuccess && a.nrows > 0) {
         h->launches += rows_warp_launches(a);
         e = launch_rows_warp(a, h->kp, h->row_sms, h->stream);
     }
+    if (e == cudaSuccess && timed) e = cudaEventRecord(h->tev[1], h->stream);
     a.nsegs = a.nsplit = a.nrank_one = 0;
     a.rows = d.bin_rows + d.n_short;
     a.nrows = d.n_long;
@@ -427,6 +439,7 @@ int phase_rows(bpmf_ctx* h, int s)
         h->launches += 1;
         e = launch_rows_tc(a, d.long_ratings, h->long_shape_degree, h->row_sms, h->stream);
     }
+    if (e == cudaSuccess && timed) e = cudaEventRecord(h->tev[2], h->stream);
     return cuda_rc(e);
 }
 
@@ -447,13 +460,14 @@ int phase_predict(bpmf_ctx* h)
     return cuda_rc(e);
 }
 
-int run_phase(bpmf_ctx* h, int phase)
+// timed: bpmf_step's call (row phases may record their launch events)
+int run_phase(bpmf_ctx* h, int phase, bool timed = false)
 {
     switch (phase) {
     case BPMF_PHASE_HYPER_USER: return phase_hyper(h, BPMF_USER, h->stream, 0);
     case BPMF_PHASE_HYPER_MOVIE: return phase_hyper(h, BPMF_MOVIE, h->stream, 0);
-    case BPMF_PHASE_ROWS_USER: return phase_rows(h, BPMF_USER);
-    case BPMF_PHASE_ROWS_MOVIE: return phase_rows(h, BPMF_MOVIE);
+    case BPMF_PHASE_ROWS_USER: return phase_rows(h, BPMF_USER, timed);
+    case BPMF_PHASE_ROWS_MOVIE: return phase_rows(h, BPMF_MOVIE, timed);
     case BPMF_PHASE_PREDICT: return phase_predict(h);
     case BPMF_PHASE_ADVANCE: h->launches += 1; return cuda_rc(launch_advance(h->ctl, h->stream));
     default: return BPMF_EINVAL;
@@ -508,6 +522,8 @@ int bpmf_destroy(bpmf_handle h)
     }
     if (h->sweep_graph) cudaGraphExecDestroy(h->sweep_graph);
     for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->tev)
         if (e) cudaEventDestroy(e);
     for (void* ptr : h->allocs) {
         if (h->p.free) h->p.free(ptr, (void*)h->stream, h->p.alloc_ctx);
@@ -762,7 +778,7 @@ int bpmf_set_tuning(bpmf_handle h, int32_t long_min_degree, int32_t long_shape_d
 int bpmf_step(bpmf_handle h, int32_t phase)
 {
     if (!h) return BPMF_EINVAL;
-    return run_phase(h, phase);
+    return run_phase(h, phase, true);
 }
 
 namespace {
@@ -1094,6 +1110,39 @@ int bpmf_status(bpmf_handle h)
 {
     if (!h) return BPMF_EINVAL;
     return sync_status(h);
+}
+
+int bpmf_set_row_timing(bpmf_handle h, int32_t on)
+{
+    if (!h) return BPMF_EINVAL;
+    if (on && !h->tev[0]) {
+        for (cudaEvent_t& e : h->tev) {
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return BPMF_ECUDA;
+            }
+        }
+    }
+    h->row_timing = on != 0;
+    h->timed_parts = 0;
+    return BPMF_OK;
+}
+
+int bpmf_row_launch_ms(bpmf_handle h, float* cuda_core_ms, float* tensor_core_ms)
+{
+    if (!h || !cuda_core_ms || !tensor_core_ms) return BPMF_EINVAL;
+    *cuda_core_ms = *tensor_core_ms = -1.f;
+    if (!h->row_timing || !h->timed_parts) return BPMF_OK;
+    if (cudaEventSynchronize(h->tev[2]) != cudaSuccess) return BPMF_ECUDA;
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, h->tev[0], h->tev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&b, h->tev[1], h->tev[2]) != cudaSuccess) {
+        cudaGetLastError();
+        return BPMF_ECUDA;
+    }
+    if (h->timed_parts & 1) *cuda_core_ms = a;
+    if (h->timed_parts & 2) *tensor_core_ms = b;
+    return BPMF_OK;
 }
 
 int bpmf_launch_count(bpmf_handle h, int64_t* launches)
