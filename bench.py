@@ -237,8 +237,10 @@ def run_native(args):
     tuning = None
     try:
         if args.autotune:
-            from paper_1705_10633_gb300.autotune import autotune
-            best, times = autotune(h, prob.M, prob.N, K, stream.cuda_stream)
+            from paper_1705_10633_gb300.autotune import TuningCache, autotune
+            cache = TuningCache(args.tuning_cache) if args.tuning_cache else None
+            best, times = autotune(h, prob.M, prob.N, K, stream.cuda_stream, cache=cache,
+                                   degrees=(np.diff(prob.csr_ptr), prob.col_degrees()))
             tuning = {"long_min_degree": best[0], "long_shape_degree": best[1],
                       "split_degree": best[2], "rank_one_degree": best[3],
                       "trials_ms": {"%d/%d/%d/%d" % k: round(v, 3) for k, v in sorted(times.items())}}
@@ -676,6 +678,8 @@ def main(argv=None):
                     help="BF16-input tensor-core Gram (lower precision; not the headline)")
     ap.add_argument("--autotune", action="store_true",
                     help="tune the row kernels' thresholds on the workload before timing")
+    ap.add_argument("--tuning-cache", default=None,
+                    help="with --autotune: JSON file of tunings by workload shape (reused on a hit)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-frac", type=float, default=0.1)

@@ -18,6 +18,10 @@ the chain (the row phases do not touch the running prediction sums).
 from __future__ import annotations
 
 import itertools
+import json
+import os
+
+import numpy as np
 
 LONG_MIN_CANDIDATES = (1, 16, 48, 128)
 SHAPE_CANDIDATES = (256, 1024, 4096, 1 << 30)
@@ -25,14 +29,62 @@ SPLIT_CANDIDATES = (128, 512, 1024, 4096, 1 << 30)
 RANK_ONE_CANDIDATES = (-1, 2, 4)
 
 
+def tuning_key(K, deg_users, deg_movies, device):
+    """Cache key of a job for its tuning: K padded to the kernels' width, the device name,
+    and for each side the power-of-two buckets of its degree quantiles 0.5, 0.9 and 0.99,
+    with the side's size to an order of magnitude -- jobs whose rows bin alike tune alike
+    (a quantile on a bucket's edge can split resamples of one distribution)."""
+    def shape(d):
+        d = np.maximum(np.asarray(d, dtype=np.float64), 1.0)
+        return [int(np.floor(np.log2(q))) for q in np.quantile(d, [0.5, 0.9, 0.99])]
+
+    return json.dumps({"kp": (int(K) + 15) // 16 * 16, "device": str(device),
+                       "users": shape(deg_users), "movies": shape(deg_movies),
+                       "size": [len(str(len(deg_users))), len(str(len(deg_movies)))]},
+                      sort_keys=True)
+
+
+class TuningCache:
+    """Tunings by `tuning_key`, kept in a JSON file (written on every store)."""
+
+    def __init__(self, path):
+        self.path = path
+        self.entries = {}
+        if path and os.path.exists(path):
+            with open(path) as f:
+                self.entries = {k: tuple(v) for k, v in json.load(f).items()}
+
+    def get(self, key):
+        return self.entries.get(key)
+
+    def put(self, key, tuning):
+        self.entries[key] = tuple(int(x) for x in tuning)
+        if self.path:
+            tmp = self.path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump({k: list(v) for k, v in self.entries.items()}, f, indent=1)
+            os.replace(tmp, self.path)
+
+
 def autotune(h, M, N, K, stream, long_min=LONG_MIN_CANDIDATES, shape=SHAPE_CANDIDATES,
-             split=SPLIT_CANDIDATES, rank_one=RANK_ONE_CANDIDATES, reps=2):
+             split=SPLIT_CANDIDATES, rank_one=RANK_ONE_CANDIDATES, reps=2, cache=None,
+             degrees=None):
     """Returns ((long_min_degree, long_shape_degree, split_degree, rank_one_degree),
     {tuple: ms for one pass of both row phases}).  `stream` is the raw cudaStream_t the
-    handle was created with.  0 in a tuple is the library default."""
+    handle was created with.  0 in a tuple is the library default.  With a `TuningCache`
+    and the job's `degrees` (users', movies'), a cached tuning for the same key is applied
+    without trials (the dict is then empty) and a new one is stored."""
     import torch
 
     import paper_1705_10633_gb300 as bp
+
+    key = None
+    if cache is not None and degrees is not None:
+        key = tuning_key(K, degrees[0], degrees[1], torch.cuda.get_device_name())
+        hit = cache.get(key)
+        if hit is not None:
+            bp.bpmf_set_tuning(h, *hit)
+            return tuple(hit), {}
 
     st = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
     U, V, hyper, sweep = bp.bpmf_get_state(h, M, N, K)
@@ -68,4 +120,6 @@ def autotune(h, M, N, K, stream, long_min=LONG_MIN_CANDIDATES, shape=SHAPE_CANDI
         bp.bpmf_set_tuning(h, *best)
     finally:
         bp.bpmf_set_state(h, U, V, hyper, sweep)
+    if key is not None:
+        cache.put(key, best)
     return best, times

@@ -125,6 +125,7 @@ class Server:
         self.backend = backend if backend is not None else DeviceBackend()
         self._pending = []  # (job, future, estimate) in arrival order
         self._active = []   # dicts: job, future, handle, left, bytes, admitted_at
+        self._cancel = set()  # futures of admitted jobs to drop at the next round boundary
         self._cv = threading.Condition()
         self._closing = False
         self.memory_in_use = 0
@@ -147,6 +148,24 @@ class Server:
             self._pending.append((job, fut, est))
             self._cv.notify()
         return fut
+
+    def cancel(self, fut) -> bool:
+        """Cancel a submitted job: a queued job is dropped at once; an admitted one at the
+        next round boundary (no sweep is interrupted), its handle destroyed and its memory
+        returned.  The future then raises CancelledError.  False if it already finished."""
+        with self._cv:
+            if fut.done():
+                return False
+            for k, (job, f, est) in enumerate(self._pending):
+                if f is fut:
+                    del self._pending[k]
+                    fut.cancel()
+                    return True
+            if any(a["fut"] is fut for a in self._active):
+                self._cancel.add(fut)
+                self._cv.notify()
+                return True
+        return False
 
     def close(self, wait=True):
         with self._cv:
@@ -175,7 +194,24 @@ class Server:
             self._active.append({"job": job, "fut": fut, "handle": handle, "left": job.sweeps,
                                  "bytes": real, "admitted_at": time.perf_counter()})
 
+    def _drop_cancelled(self):
+        with self._cv:
+            drop = [a for a in self._active if a["fut"] in self._cancel]
+            self._cancel.clear()
+        if not drop:
+            return
+        self._active = [a for a in self._active if all(a is not d for d in drop)]
+        for a in drop:
+            try:
+                self.backend.destroy(a["handle"])
+            finally:
+                self.memory_in_use -= a["bytes"]
+                a["fut"].cancel()
+
     def _round(self):
+        self._drop_cancelled()
+        if not self._active:
+            return
         groups = {}
         for a in self._active:
             n = min(self.sweeps_per_round, a["left"])

@@ -97,3 +97,29 @@ def test_autotune_split_degree_below_k64(bp):
         assert bp.bpmf_status(h) == 0
     finally:
         bp.bpmf_destroy(h)
+
+
+def test_autotune_cache_hit_applies_the_stored_tuning(bp, tmp_path):
+    import torch
+
+    from paper_1705_10633_gb300.autotune import TuningCache, autotune
+    prob = workloads.random_small(500, 100, 24, 20000, seed=73, n_test=50, long_rows=3,
+                                  long_deg=90)
+    degs = (np.diff(prob.csr_ptr), prob.col_degrees())
+    cache = TuningCache(str(tmp_path / "tuning.json"))
+    st = torch.cuda.Stream()
+    a = bp.create_from_problem(prob, stream=st.cuda_stream)
+    b = bp.create_from_problem(prob, stream=st.cuda_stream)
+    try:
+        best, times = autotune(a, prob.M, prob.N, prob.K, st.cuda_stream, split=(32, 1 << 30),
+                               rank_one=(-1,), cache=cache, degrees=degs)
+        assert times and best in times
+        hit, times2 = autotune(b, prob.M, prob.N, prob.K, st.cuda_stream, cache=TuningCache(
+            str(tmp_path / "tuning.json")), degrees=degs)
+        assert times2 == {} and hit == best
+        for side in (0, 1):
+            ia, ib = bp.bpmf_info(a, side), bp.bpmf_info(b, side)
+            assert (ia["n_split"], ia["n_segments"]) == (ib["n_split"], ib["n_segments"])
+    finally:
+        bp.bpmf_destroy(a)
+        bp.bpmf_destroy(b)

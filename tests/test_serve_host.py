@@ -107,3 +107,28 @@ def test_closed_server_rejects_jobs():
     srv.close()
     with pytest.raises(RuntimeError):
         srv.submit(_job(1))
+
+
+def test_cancel_queued_and_running_jobs():
+    import concurrent.futures as cf
+    be = FakeBackend(delay=0.01)
+    srv = Server(memory_limit=1e12, max_active=1, sweeps_per_round=1, backend=be)
+    try:
+        running = srv.submit(_job(1, sweeps=10_000))  # admitted, ~100 s of rounds
+        queued = srv.submit(_job(2))                   # waits for the only slot
+        deadline = time.time() + 5
+        while be.created < 1 and time.time() < deadline:
+            time.sleep(0.005)
+        assert be.created == 1
+        assert srv.cancel(queued) and queued.cancelled()
+        assert srv.cancel(running)
+        with pytest.raises(cf.CancelledError):
+            running.result(timeout=5)
+        later = srv.submit(_job(3, sweeps=3))
+        assert later.result(timeout=5).predictions[0] == 3.0
+        assert not srv.cancel(later)  # already finished
+    finally:
+        srv.close()
+    assert be.order == [1, 3]          # the cancelled queued job was never created
+    assert be.active == set() and srv.memory_in_use == 0
+    assert be.swept[1] < 10_000
