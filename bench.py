@@ -293,6 +293,19 @@ def run_native(args):
         phase_sweep_ms = sum(phase_ms.values())
         info_u = bp.bpmf_info(h, 0)
         info_v = bp.bpmf_info(h, 1)
+        if args.log_jsonl and rank == 0:
+            # per-sweep log after the measurement: one bpmf_sweep call per record, its RMSEs
+            # read back (wall clock, so each record includes the read)
+            done = args.warmup + args.steps + nph  # sweeps run so far on this handle
+            with open(args.log_jsonl, "a") as f:
+                for k in range(args.steps):
+                    t_a = time.perf_counter()
+                    r_s, r_a = bp.bpmf_sweep(h, 1)
+                    t_ms = (time.perf_counter() - t_a) * 1e3
+                    f.write(json.dumps({"job": prob.name, "sweep": done + k + 1,
+                                        "rmse_sample": finite_or_none(r_s),
+                        "rmse_avg": finite_or_none(r_a), "t_ms": round(t_ms, 4),
+                        "rows_per_s": round((prob.M + prob.N) / (t_ms / 1e3), 1)}) + "\n")
     finally:
         bp.bpmf_destroy(h)
 
@@ -684,6 +697,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-frac", type=float, default=0.1)
     ap.add_argument("--ref-frac", type=float, default=0.01)
+    ap.add_argument("--log-jsonl", default=None,
+                    help="append one JSON record per sweep (sweep, RMSEs, time) after the run")
     ap.add_argument("--fig3", action="store_true",
                     help="row update time against degree for every route (the paper's Fig. 3)")
     args = ap.parse_args(argv)

@@ -9,6 +9,8 @@
 #include <numeric>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "bpmf.h"
 #include "bpmf_internal.cuh"
 #include "philox.cuh"
@@ -460,9 +462,29 @@ int phase_predict(bpmf_ctx* h)
     return cuda_rc(e);
 }
 
+// Host-side NVTX range for the lifetime of a scope (annotates the enqueue of a phase or a
+// sweep call for a profiler's timeline; a no-op without a tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
+const char* phase_name(int phase)
+{
+    switch (phase) {
+    case BPMF_PHASE_HYPER_USER: return "bpmf hyper users";
+    case BPMF_PHASE_HYPER_MOVIE: return "bpmf hyper movies";
+    case BPMF_PHASE_ROWS_USER: return "bpmf rows users";
+    case BPMF_PHASE_ROWS_MOVIE: return "bpmf rows movies";
+    case BPMF_PHASE_PREDICT: return "bpmf predict";
+    default: return "bpmf advance";
+    }
+}
+
 // timed: bpmf_step's call (row phases may record their launch events)
 int run_phase(bpmf_ctx* h, int phase, bool timed = false)
 {
+    const NvtxRange range(phase_name(phase));
     switch (phase) {
     case BPMF_PHASE_HYPER_USER: return phase_hyper(h, BPMF_USER, h->stream, 0);
     case BPMF_PHASE_HYPER_MOVIE: return phase_hyper(h, BPMF_MOVIE, h->stream, 0);
@@ -911,6 +933,7 @@ int read_rmse(bpmf_ctx* h, double* rmse_sample, double* rmse_avg)
 int bpmf_sweep(bpmf_handle h, int32_t n_sweeps, double* rmse_sample, double* rmse_avg)
 {
     if (!h || n_sweeps < 0) return BPMF_EINVAL;
+    const NvtxRange range("bpmf_sweep");
     if (n_sweeps > 0 && h->num_sms >= 8) {
         const int first = h->p.order == 0 ? BPMF_MOVIE : BPMF_USER;
         int rc = sweep_begin(h, first);
