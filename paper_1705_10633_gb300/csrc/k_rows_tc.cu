@@ -41,7 +41,6 @@ constexpr int kKT = 64;
 constexpr int kStageRatings = 64;
 constexpr int kNAcc = 3;
 constexpr int kChunkStages = 16;  // stages per TMEM accumulation before it is flushed
-constexpr int kGatherThreads = 64;
 constexpr int kRowRing = 32;   // row descriptors in flight
 constexpr int kIdxRing = 8;    // stages of rating indices / values in flight
 constexpr uint32_t kTmemCols = 512;
@@ -56,16 +55,22 @@ constexpr uint32_t kLamFloats = 64 * 64 + 64;
 constexpr uint32_t kCholScratchFloats = 2 * 64 + 64 + 64;
 
 // Two shapes of the CTA, chosen per launch by the rows' mean degree:
-//   NCHOL Cholesky warps (and Lambda buffers) and NSTAGE gather stages.
-// Rows of a few hundred ratings need many rows in factorisation at once (8, 3);
+//   NCHOL Cholesky warps (and Lambda buffers), NSTAGE gather stages and EXTRA gather
+//   warps beside warps 2-3.
+// Rows of a few hundred ratings need many rows in factorisation at once (8, 3, 0);
 // rows of thousands of ratings, whose gathered rows come partly from HBM, need
-// more copies in flight and few rows in factorisation (4, 6).  Registers after
-// setmaxnreg: warps 0-3 kProdRegs, drain kDrainRegs, Cholesky kCholRegs.
-template <int NCHOL, int NSTAGE>
+// more copies in flight and more threads issuing them, and few rows in factorisation
+// (2, 7, 2).  Warps: 0 MMA, 1 prefetch, 2-3 gather, 4-7 drain (TMEM lane quarters
+// 0-3), 8 .. 7 + EXTRA gather, then the Cholesky warps.  Registers after setmaxnreg:
+// producers kProdRegs, drain kDrainRegs, Cholesky kCholRegs.
+template <int NCHOL, int NSTAGE, int EXTRA>
 struct TcShape {
     static constexpr int kNChol = NCHOL;
     static constexpr int kNStage = NSTAGE;
-    static constexpr int kThreads = (8 + NCHOL) * 32;
+    static constexpr int kGather = 64 + 32 * EXTRA;  // gather threads
+    static constexpr int kCholWarp0 = 8 + EXTRA;
+    static constexpr int kThreads = (8 + EXTRA + NCHOL) * 32;
+    static_assert(kGather == 64 || kGather == 128, "gather threads");
     static constexpr uint32_t kOffStages = 0;
     static constexpr uint32_t kOffLam = kOffStages + NSTAGE * kStageBytes;
     static constexpr uint32_t kOffChol = kOffLam + NCHOL * kLamFloats * 4;
@@ -81,10 +86,16 @@ struct TcShape {
     static constexpr int kDrainRegs = NCHOL == 8 ? 96 : 128;
     static constexpr int kCholRegs = NCHOL == 8 ? 168 : 176;
     static_assert(kSmemBytes <= 232448, "shared memory");
-    static_assert(32 * (4 * kProdRegs + 4 * kDrainRegs + NCHOL * kCholRegs) <= 65536, "registers");
+    static_assert(32 * ((4 + EXTRA) * kProdRegs + 4 * kDrainRegs + NCHOL * kCholRegs) <=
+                      kThreads * (65536 / kThreads / 8 * 8),
+                  "registers");
 };
-using ShapeShortRows = TcShape<8, 3>;
-using ShapeLongRows = TcShape<4, 6>;
+using ShapeShortRows = TcShape<8, 3, 0>;
+using ShapeLongRows = TcShape<2, 7, 2>;
+// The BF16 Gram gathers half the bytes (h rows only): its long rows run better with
+// four factorisation warps and 64 gather threads (measured: movie launch 5.00 against
+// 5.73 ms with the shape above, which takes the FP16 split's from 6.08 to 5.87 ms).
+using ShapeLongRowsBf16 = TcShape<4, 6, 0>;
 
 // Instruction descriptor of kind::f16: D = F32, A = B = F16, both MN-major.
 constexpr uint32_t make_idesc(int M, int N)
@@ -327,7 +338,7 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
                         kThreads);
     if (tid == 0) {
         for (int s = 0; s < kNStage; ++s) {
-            mbar_init(bar_stage_full + 8 * s, kGatherThreads);
+            mbar_init(bar_stage_full + 8 * s, Shape::kGather);
             mbar_init(bar_stage_empty + 8 * s, 1);
         }
         for (int s = 0; s < kNAcc; ++s) {
@@ -344,7 +355,7 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
         }
         for (int s = 0; s < kIdxRing; ++s) {
             mbar_init(bar_idx_full + 8 * s, 32);
-            mbar_init(bar_idx_empty + 8 * s, kGatherThreads);
+            mbar_init(bar_idx_empty + 8 * s, Shape::kGather);
         }
         mbar_init(bar_final, 1);
         *abort_flag = 0;
@@ -365,6 +376,92 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
     const uint32_t tmem_base = *tmem_slot;
     const uint32_t sweep = (uint32_t)a.ctl->sweep;
     constexpr int64_t kChunkRatings = (int64_t)kChunkStages * kStageRatings;
+
+    // ======================= gather (warps 2-3 and the extra gather warps) ==========
+    // gt: this thread's index among the kGather gather threads
+    constexpr int kGatherN = Shape::kGather;
+    constexpr int kRps = kGatherN / 16, kRpsB = kGatherN / 8;  // ratings per copy round
+    constexpr int kCopies = kBf16 ? 512 / kGatherN : 1024 / kGatherN;
+    auto gather_role = [&](const int gt) {
+        uint32_t g = 0;
+        bool ok = true;
+        for (int64_t j = 0; j < nj && ok; ++j) {
+            const int rs = (int)(j % kRowRing);
+            if (!wait_bounded(bar_row_full + 8 * rs, (uint32_t)((j / kRowRing) & 1), wc)) break;
+            const int64_t p0 = row_ring[4 * rs + 1], p1 = row_ring[4 * rs + 2];
+            for (int64_t base = p0; base < p1; base += kStageRatings, ++g) {
+                const uint32_t is = g % kIdxRing, s = g % kNStage;
+                if (!wait_bounded(bar_idx_full + 8 * is, (g / kIdxRing) & 1u, wc) ||
+                    !wait_bounded(bar_stage_empty + 8 * s, ((g / kNStage) & 1u) ^ 1u, wc)) {
+                    ok = false;
+                    break;
+                }
+                const int cnt = (int)min((int64_t)kStageRatings, p1 - base);
+                // this thread's rows (-1 past the row's end), read before the slot is
+                // released: FP16 split, rating (gt >> 4) + kRps k, 16-B chunk gt & 15 of
+                // its h and l rows; BF16, rating (gt >> 3) + kRpsB k, chunk gt & 7 of its
+                // h row (kRps = gather threads / 16 ratings per round)
+                int cols[kCopies];
+                if constexpr (!kBf16) {
+#pragma unroll
+                    for (int k = 0; k < kCopies; ++k) {
+                        const int qq = (gt >> 4) + kRps * k;
+                        cols[k] = qq < cnt ? idx_ring[is * 128 + qq] : -1;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < kCopies; ++k) {
+                        const int qq = (gt >> 3) + kRpsB * k;
+                        cols[k] = qq < cnt ? idx_ring[is * 128 + qq] : -1;
+                    }
+                }
+                // the first 64 threads also carry the stage's 64 rating values
+                const float rv = gt < 64 && gt < cnt ? val_ring[is * 128 + gt] : 0.f;
+                mbar_arrive(bar_idx_empty + 8 * is);
+                const uint32_t sH = sbase + kOffStages + s * kStageBytes;
+                const uint32_t sL = sH + kTileBytes;
+                const uint32_t sR = sL + kTileBytes;
+                if constexpr (!kBf16) {
+                    const int c = gt & 15, ch = c & 7;
+                    const __half* Ysrc = (c >> 3) ? a.Yl : a.Yh;
+                    const uint32_t tile = (c >> 3) ? sL : sH;
+#pragma unroll
+                    for (int k = 0; k < kCopies; ++k) {
+                        const int qq = (gt >> 4) + kRps * k;
+                        const uint32_t dst = tile + qq * 128 + ((ch ^ (qq & 7)) << 4);
+                        if (cols[k] >= 0)
+                            cp_async16(dst, Ysrc + (int64_t)cols[k] * kKT + ch * 8, 16);
+                        else
+                            cp_async16(dst, a.Yh, 0);  // zero fill past the row's end
+                    }
+                } else {
+                    // h rows only; the l atom stays zero
+                    const int ch = gt & 7;
+#pragma unroll
+                    for (int k = 0; k < kCopies; ++k) {
+                        const int qq = (gt >> 3) + kRpsB * k;
+                        const uint32_t dst = sH + qq * 128 + ((ch ^ (qq & 7)) << 4);
+                        if (cols[k] >= 0)
+                            cp_async16(dst, a.Yh + (int64_t)cols[k] * kKT + ch * 8, 16);
+                        else
+                            cp_async16(dst, a.Yh, 0);
+                    }
+                }
+                if (gt < 64) {
+                    __half hi, lo;
+                    split16(rv, kBf16, hi, lo);
+                    const uint32_t packed = (uint32_t)__half_as_ushort(hi) |
+                                            ((uint32_t)__half_as_ushort(lo) << 16);
+                    asm volatile("st.shared.b32 [%0], %1;" ::"r"(sR + gt * 128 + ((gt & 7) << 4)),
+                                 "r"(packed)
+                                 : "memory");
+                }
+                fence_proxy_async();
+                if (!a.test_stall) cp_async_arrive(bar_stage_full + 8 * s);
+            }
+        }
+        cp_async_wait_all();
+    };
 
     if (warp < 4) {
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(Shape::kProdRegs) : "memory");
@@ -473,83 +570,7 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
             }
             cp_async_wait_all();
         } else {
-            // ======================= gather =======================
-            const int gt = tid - 64;  // 0..63
-            uint32_t g = 0;
-            bool ok = true;
-            for (int64_t j = 0; j < nj && ok; ++j) {
-                const int rs = (int)(j % kRowRing);
-                if (!wait_bounded(bar_row_full + 8 * rs, (uint32_t)((j / kRowRing) & 1), wc)) break;
-                const int64_t p0 = row_ring[4 * rs + 1], p1 = row_ring[4 * rs + 2];
-                for (int64_t base = p0; base < p1; base += kStageRatings, ++g) {
-                    const uint32_t is = g % kIdxRing, s = g % kNStage;
-                    if (!wait_bounded(bar_idx_full + 8 * is, (g / kIdxRing) & 1u, wc) ||
-                        !wait_bounded(bar_stage_empty + 8 * s, ((g / kNStage) & 1u) ^ 1u, wc)) {
-                        ok = false;
-                        break;
-                    }
-                    const int cnt = (int)min((int64_t)kStageRatings, p1 - base);
-                    // this thread's copies: id = gt + 64 k -> rating id / 16, 16-B chunk id % 16
-                    // this thread's rows (-1 past the row's end), read before the slot is
-                    // released: FP16 split, rating (gt >> 4) + 4k, 16-B chunk gt & 15 of its
-                    // h and l rows; BF16, rating (gt >> 3) + 8k, chunk gt & 7 of its h row
-                    int cols[16];
-                    if constexpr (!kBf16) {
-#pragma unroll
-                        for (int k = 0; k < 16; ++k) {
-                            const int qq = (gt >> 4) + 4 * k;
-                            cols[k] = qq < cnt ? idx_ring[is * 128 + qq] : -1;
-                        }
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const int qq = (gt >> 3) + 8 * k;
-                            cols[k] = qq < cnt ? idx_ring[is * 128 + qq] : -1;
-                        }
-                    }
-                    const float rv = gt < cnt ? val_ring[is * 128 + gt] : 0.f;
-                    mbar_arrive(bar_idx_empty + 8 * is);
-                    const uint32_t sH = sbase + kOffStages + s * kStageBytes;
-                    const uint32_t sL = sH + kTileBytes;
-                    const uint32_t sR = sL + kTileBytes;
-                    if constexpr (!kBf16) {
-                        const int c = gt & 15, ch = c & 7;
-                        const __half* Ysrc = (c >> 3) ? a.Yl : a.Yh;
-                        const uint32_t tile = (c >> 3) ? sL : sH;
-#pragma unroll
-                        for (int k = 0; k < 16; ++k) {
-                            const int qq = (gt >> 4) + 4 * k;
-                            const uint32_t dst = tile + qq * 128 + ((ch ^ (qq & 7)) << 4);
-                            if (cols[k] >= 0)
-                                cp_async16(dst, Ysrc + (int64_t)cols[k] * kKT + ch * 8, 16);
-                            else
-                                cp_async16(dst, a.Yh, 0);  // zero fill past the row's end
-                        }
-                    } else {
-                        // h rows only; the l atom stays zero
-                        const int ch = gt & 7;
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const int qq = (gt >> 3) + 8 * k;
-                            const uint32_t dst = sH + qq * 128 + ((ch ^ (qq & 7)) << 4);
-                            if (cols[k] >= 0)
-                                cp_async16(dst, a.Yh + (int64_t)cols[k] * kKT + ch * 8, 16);
-                            else
-                                cp_async16(dst, a.Yh, 0);
-                        }
-                    }
-                    __half hi, lo;
-                    split16(rv, kBf16, hi, lo);
-                    const uint32_t packed = (uint32_t)__half_as_ushort(hi) |
-                                            ((uint32_t)__half_as_ushort(lo) << 16);
-                    asm volatile("st.shared.b32 [%0], %1;" ::"r"(sR + gt * 128 + ((gt & 7) << 4)),
-                                 "r"(packed)
-                                 : "memory");
-                    fence_proxy_async();
-                    if (!a.test_stall) cp_async_arrive(bar_stage_full + 8 * s);
-                }
-            }
-            cp_async_wait_all();
+            gather_role(tid - 64);
         }
     } else if (warp < 8) {
         // ======================= TMEM drain =======================
@@ -614,10 +635,13 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
             mbar_arrive(bar_lam_full + 8 * b);
             named_bar(1, 128);  // rtmp is reused by the next row
         }
+    } else if (warp < Shape::kCholWarp0) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(Shape::kProdRegs) : "memory");
+        gather_role(64 + tid - 256);
     } else {
         // ======================= Cholesky, solve, sample =======================
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(Shape::kCholRegs) : "memory");
-        const int cw = warp - 8;
+        const int cw = warp - Shape::kCholWarp0;
         float* scratch = chol_scratch + cw * kCholScratchFloats;
         float* colbuf = scratch;
         float* dinv = scratch + 128;
@@ -674,7 +698,7 @@ cudaError_t launch_rows_tc(const RowArgs& a, int64_t nratings, int64_t shape_deg
     if (a.nrows <= 0) return cudaSuccess;
     const bool longrows = nratings >= shape_degree * a.nrows;
     if (a.bf16)
-        return longrows ? launch_shape<ShapeLongRows, true>(a, num_sms, s)
+        return longrows ? launch_shape<ShapeLongRowsBf16, true>(a, num_sms, s)
                         : launch_shape<ShapeShortRows, true>(a, num_sms, s);
     return longrows ? launch_shape<ShapeLongRows, false>(a, num_sms, s)
                     : launch_shape<ShapeShortRows, false>(a, num_sms, s);

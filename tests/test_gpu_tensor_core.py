@@ -42,7 +42,8 @@ def test_long_rows_tensor_core_parity(bp, K, long_min):
 
 def test_long_row_shape_parity(bp):
     # 40 movies with ~3,000 ratings each: the movie side's mean degree selects the CTA
-    # shape with 6 gather stages and 4 factorisation warps; rows span 1-3 chunks of
+    # shape with 7 gather stages, 128 gather threads and 2 factorisation warps (6, 64 and
+    # 4 under the BF16 Gram); rows span 1-3 chunks of
     # 1024 ratings (so a row's accumulator is drained more than once)
     prob = workloads.random_small(8000, 40, 64, 150000, seed=31, n_test=300)
     deg = prob.col_degrees()
