@@ -687,6 +687,16 @@ cudaError_t launch_shape(const RowArgs& a, int num_sms, cudaStream_t s)
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Shape::kSmemBytes);
     if (e != cudaSuccess) return e;
+    // setmaxnreg.inc takes registers that other warps released from what the CTA was
+    // launched with (the compiled count times the threads): if the split's total were
+    // above that, the Cholesky warps' increase would never be granted.  Refuse the
+    // launch instead (the compiled count can sit below the launch bound).
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, rows_tc_kernel<Shape, kBf16>);
+    if (e != cudaSuccess) return e;
+    const long split = 32L * ((4 + Shape::kCholWarp0 - 8) * Shape::kProdRegs +
+                              4 * Shape::kDrainRegs + Shape::kNChol * Shape::kCholRegs);
+    if (split > (long)fa.numRegs * Shape::kThreads) return cudaErrorInvalidConfiguration;
     int64_t grid = a.nrows < num_sms ? a.nrows : num_sms;
     rows_tc_kernel<Shape, kBf16><<<(unsigned)grid, Shape::kThreads, Shape::kSmemBytes, s>>>(a);
     return cudaGetLastError();
