@@ -272,8 +272,8 @@ def run_native(args):
         # phase breakdown (not part of the headline): phase-by-phase sweeps with
         # CUDA events on the same stream, for the roofline of the dominant launch
         nph = max(2, min(5, args.steps))
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(phases) + 1)]
-              for _ in range(nph)]
+        ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(len(phases))] for _ in range(nph)]
         # the library's own events around each row phase's CUDA-core and tensor-core
         # launches (on the handle's stream)
         bp.bpmf_set_row_timing(h, True)
@@ -281,14 +281,14 @@ def run_native(args):
         with torch.cuda.stream(stream):
             for s_ in range(nph):
                 for p_, ph in enumerate(phases):
-                    ev[s_][p_].record(stream)
+                    ev[s_][p_][0].record(stream)
                     bp.bpmf_step(h, ph)
-                    if names[p_] in launch_ms:
+                    ev[s_][p_][1].record(stream)
+                    if names[p_] in launch_ms:  # waits for the phase (after its end event)
                         launch_ms[names[p_]].append(bp.bpmf_row_launch_ms(h))
-                ev[s_][-1].record(stream)
         torch.cuda.synchronize(dev)
         bp.bpmf_set_row_timing(h, False)
-        phase_ms = {n: sum(ev[s_][p_].elapsed_time(ev[s_][p_ + 1]) for s_ in range(nph))
+        phase_ms = {n: sum(ev[s_][p_][0].elapsed_time(ev[s_][p_][1]) for s_ in range(nph))
                     / nph for p_, n in enumerate(names)}
         phase_sweep_ms = sum(phase_ms.values())
         info_u = bp.bpmf_info(h, 0)

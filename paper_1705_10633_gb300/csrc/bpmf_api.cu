@@ -350,12 +350,8 @@ int sync_status(bpmf_ctx* h)
 int phase_hyper(bpmf_ctx* h, int s, cudaStream_t st, uint32_t sweep_offset)
 {
     DevSide& d = h->side[s];
-    cudaError_t e = launch_hyper_shift(d.X, d.rows, h->K, h->kp, d.shift64, st);
-    if (e == cudaSuccess)
-        e = launch_hyper_reduce(d.X, d.rows, h->kp, d.shift64, d.partials, d.red_blocks, st);
-    if (e == cudaSuccess) e = launch_hyper_combine(d.partials, d.red_blocks, h->kp, d.sums, st);
-    if (e != cudaSuccess) return BPMF_ECUDA;
     NWArgs a;
+    memset(&a, 0, sizeof(a));
     a.sums = d.sums;
     a.shift64 = d.shift64;
     a.n = d.rows;
@@ -376,7 +372,16 @@ int phase_hyper(bpmf_ctx* h, int s, cudaStream_t st, uint32_t sweep_offset)
     a.lam32 = d.lam32;
     a.lammu32 = d.lammu32;
     a.draws = d.nw_draws;
-    h->launches += 5;
+    // shift + partials + random draws in one launch; a few partials are combined by the
+    // draw kernel itself, more by their own launch
+    const bool fuse = d.red_blocks <= kFuseCombineBlocks;
+    a.partials = d.partials;
+    a.nparts = fuse ? d.red_blocks : 0;
+    cudaError_t e = launch_hyper_stats_draws(d.X, d.rows, h->K, h->kp, d.shift64, d.partials,
+                                             d.red_blocks, a, st);
+    if (e == cudaSuccess && !fuse) e = launch_hyper_combine(d.partials, d.red_blocks, h->kp, d.sums, st);
+    if (e != cudaSuccess) return BPMF_ECUDA;
+    h->launches += fuse ? 2 : 3;
     return cuda_rc(launch_nw_sample(a, st));
 }
 

@@ -80,10 +80,6 @@ constexpr int kCheckSumBlocks = 512;
 cudaError_t launch_check_sum(const int32_t* col, const float* val, int64_t n, int32_t ncols,
                              double* scratch, unsigned int* bad, cudaStream_t s);
 
-// Hyper step, part 0: the shift (FP64 mean of the first rows, kp entries, zero
-// beyond K) that parts 1 and 2 subtract.
-cudaError_t launch_hyper_shift(const float* X, int64_t rows, int K, int kp, double* shift64,
-                               cudaStream_t s);
 // Hyper step, part 1: per-block partial sums of (x - shift) and (x - shift)(x - shift)^T.
 int hyper_reduce_blocks(int64_t rows, int num_sms);
 __host__ __device__ inline size_t hyper_partial_doubles(int kp)
@@ -115,11 +111,20 @@ struct NWArgs {
                             // then the chunk-transposed lower Cholesky factor (identity beyond K)
     float* lammu32;         // out: kp
     double* draws;          // K(K-1)/2 + 2K scratch: the step's random draws
+    const double* partials; // nparts > 0: the reduction's block partials, combined here
+    int nparts;             // (fixed order); 0: `sums` holds the combined sums
 };
 // Doubles of NWArgs::draws for K.
 inline size_t nw_draws_doubles(int K) { return (size_t)K * (K - 1) / 2 + 2 * (size_t)K; }
-// The draws kernel (many CTAs) then the one-CTA draw: two launches.
+// The one-CTA draw (its random numbers come from launch_hyper_stats_draws).
 cudaError_t launch_nw_sample(const NWArgs& a, cudaStream_t s);
+// The hyper step's first launch: the shift (FP64 mean of the first rows, computed by every
+// block, published by block 0), the reduction's block partials, and in extra blocks the
+// draw's random numbers.
+cudaError_t launch_hyper_stats_draws(const float* X, int64_t rows, int K, int kp, double* shift64,
+                                     double* partials, int nblocks, const NWArgs& a, cudaStream_t s);
+// Reductions of at most this many blocks are combined inside the draw kernel.
+constexpr int kFuseCombineBlocks = 8;
 // Index of (i, j) in the chunk-transposed copy of a kp x kp matrix (kp a multiple
 // of 4): float4 (i, 4c .. 4c + 3) sits at float4 index c * kp + i.
 __host__ __device__ inline int chunk_t_index(int i, int j, int kp)

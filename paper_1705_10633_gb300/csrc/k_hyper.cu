@@ -2,8 +2,8 @@
 // movies/users based on V/U", Sec. 2): sufficient statistics of a factor matrix
 // and the Normal-Wishart draw of (mu, Lambda).
 //
-//   shift  : s = FP64 mean of the first rows (fixed order).
-//   reduce : every block streams a contiguous slab of rows once (HBM bound),
+//   reduce : every block takes the shift s (FP64 mean of the first rows, fixed
+//            order), then streams a contiguous slab of rows once (HBM bound),
 //            accumulating (x - s) and (x - s)(x - s)^T in FP32 registers over
 //            64-row chunks and folding each chunk into FP64 accumulators, so the
 //            sums stay small.
@@ -11,6 +11,8 @@
 //   nw     : one CTA in FP64 -- posterior parameters, chol(W*) through the
 //            reversed factorisation of its inverse, Bartlett Wishart draw with
 //            Marsaglia-Tsang gammas, chol(Lambda), mean draw.
+#include <string.h>
+
 #include "bpmf_internal.cuh"
 #include "philox.cuh"
 
@@ -21,6 +23,58 @@ namespace bpmf {
 // ---------------------------------------------------------------------------
 constexpr int kRedThreads = 256;
 constexpr int kRedChunk = 64;
+constexpr int64_t kShiftRows = 256;  // rows whose FP64 mean is the statistics' shift
+constexpr int kGammaMaxAttempts = 64;
+
+// One thread's share of the Normal-Wishart step's random draws, which depend only on
+// (seed, sweep, side) and the posterior degrees of freedom (nu0 + rows, fixed per side):
+// draws[q] for q < K(K-1)/2 the Bartlett factor's off-diagonal normals (stream 0), then K
+// normals of the mean draw (stream 1), then the Bartlett diagonal sqrt(chi^2(nu* - k)) =
+// sqrt(2 Gamma((nu* - k) / 2)) by Marsaglia-Tsang.  Thread q takes one Philox call (four
+// normals) or one gamma; they run as extra blocks of the reduction launch, spread over
+// SMs (FP64 is slow on this GPU, and the one-CTA draw kernel only reads them).
+__device__ void nw_draws_thread(const NWArgs& a, int q)
+{
+    const int K = a.K, noff = K * (K - 1) / 2;
+    const int ncall0 = (noff + 3) / 4, ncall1 = (K + 3) / 4;
+    const uint32_t sweep = (uint32_t)a.ctl->sweep + a.sweep_offset;
+    if (q < ncall0 + ncall1) {
+        const bool mean = q >= ncall0;
+        const uint32_t c = mean ? (uint32_t)(q - ncall0) : (uint32_t)q;
+        const uint4 w = philox_call(a.seed, c, mean ? 1u : 0u, sweep, a.c3_normal);
+        const double2 z0 = box_muller_f64(w.x, w.y), z1 = box_muller_f64(w.z, w.w);
+        const double z[4] = {z0.x, z0.y, z1.x, z1.y};
+        const int base = mean ? noff : 0, lim = mean ? K : noff;
+        for (int u = 0; u < 4; ++u)
+            if ((int)(4 * c) + u < lim) a.draws[base + 4 * c + u] = z[u];
+    } else if (q < ncall0 + ncall1 + K) {
+        const int k = q - ncall0 - ncall1;
+        const double nu_s = a.nu0 + (double)a.n;
+        const double shape = 0.5 * (nu_s - (double)k);
+        const double d = shape - 1.0 / 3.0;
+        const double c = 1.0 / sqrt(9.0 * d);
+        double g = -1.0;
+        for (int att = 0; att < kGammaMaxAttempts; ++att) {
+            const uint4 wd = philox_call(a.seed, (uint32_t)att, (uint32_t)k, sweep, a.c3_gamma);
+            const double x = box_muller_f64(wd.x, wd.y).x;
+            const double sx = 1.0 + c * x;
+            if (sx <= 0.0) continue;
+            const double v = sx * sx * sx;
+            const double u = (double)((wd.z >> 8) + 1u) * 0x1p-24;
+            if (log(u) < 0.5 * x * x + d - d * v + d * log(v)) {
+                g = d * v;
+                break;
+            }
+        }
+        if (g < 0.0) {
+            atomicOr(&a.ctl->status, kStatusGamma);
+            g = shape;
+        }
+        a.draws[noff + K + k] = sqrt(2.0 * g);
+    }
+}
+
+int nw_draws_threads(int K) { return (K * (K - 1) / 2 + 3) / 4 + (K + 3) / 4 + K; }
 
 int hyper_reduce_blocks(int64_t rows, int num_sms)
 {
@@ -33,18 +87,48 @@ int hyper_reduce_blocks(int64_t rows, int num_sms)
 
 template <int KT>
 __global__ void __launch_bounds__(kRedThreads) hyper_reduce_kernel(const float* __restrict__ X,
-                                                                   int64_t rows,
-                                                                   const double* __restrict__ shift64,
-                                                                   double* __restrict__ partials)
+                                                                   int64_t rows, int shiftK,
+                                                                   double* __restrict__ shift64,
+                                                                   double* __restrict__ partials,
+                                                                   int nred, NWArgs draws)
 {
+    // blocks past the reduction's draw the Normal-Wishart step's random numbers
+    if ((int)blockIdx.x >= nred) {
+        nw_draws_thread(draws, ((int)blockIdx.x - nred) * kRedThreads + (int)threadIdx.x);
+        return;
+    }
     constexpr int TT = KT / 16;  // each thread owns a TT x TT tile of the scatter
     __shared__ __align__(16) float xs[kRedChunk][KT];
     __shared__ float sh[KT];
     const int t = threadIdx.x;
     const int ty = t / 16, tx = t % 16;
-    if (t < KT) sh[t] = (float)shift64[t];
-    const int64_t r0 = rows * blockIdx.x / gridDim.x;
-    const int64_t r1 = rows * (blockIdx.x + 1) / gridDim.x;
+    if (shiftK > 0) {
+        // the shift: FP64 mean of the first kShiftRows rows, zero beyond shiftK columns,
+        // taken by every block in the same fixed order (column c = t mod 64 of rows
+        // t / 64 (mod 4), four partial sums); block 0 publishes it for the draw.
+        // Subtracting a value near the mean keeps the FP32 chunk sums of (x - s)(x - s)^T
+        // from cancelling against d d^T; taken from the data (not the last drawn mu, which
+        // on a side with few rows can sit far from the sample mean) and in a fixed order,
+        // it keeps resumed chains bit-identical.
+        __shared__ double part[4][64];
+        const int c = t & 63, g = t >> 6;
+        const int64_t n = rows < kShiftRows ? rows : kShiftRows;
+        double s = 0.0;
+        if (c < shiftK)
+            for (int64_t r = g; r < n; r += 4) s += (double)X[r * KT + c];
+        part[g][c] = s;
+        __syncthreads();
+        if (t < KT) {
+            const double tot = (part[0][t] + part[1][t]) + (part[2][t] + part[3][t]);
+            const double v = (t < shiftK && n > 0) ? tot / (double)n : 0.0;
+            sh[t] = (float)v;
+            if (blockIdx.x == 0) shift64[t] = v;
+        }
+    } else if (t < KT) {
+        sh[t] = (float)shift64[t];
+    }
+    const int64_t r0 = rows * blockIdx.x / nred;
+    const int64_t r1 = rows * (blockIdx.x + 1) / nred;
     double acc64[TT][TT];
     double s64 = 0.0;
 #pragma unroll
@@ -104,51 +188,34 @@ __global__ void __launch_bounds__(kRedThreads) hyper_reduce_kernel(const float* 
         for (int j = 0; j < TT; ++j) out[KT + (ty * TT + i) * KT + tx * TT + j] = acc64[i][j];
 }
 
-// Shift for the statistics: the FP64 mean of the first rows (at most kShiftRows),
-// zero beyond K.  Subtracting a value near the mean keeps the FP32 chunk sums of
-// (x - s)(x - s)^T from cancelling against d d^T; a shift taken from the data itself
-// (rather than from the last drawn mu, which can sit far from the sample mean when a
-// side has few rows) and computed in a fixed order keeps resumed chains bit-identical.
-constexpr int64_t kShiftRows = 256;
-
-// 256 threads: column c = t mod 64 of rows r = t / 64 (mod 4), four partial sums added
-// in a fixed order (a quarter of the dependent chain of one thread per column).
-__global__ void __launch_bounds__(256) hyper_shift_kernel(const float* __restrict__ X,
-                                                          int64_t rows, int K, int kp,
-                                                          double* __restrict__ shift64)
+static cudaError_t reduce_launch(const float* X, int64_t rows, int kp, int shiftK, double* shift64,
+                                 double* partials, int nblocks, int ndraw, const NWArgs& draws,
+                                 cudaStream_t s)
 {
-    __shared__ double part[4][64];
-    const int t = threadIdx.x, c = t & 63, g = t >> 6;
-    const int64_t n = rows < kShiftRows ? rows : kShiftRows;
-    double s = 0.0;
-    if (c < K)
-        for (int64_t r = g; r < n; r += 4) s += (double)X[r * kp + c];
-    part[g][c] = s;
-    __syncthreads();
-    if (t < kp) {
-        const double tot = (part[0][t] + part[1][t]) + (part[2][t] + part[3][t]);
-        shift64[t] = (t < K && n > 0) ? tot / (double)n : 0.0;
+    const int grid = nblocks + ndraw;
+    switch (kp) {
+    case 16: hyper_reduce_kernel<16><<<grid, kRedThreads, 0, s>>>(X, rows, shiftK, shift64, partials, nblocks, draws); break;
+    case 32: hyper_reduce_kernel<32><<<grid, kRedThreads, 0, s>>>(X, rows, shiftK, shift64, partials, nblocks, draws); break;
+    case 48: hyper_reduce_kernel<48><<<grid, kRedThreads, 0, s>>>(X, rows, shiftK, shift64, partials, nblocks, draws); break;
+    case 64: hyper_reduce_kernel<64><<<grid, kRedThreads, 0, s>>>(X, rows, shiftK, shift64, partials, nblocks, draws); break;
+    default: return cudaErrorInvalidValue;
     }
-}
-
-cudaError_t launch_hyper_shift(const float* X, int64_t rows, int K, int kp, double* shift64,
-                               cudaStream_t s)
-{
-    hyper_shift_kernel<<<1, 256, 0, s>>>(X, rows, K, kp, shift64);
     return cudaGetLastError();
 }
 
 cudaError_t launch_hyper_reduce(const float* X, int64_t rows, int kp, const double* shift64,
                                 double* partials, int nblocks, cudaStream_t s)
 {
-    switch (kp) {
-    case 16: hyper_reduce_kernel<16><<<nblocks, kRedThreads, 0, s>>>(X, rows, shift64, partials); break;
-    case 32: hyper_reduce_kernel<32><<<nblocks, kRedThreads, 0, s>>>(X, rows, shift64, partials); break;
-    case 48: hyper_reduce_kernel<48><<<nblocks, kRedThreads, 0, s>>>(X, rows, shift64, partials); break;
-    case 64: hyper_reduce_kernel<64><<<nblocks, kRedThreads, 0, s>>>(X, rows, shift64, partials); break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    NWArgs none;
+    memset(&none, 0, sizeof(none));
+    return reduce_launch(X, rows, kp, 0, const_cast<double*>(shift64), partials, nblocks, 0, none, s);
+}
+
+cudaError_t launch_hyper_stats_draws(const float* X, int64_t rows, int K, int kp, double* shift64,
+                                     double* partials, int nblocks, const NWArgs& a, cudaStream_t s)
+{
+    const int ndraw = (nw_draws_threads(K) + kRedThreads - 1) / kRedThreads;
+    return reduce_launch(X, rows, kp, K, shift64, partials, nblocks, ndraw, a, s);
 }
 
 __global__ void hyper_combine_kernel(const double* __restrict__ partials, int nblocks, int E,
@@ -181,8 +248,6 @@ cudaError_t launch_hyper_combine(const double* partials, int nblocks, int kp, do
 // Normal-Wishart draw, one CTA, FP64.  Matrices are K x K row-major in smem.
 // ---------------------------------------------------------------------------
 constexpr int kNWThreads = 256;
-constexpr int kGammaMaxAttempts = 64;
-
 // 1 / sqrt(p) for p > 0 in FP64: an FP32 estimate refined by two steps of Newton's
 // iteration for the reciprocal square root, y <- y (3 - p y^2) / 2, whose relative error
 // squares each step (2^-23 -> 2^-45 -> FP64 rounding).  A handful of FP64 operations
@@ -251,53 +316,22 @@ __device__ __forceinline__ double dot4(const double* x, int sx, const double* y,
     return (s0 + s1) + (s2 + s3);
 }
 
-// The Normal-Wishart step's random numbers, which depend only on (seed, sweep, side)
-// and the posterior degrees of freedom (nu0 + rows, fixed per side): draws[q] for
-// q < K(K-1)/2 the Bartlett factor's off-diagonal normals (stream 0), then K normals of
-// the mean draw (stream 1), then the Bartlett diagonal sqrt(chi^2(nu* - k)) =
-// sqrt(2 Gamma((nu* - k) / 2)) by Marsaglia-Tsang.  One thread per Philox call (four
-// normals) or per gamma, over as many CTAs as that takes: FP64 is slow on this GPU, and
-// spreading these draws over SMs takes them off the one-CTA kernel that uses them.
-__global__ void nw_draws_kernel(NWArgs a, double* __restrict__ draws)
+// Entry e of the reduction's sums: from `sums`, or (nparts > 0) the fixed-order sum of the
+// block partials, in the combine kernel's order (four interleaved accumulators).
+__device__ double nw_sum(const NWArgs& a, int e)
 {
-    const int K = a.K, noff = K * (K - 1) / 2;
-    const int ncall0 = (noff + 3) / 4, ncall1 = (K + 3) / 4;
-    const uint32_t sweep = (uint32_t)a.ctl->sweep + a.sweep_offset;
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < ncall0 + ncall1) {
-        const bool mean = q >= ncall0;
-        const uint32_t c = mean ? (uint32_t)(q - ncall0) : (uint32_t)q;
-        const uint4 w = philox_call(a.seed, c, mean ? 1u : 0u, sweep, a.c3_normal);
-        const double2 z0 = box_muller_f64(w.x, w.y), z1 = box_muller_f64(w.z, w.w);
-        const double z[4] = {z0.x, z0.y, z1.x, z1.y};
-        const int base = mean ? noff : 0, lim = mean ? K : noff;
-        for (int u = 0; u < 4; ++u)
-            if ((int)(4 * c) + u < lim) draws[base + 4 * c + u] = z[u];
-    } else if (q < ncall0 + ncall1 + K) {
-        const int k = q - ncall0 - ncall1;
-        const double nu_s = a.nu0 + (double)a.n;
-        const double shape = 0.5 * (nu_s - (double)k);
-        const double d = shape - 1.0 / 3.0;
-        const double c = 1.0 / sqrt(9.0 * d);
-        double g = -1.0;
-        for (int att = 0; att < kGammaMaxAttempts; ++att) {
-            const uint4 wd = philox_call(a.seed, (uint32_t)att, (uint32_t)k, sweep, a.c3_gamma);
-            const double x = box_muller_f64(wd.x, wd.y).x;
-            const double sx = 1.0 + c * x;
-            if (sx <= 0.0) continue;
-            const double v = sx * sx * sx;
-            const double u = (double)((wd.z >> 8) + 1u) * 0x1p-24;
-            if (log(u) < 0.5 * x * x + d - d * v + d * log(v)) {
-                g = d * v;
-                break;
-            }
-        }
-        if (g < 0.0) {
-            atomicOr(&a.ctl->status, kStatusGamma);
-            g = shape;
-        }
-        draws[noff + K + k] = sqrt(2.0 * g);
+    if (a.nparts == 0) return a.sums[e];
+    const int E = (int)hyper_partial_doubles(a.kp);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int b = 0;
+    for (; b + 3 < a.nparts; b += 4) {
+        a0 += a.partials[(size_t)b * E + e];
+        a1 += a.partials[(size_t)(b + 1) * E + e];
+        a2 += a.partials[(size_t)(b + 2) * E + e];
+        a3 += a.partials[(size_t)(b + 3) * E + e];
     }
+    for (; b < a.nparts; ++b) a0 += a.partials[(size_t)b * E + e];
+    return (a0 + a1) + (a2 + a3);
 }
 
 __global__ void __launch_bounds__(kNWThreads) nw_sample_kernel(NWArgs a)
@@ -318,14 +352,14 @@ __global__ void __launch_bounds__(kNWThreads) nw_sample_kernel(NWArgs a)
     // ---- statistics: mean = s + S1/n, S = S2/n - d d^T with d = S1/n ----
     for (int k = t; k < K; k += blockDim.x) {
         const double s = (double)(float)a.shift64[k];
-        const double d = a.sums[k] / n;
+        const double d = nw_sum(a, k) / n;
         dvec[k] = d;
         mean[k] = s + d;
     }
     __syncthreads();
     for (int e = t; e < KK; e += blockDim.x) {
         const int i = e / K, j = e % K;
-        const double S = a.sums[a.kp + i * a.kp + j] / n - dvec[i] * dvec[j];
+        const double S = nw_sum(a, a.kp + i * a.kp + j) / n - dvec[i] * dvec[j];
         M1[e] = S;
         a.stats[K + e] = S;
     }
@@ -462,11 +496,6 @@ cudaError_t launch_nw_sample(const NWArgs& a, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int noff = a.K * (a.K - 1) / 2;
-    const int nthreads = (noff + 3) / 4 + (a.K + 3) / 4 + a.K;
-    nw_draws_kernel<<<(nthreads + 31) / 32, 32, 0, s>>>(a, a.draws);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     nw_sample_kernel<<<1, kNWThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
