@@ -12,17 +12,18 @@
 // 128B-swizzled atoms of a stage (h rows, l rows, and the ratings in the first
 // two columns of an otherwise zero atom), so each k-block reads them once.
 //
-// CTA = 16 warps, one CTA per SM, persistent over the rows of the long bin:
+// One CTA per SM, persistent over the rows of the long bin (12 or 16 warps, by shape):
 //   warp 0       MMA issuer (one lane) and TMEM owner (512 columns)
 //   warp 1       prefetch: row descriptors (row, first, last rating) into a
 //                ring, and every stage's rating indices and values into a
 //                second ring, far ahead of use (cp.async, mbarrier completion)
-//   warps 2-3    gather: cp.async of the 128-B h and l rows of each rating into
-//                128B-swizzled tiles (MN-major operand layout); they never wait
-//                for their copies, the stage barrier completes when they land
+//   warps 2-3    gather (with warps 8-9 in the long-row shape): cp.async of the
+//                128-B h and l rows of each rating into 128B-swizzled tiles
+//                (MN-major operand layout); they never wait for their copies,
+//                the stage barrier completes when they land
 //   warps 4-7    drain: TMEM -> shared Lambda_i += alpha Gram (the buffer starts
 //                from Lambda_X), b_i
-//   warps 8-15   one row each: Cholesky, solves, Philox noise, store
+//   the rest     one row each: Cholesky, solves, Philox noise, store
 // Stages of 64 ratings flow producer -> MMA through mbarriers; accumulators
 // (3 TMEM slots of 144 columns) MMA -> drain; Lambda buffers (one per Cholesky warp) drain ->
 // Cholesky.  A long row is accumulated in chunks of 16 stages, each in a fresh
