@@ -369,7 +369,8 @@ def run_native(args):
                                        "sustained bf16; FP16 runs at the bf16 rate)"}}
                    if tc_path else {}),
                 "phase_note": "phases timed one by one (hyper steps not overlapped, all SMs to "
-                              "the row kernel); %.2f ms per sweep that way" % phase_sweep_ms}
+                              "the row kernel, row phases also recording their launch events); "
+                              "%.2f ms per sweep that way" % phase_sweep_ms}
     if tc_path and n_long > 0 and n_short > 0:
         cc_flops = row_alu_flops(n_short, K) + row_gram_flops(short_ratings, K)
         roofline["cuda_core_launch"] = {
