@@ -3,15 +3,17 @@
 // and the Normal-Wishart draw of (mu, Lambda).
 //
 //   reduce : every block takes the shift s (FP64 mean of the first rows, fixed
-//            order), then streams a contiguous slab of rows once (HBM bound),
-//            accumulating (x - s) and (x - s)(x - s)^T in FP32 registers over
-//            64-row chunks and folding each chunk into FP64 accumulators, so the
-//            sums stay small.
+//            order), then streams a contiguous slab of rows once, the next 64-row
+//            chunk in flight while the current one is summed, accumulating (x - s)
+//            and the lower triangle of (x - s)(x - s)^T in FP32 registers over each
+//            chunk and folding it into FP64 accumulators, so the sums stay small.
 //   combine: fixed-order FP64 sum of the block partials (deterministic).
 //   nw     : one CTA in FP64 -- posterior parameters, chol(W*) through the
 //            reversed factorisation of its inverse, Bartlett Wishart draw with
 //            Marsaglia-Tsang gammas, chol(Lambda), mean draw.
 #include <string.h>
+
+#include <algorithm>
 
 #include "bpmf_internal.cuh"
 #include "philox.cuh"
@@ -79,6 +81,9 @@ int nw_draws_threads(int K) { return (K * (K - 1) / 2 + 3) / 4 + (K + 3) / 4 + K
 int hyper_reduce_blocks(int64_t rows, int num_sms)
 {
     int64_t want = (rows + 1023) / 1024;  // at least ~1k rows per block
+    // a small side: up to the blocks the draw kernel combines itself, of at least 128
+    // rows each, so that no block walks through more than a few chunks in sequence
+    if (want < kFuseCombineBlocks) want = std::min<int64_t>(kFuseCombineBlocks, (rows + 127) / 128);
     int64_t cap = (int64_t)num_sms * 2;
     if (want > cap) want = cap;
     if (want < 1) want = 1;
@@ -97,11 +102,21 @@ __global__ void __launch_bounds__(kRedThreads) hyper_reduce_kernel(const float* 
         nw_draws_thread(draws, ((int)blockIdx.x - nred) * kRedThreads + (int)threadIdx.x);
         return;
     }
-    constexpr int TT = KT / 16;  // each thread owns a TT x TT tile of the scatter
+    // The scatter is a 16 x 16 grid of TT x TT tiles; threads 0..135 own the tiles on
+    // and below the diagonal (t = ty (ty + 1) / 2 + tx, tx <= ty) and also write their
+    // mirror images; the other threads only stage rows.
+    constexpr int TT = KT / 16;
+    constexpr int kLowerTiles = 16 * 17 / 2;
+    constexpr int F4 = KT / 4;
+    constexpr int NPF = kRedChunk * F4 / kRedThreads;  // float4 a thread stages per chunk
+    static_assert(NPF * kRedThreads == kRedChunk * F4, "chunk staging");
     __shared__ __align__(16) float xs[kRedChunk][KT];
     __shared__ float sh[KT];
     const int t = threadIdx.x;
-    const int ty = t / 16, tx = t % 16;
+    const bool tile_on = t < kLowerTiles;
+    int ty = 0;
+    while (tile_on && (ty + 1) * (ty + 2) / 2 <= t) ++ty;
+    const int tx = tile_on ? t - ty * (ty + 1) / 2 : 0;
     if (shiftK > 0) {
         // the shift: FP64 mean of the first kShiftRows rows, zero beyond shiftK columns,
         // taken by every block in the same fixed order (column c = t mod 64 of rows
@@ -129,6 +144,18 @@ __global__ void __launch_bounds__(kRedThreads) hyper_reduce_kernel(const float* 
     }
     const int64_t r0 = rows * blockIdx.x / nred;
     const int64_t r1 = rows * (blockIdx.x + 1) / nred;
+    // a chunk's rows in registers (rows past the slab's end zero)
+    float4 pf[NPF];
+    auto load_chunk = [&](int64_t base) {
+        const int cnt = (int)min((int64_t)kRedChunk, r1 - base);
+#pragma unroll
+        for (int i = 0; i < NPF; ++i) {
+            const int e = t + i * kRedThreads, r = e / F4, f = e % F4;
+            pf[i] = r < cnt ? __ldg(reinterpret_cast<const float4*>(X + (base + r) * KT) + f)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    if (r0 < r1) load_chunk(r0);
     double acc64[TT][TT];
     double s64 = 0.0;
 #pragma unroll
@@ -138,13 +165,12 @@ __global__ void __launch_bounds__(kRedThreads) hyper_reduce_kernel(const float* 
     __syncthreads();
     for (int64_t base = r0; base < r1; base += kRedChunk) {
         const int cnt = (int)min((int64_t)kRedChunk, r1 - base);
-        // stage (x - s) for the chunk; rows past the end are zero
-        constexpr int F4 = KT / 4;
-        for (int e = t; e < kRedChunk * F4; e += kRedThreads) {
-            const int r = e / F4, f = e % F4;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        // stage (x - s) for the chunk; rows past the end stay zero
+#pragma unroll
+        for (int i = 0; i < NPF; ++i) {
+            const int e = t + i * kRedThreads, r = e / F4, f = e % F4;
+            float4 v = pf[i];
             if (r < cnt) {
-                v = __ldg(reinterpret_cast<const float4*>(X + (base + r) * KT) + f);
                 v.x -= sh[4 * f + 0];
                 v.y -= sh[4 * f + 1];
                 v.z -= sh[4 * f + 2];
@@ -153,39 +179,52 @@ __global__ void __launch_bounds__(kRedThreads) hyper_reduce_kernel(const float* 
             *reinterpret_cast<float4*>(&xs[r][4 * f]) = v;
         }
         __syncthreads();
-        float acc[TT][TT];
+        // the next chunk's loads are in flight while this one is summed
+        if (base + kRedChunk < r1) load_chunk(base + kRedChunk);
         float s32 = 0.f;
+        if (t < KT)
+#pragma unroll 8
+            for (int r = 0; r < kRedChunk; ++r) s32 += xs[r][t];
+        s64 += (double)s32;
+        if (tile_on) {
+            float acc[TT][TT];
 #pragma unroll
-        for (int i = 0; i < TT; ++i)
+            for (int i = 0; i < TT; ++i)
 #pragma unroll
-            for (int j = 0; j < TT; ++j) acc[i][j] = 0.f;
+                for (int j = 0; j < TT; ++j) acc[i][j] = 0.f;
 #pragma unroll 4
-        for (int r = 0; r < kRedChunk; ++r) {
-            float a[TT], b[TT];
+            for (int r = 0; r < kRedChunk; ++r) {
+                float a[TT], b[TT];
 #pragma unroll
-            for (int i = 0; i < TT; ++i) {
-                a[i] = xs[r][ty * TT + i];
-                b[i] = xs[r][tx * TT + i];
+                for (int i = 0; i < TT; ++i) {
+                    a[i] = xs[r][ty * TT + i];
+                    b[i] = xs[r][tx * TT + i];
+                }
+#pragma unroll
+                for (int i = 0; i < TT; ++i)
+#pragma unroll
+                    for (int j = 0; j < TT; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
             }
 #pragma unroll
             for (int i = 0; i < TT; ++i)
 #pragma unroll
-                for (int j = 0; j < TT; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-            if (t < KT) s32 += xs[r][t];
+                for (int j = 0; j < TT; ++j) acc64[i][j] += (double)acc[i][j];
         }
-#pragma unroll
-        for (int i = 0; i < TT; ++i)
-#pragma unroll
-            for (int j = 0; j < TT; ++j) acc64[i][j] += (double)acc[i][j];
-        s64 += (double)s32;
         __syncthreads();
     }
     double* out = partials + (size_t)blockIdx.x * hyper_partial_doubles(KT);
     if (t < KT) out[t] = s64;
+    if (tile_on) {
+        // entry (p, q) and its mirror (q, p): fmaf(x_p, x_q, .) equals fmaf(x_q, x_p, .),
+        // so the mirror is the value the upper tile's own sum would give
 #pragma unroll
-    for (int i = 0; i < TT; ++i)
+        for (int i = 0; i < TT; ++i)
 #pragma unroll
-        for (int j = 0; j < TT; ++j) out[KT + (ty * TT + i) * KT + tx * TT + j] = acc64[i][j];
+            for (int j = 0; j < TT; ++j) {
+                out[KT + (ty * TT + i) * KT + tx * TT + j] = acc64[i][j];
+                out[KT + (tx * TT + j) * KT + ty * TT + i] = acc64[i][j];
+            }
+    }
 }
 
 static cudaError_t reduce_launch(const float* X, int64_t rows, int kp, int shiftK, double* shift64,
