@@ -160,8 +160,8 @@ def row_gather_bytes(nnz, rows, K, split=True):
 # DRAM bytes (read + write) per launch of the dominant row kernel, per workload and
 # phase, from one ncu capture of this kernel version (null once the kernel changes):
 # the tensor-core user launch of the 480k x 18k K = 64 workload (its 352,197 rows of 48
-# ratings or more), scaled x 4.99 from its 96k-row slice.
-TRAFFIC = {"config3_480kx18k_K64": {"rows_user": 895e6}}
+# ratings or more), captured at full size (861.4 MB read + 144.7 MB written).
+TRAFFIC = {"config3_480kx18k_K64": {"rows_user": 1006e6}}
 
 
 def l2_note(nnz):
