@@ -404,7 +404,8 @@ def run_native(args):
                       "bins": {"users": [info_u["n_short"], info_u["n_long"]],
                                "movies": [info_v["n_short"], info_v["n_long"]],
                                "split_rows_segments": [[info_u["n_split"], info_u["n_segments"]],
-                                                       [info_v["n_split"], info_v["n_segments"]]]},
+                                                       [info_v["n_split"], info_v["n_segments"]]],
+                               "balanced_plan": [info_u["balanced"], info_v["balanced"]]},
                       "tuning": tuning, "parallelism": "replicas x%d" % world, "rmse_sample": finite_or_none(rs), "rmse_avg": finite_or_none(ra)},
            "roofline": roofline, "clocks": clk, "gpu_launches": int(launches), "e2e": e2e}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

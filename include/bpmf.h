@@ -207,9 +207,14 @@ int bpmf_status(bpmf_handle h);
 
 /* Diagnostics: number of rows of `side` on the CUDA-core kernel and on the
  * tensor-core kernel, how many of the former are split and into how many
- * segments, the centring mean, and device bytes held.  NULL outputs are skipped. */
+ * segments, the centring mean, device bytes held, and `balanced`: bit 0 (bit 1)
+ * set when the tensor-core rows are dealt to the CTAs of a launch on every SM
+ * (on all SMs but one, as bpmf_sweep launches) by the balanced plan -- each row,
+ * longest first, to the CTA with the least work so far, made where the plain
+ * round-robin order would leave one CTA over 5% above the mean -- instead of
+ * round-robin.  NULL outputs are skipped. */
 int bpmf_info(bpmf_handle h, int32_t side, int64_t* n_short, int64_t* n_long, int64_t* n_split,
-              int64_t* n_segments, double* rbar, int64_t* device_bytes);
+              int64_t* n_segments, double* rbar, int64_t* device_bytes, int32_t* balanced);
 
 /* Number of kernels this handle has launched so far (all phases, all sweeps). */
 int bpmf_launch_count(bpmf_handle h, int64_t* launches);

@@ -83,7 +83,8 @@ def lib():
     L.bpmf_get_stats.argtypes = [vp, i32, P(i64), vp, vp]
     L.bpmf_debug_means.argtypes = [vp, i32, vp]
     L.bpmf_status.argtypes = [vp]
-    L.bpmf_info.argtypes = [vp, i32, P(i64), P(i64), P(i64), P(i64), P(C.c_double), P(i64)]
+    L.bpmf_info.argtypes = [vp, i32, P(i64), P(i64), P(i64), P(i64), P(C.c_double), P(i64),
+                            P(i32)]
     L.bpmf_launch_count.argtypes = [vp, P(i64)]
     L.bpmf_set_row_timing.argtypes = [vp, i32]
     L.bpmf_row_launch_ms.argtypes = [vp, P(C.c_float), P(C.c_float)]
@@ -272,10 +273,12 @@ def bpmf_status(h):
 def bpmf_info(h, side):
     ns, nl, nsp, nsg, nb = (C.c_int64() for _ in range(5))
     rb = C.c_double()
+    bal = C.c_int32()
     _check(lib().bpmf_info(h, int(side), C.byref(ns), C.byref(nl), C.byref(nsp), C.byref(nsg),
-                           C.byref(rb), C.byref(nb)), "bpmf_info")
+                           C.byref(rb), C.byref(nb), C.byref(bal)), "bpmf_info")
     return {"n_short": ns.value, "n_long": nl.value, "n_split": nsp.value,
-            "n_segments": nsg.value, "rbar": rb.value, "device_bytes": nb.value}
+            "n_segments": nsg.value, "rbar": rb.value, "device_bytes": nb.value,
+            "balanced": bal.value}
 
 
 def bpmf_set_row_timing(h, on=True):

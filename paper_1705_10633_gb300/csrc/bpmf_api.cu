@@ -5,8 +5,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <new>
 #include <numeric>
+#include <queue>
+#include <utility>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -46,6 +49,13 @@ struct DevSide {
     int64_t n_rank_one = 0;  // last rows of the short bin, on the rank-one route
     float* part = nullptr;           // seg_cap partials
     unsigned int* seg_done = nullptr;  // split_cap counters, zero between launches
+    // balanced plans of the long bin for the two grids a tensor-core launch can have
+    // (every SM, or one left to the hyper steps): rows grouped by CTA, per-CTA offsets;
+    // plan_grid 0 when round-robin is kept
+    int32_t* plan_rows[2] = {nullptr, nullptr};
+    int64_t* plan_first[2] = {nullptr, nullptr};
+    int64_t plan_grid[2] = {0, 0};
+    int64_t plan_cap[2] = {0, 0};
     double* mu64 = nullptr;
     double* shift64 = nullptr;  // kp: shift of the hyper statistics
     double* lam64 = nullptr;
@@ -320,8 +330,74 @@ int plan_segments(bpmf_ctx* h, DevSide& d, const std::vector<int32_t>& order)
     return BPMF_OK;
 }
 
-// Bins of one side (every row in the short bin when the tensor-core kernel is off)
-// and the split of its long CUDA-core rows.
+// Balanced assignment of the tensor-core bin's rows to the CTAs of a launch (the
+// paper's workload model, Sec. 4.2: an item costs a fixed part plus a part per rating).
+// A row's work is its 64-rating stages plus two; rows go, longest first, each to the CTA
+// with the least work so far (longest-processing-time list scheduling).  Made for the two
+// grids a launch can have, and only where the plain order (row j to CTA j mod G) would
+// leave the busiest CTA more than kPlanImbalance above the mean: a few capped columns of
+// 2.7e5 ratings among ten thousand shorter ones put 26% more on some CTAs of the
+// 480k x 18k workload's movie launch, while its users are within 2%.
+constexpr double kPlanImbalance = 1.05;
+
+int plan_long_bin(bpmf_ctx* h, DevSide& d, const std::vector<int32_t>& order)
+{
+    d.plan_grid[0] = d.plan_grid[1] = 0;
+    const int64_t n = d.n_long;
+    if (!h->tc || n == 0) return BPMF_OK;
+    std::vector<int64_t> cost((size_t)n);
+    int64_t total = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        const int32_t row = order[(size_t)(d.n_short + k)];
+        const int64_t deg = d.ptr_h[(size_t)row + 1] - d.ptr_h[(size_t)row];
+        cost[(size_t)k] = (deg + 63) / 64 + 2;
+        total += cost[(size_t)k];
+    }
+    std::vector<int32_t> plan((size_t)n), owner((size_t)n);
+    std::vector<int64_t> first, rr, fill;
+    for (int q = 0; q < 2; ++q) {
+        const int64_t G = std::min<int64_t>(n, h->num_sms - q);
+        if (G < 1 || n <= G) continue;  // one row per CTA at most: nothing to balance
+        rr.assign((size_t)G, 0);
+        for (int64_t k = 0; k < n; ++k) rr[(size_t)(k % G)] += cost[(size_t)k];
+        const int64_t rr_max = *std::max_element(rr.begin(), rr.end());
+        if ((double)rr_max * (double)G <= kPlanImbalance * (double)total) continue;
+        using Load = std::pair<int64_t, int64_t>;  // (work so far, CTA): ties by CTA index
+        std::priority_queue<Load, std::vector<Load>, std::greater<Load>> least;
+        for (int64_t c = 0; c < G; ++c) least.push({0, c});
+        for (int64_t k = 0; k < n; ++k) {
+            Load l = least.top();
+            least.pop();
+            owner[(size_t)k] = (int32_t)l.second;
+            l.first += cost[(size_t)k];
+            least.push(l);
+        }
+        first.assign((size_t)G + 1, 0);
+        for (int64_t k = 0; k < n; ++k) ++first[(size_t)owner[(size_t)k] + 1];
+        for (int64_t c = 0; c < G; ++c) first[(size_t)c + 1] += first[(size_t)c];
+        fill.assign(first.begin(), first.end() - 1);
+        for (int64_t k = 0; k < n; ++k)
+            plan[(size_t)fill[(size_t)owner[(size_t)k]]++] = order[(size_t)(d.n_short + k)];
+        if (n > d.plan_cap[q]) {
+            if (!alloc_n(h, &d.plan_rows[q], (size_t)n)) return BPMF_ENOMEM;
+            d.plan_cap[q] = n;
+        }
+        if (!d.plan_first[q] && !alloc_n(h, &d.plan_first[q], (size_t)h->num_sms + 1))
+            return BPMF_ENOMEM;
+        cudaError_t e = cudaMemcpyAsync(d.plan_rows[q], plan.data(), sizeof(int32_t) * n,
+                                        cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d.plan_first[q], first.data(), sizeof(int64_t) * (G + 1),
+                                cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // host vectors are reused
+        if (e != cudaSuccess) return BPMF_ECUDA;
+        d.plan_grid[q] = G;
+    }
+    return BPMF_OK;
+}
+
+// Bins of one side (every row in the short bin when the tensor-core kernel is off),
+// the split of its long CUDA-core rows and the balanced plan of its tensor-core rows.
 int bin_side(bpmf_ctx* h, DevSide& d, std::vector<int32_t>& order)
 {
     bin_rows(d.rows, d.ptr_h.data(), h->tc ? h->long_min : INT64_MAX, order, &d.n_short, &d.n_long,
@@ -329,7 +405,9 @@ int bin_side(bpmf_ctx* h, DevSide& d, std::vector<int32_t>& order)
     cudaError_t e = cudaMemcpyAsync(d.bin_rows, order.data(), sizeof(int32_t) * d.rows,
                                     cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return BPMF_ECUDA;
-    return plan_segments(h, d, order);  // waits for the stream: `order` may be reused
+    const int rc = plan_segments(h, d, order);  // waits for the stream: `order` may be reused
+    if (rc != BPMF_OK) return rc;
+    return plan_long_bin(h, d, order);
 }
 
 int sync_status(bpmf_ctx* h)
@@ -442,6 +520,13 @@ int phase_rows(bpmf_ctx* h, int s, bool timed = false)
     a.nsegs = a.nsplit = a.nrank_one = 0;
     a.rows = d.bin_rows + d.n_short;
     a.nrows = d.n_long;
+    const int64_t grid = std::min<int64_t>(d.n_long, h->row_sms);  // the launch's CTAs
+    for (int q = 0; q < 2; ++q)
+        if (d.plan_grid[q] > 0 && d.plan_grid[q] == grid) {
+            a.rows = d.plan_rows[q];
+            a.cta_first = d.plan_first[q];
+            a.plan_grid = grid;
+        }
     if (e == cudaSuccess && a.nrows > 0) {
         h->launches += 1;
         e = launch_rows_tc(a, d.long_ratings, h->long_shape_degree, h->row_sms, h->stream);
@@ -1181,9 +1266,10 @@ int bpmf_launch_count(bpmf_handle h, int64_t* launches)
 }
 
 int bpmf_info(bpmf_handle h, int32_t side, int64_t* n_short, int64_t* n_long, int64_t* n_split,
-              int64_t* n_segments, double* rbar, int64_t* device_bytes)
+              int64_t* n_segments, double* rbar, int64_t* device_bytes, int32_t* balanced)
 {
     if (!h || (side != 0 && side != 1)) return BPMF_EINVAL;
+    if (balanced) *balanced = (h->side[side].plan_grid[0] > 0 ? 1 : 0) | (h->side[side].plan_grid[1] > 0 ? 2 : 0);
     if (n_short) *n_short = h->side[side].n_short;
     if (n_long) *n_long = h->side[side].n_long;
     if (n_split) *n_split = h->side[side].n_split;

@@ -44,6 +44,12 @@ struct RowArgs {
     const __half* Yl;
     const int32_t* rows;   // rows of this bin, longest first
     int64_t nrows;
+    // tensor-core kernel: a balanced assignment of the rows to the CTAs of a launch of
+    // exactly plan_grid CTAs -- CTA b takes rows[cta_first[b]] .. rows[cta_first[b + 1] - 1]
+    // (its rows longest first).  Without one (nullptr, or another grid) CTA b takes
+    // rows[b], rows[b + grid], ...
+    const int64_t* cta_first;
+    int64_t plan_grid;
     // CUDA-core kernel only: the first nsplit rows are done as nsegs segments, each
     // writing its partial Gram rows and right-hand side to part; the last segment of
     // a row to finish (counted in seg_done, which it resets) sums them in segment

@@ -12,7 +12,11 @@
 // 128B-swizzled atoms of a stage (h rows, l rows, and the ratings in the first
 // two columns of an otherwise zero atom), so each k-block reads them once.
 //
-// One CTA per SM, persistent over the rows of the long bin (12 or 16 warps, by shape):
+// One CTA per SM, persistent over the rows of the long bin (12 or 16 warps, by shape).
+// The rows, longest first, are dealt round-robin to the CTAs, or by the host's balanced
+// plan (each row to the CTA with the least work so far) where round-robin would leave
+// one CTA well above the mean (a few rows of 2.7e5 ratings among thousands of shorter
+// ones).  Warp roles:
 //   warp 0       MMA issuer (one lane) and TMEM owner (512 columns)
 //   warp 1       prefetch: row descriptors (row, first, last rating) into a
 //                ring, and every stage's rating indices and values into a
@@ -319,8 +323,12 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int G = gridDim.x;
-    // rows of this CTA: a.rows[blockIdx.x + j * G] for j < nj (longest first)
-    const int64_t nj = a.nrows > blockIdx.x ? (a.nrows - blockIdx.x + G - 1) / G : 0;
+    // rows of this CTA, longest first: a.rows[first + j] for j < nj under a balanced
+    // plan made for this grid, else a.rows[blockIdx.x + j * G]
+    const bool planned = a.cta_first != nullptr && a.plan_grid == (int64_t)G;
+    const int64_t first = planned ? __ldg(a.cta_first + blockIdx.x) : 0;
+    const int64_t nj = planned ? __ldg(a.cta_first + blockIdx.x + 1) - first
+                               : (a.nrows > blockIdx.x ? (a.nrows - blockIdx.x + G - 1) / G : 0);
     const WaitCtx wc{abort_flag, a.timeout_ns, a.ctl};
 
     // ---- set-up: zero the ratings atoms (and the l atoms, which the BF16 Gram leaves
@@ -530,7 +538,7 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
                 int my_row = -1;
                 long long my_p0 = 0, my_p1 = 0;
                 if (jj < nj) {
-                    my_row = __ldg(a.rows + blockIdx.x + jj * G);
+                    my_row = __ldg(a.rows + (planned ? first + jj : blockIdx.x + jj * G));
                     my_p0 = __ldg(a.ptr + my_row);
                     my_p1 = __ldg(a.ptr + my_row + 1);
                 }

@@ -51,6 +51,42 @@ def test_long_row_shape_parity(bp):
     assert_worst(step_parity(bp, prob, sweeps=2))
 
 
+def test_balanced_row_plan_parity_and_identity(bp):
+    """Tensor-core rows dealt to the CTAs by the balanced plan (each row, longest first, to
+    the CTA with the least work so far).  2,000 users with ~60 ratings and 160 with ~1,060:
+    round-robin would give a few CTAs two of the long rows (the busiest 1.27x the mean), so
+    the user side gets a plan for both launch grids; the movie side (within 4%) keeps
+    round-robin.  Parity with the oracle, and bpmf_sweep (one SM left to the hyper steps)
+    bit-identical to phase-by-phase stepping (every SM): a row's result does not depend on
+    which CTA takes it."""
+    import torch
+    prob = workloads.random_small(2000, 1200, 64, 120000, seed=77, n_test=300, long_rows=160,
+                                  long_deg=1000)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    a = bp.create_from_problem(prob, stream=sa.cuda_stream)
+    b = bp.create_from_problem(prob, stream=sb.cuda_stream)
+    try:
+        assert bp.bpmf_info(a, 0)["balanced"] == 3 and bp.bpmf_info(a, 1)["balanced"] == 0
+        assert bp.bpmf_info(a, 0)["n_long"] > 2 * torch.cuda.get_device_properties(0).multi_processor_count
+        ra = bp.bpmf_sweep(a, 2)
+        seq = (bp.BPMF_PHASE_HYPER_MOVIE, bp.BPMF_PHASE_ROWS_MOVIE, bp.BPMF_PHASE_HYPER_USER,
+               bp.BPMF_PHASE_ROWS_USER, bp.BPMF_PHASE_PREDICT, bp.BPMF_PHASE_ADVANCE)
+        for _ in range(2):
+            for ph in seq:
+                bp.bpmf_step(b, ph)
+        rb = bp.bpmf_sweep(b, 0)
+        st_a = bp.bpmf_get_state(a, prob.M, prob.N, prob.K)
+        st_b = bp.bpmf_get_state(b, prob.M, prob.N, prob.K)
+        for x, y in zip(st_a[:3], st_b[:3]):
+            np.testing.assert_array_equal(x, y)
+        assert ra == rb
+        assert bp.bpmf_status(a) == 0 and bp.bpmf_status(b) == 0
+    finally:
+        bp.bpmf_destroy(a)
+        bp.bpmf_destroy(b)
+    assert_worst(step_parity(bp, prob, sweeps=1))
+
+
 # BF16 Gram: per-row means and samples within 1e-2 relative of the FP64 oracle (the
 # rows enter the MMA rounded to 8 significant bits, 2^-9 relative per entry; the
 # measured worst is printed).
