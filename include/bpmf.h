@@ -205,6 +205,20 @@ int bpmf_debug_means(bpmf_handle h, int32_t side, float* out);
  * BPMF_ETIMEOUT.  Syncs the handle's stream. */
 int bpmf_status(bpmf_handle h);
 
+/* Host only (no device work, no handle): the balanced plan bpmf_create makes for
+ * the tensor-core rows of a launch of `grid` CTAs.  degree[k] (n entries, >= 0) are
+ * the rows' rating counts in the order the kernel deals them (longest first); a row
+ * costs its 64-rating stages plus two (Sec. 4.2's fixed-plus-per-rating cost of an
+ * item).  When round-robin (row k to CTA k mod grid) would leave the busiest CTA
+ * more than 5% above the mean cost and there are more rows than CTAs, *planned = 1,
+ * order_out[p] (n entries) is the row placed at p and CTA c takes places
+ * first_out[c] .. first_out[c + 1] - 1 (first_out: min(n, grid) + 1 entries), each
+ * row, longest first, given to the CTA with the least cost so far (ties: lowest
+ * CTA); else *planned = 0 and the outputs are not written.  BPMF_EINVAL on a
+ * negative n or degree, grid < 1, or a NULL pointer that is needed. */
+int bpmf_balance_rows(int64_t n, const int64_t* degree, int64_t grid, int32_t* order_out,
+                      int64_t* first_out, int32_t* planned);
+
 /* Diagnostics: number of rows of `side` on the CUDA-core kernel and on the
  * tensor-core kernel, how many of the former are split and into how many
  * segments, the centring mean, device bytes held, and `balanced`: bit 0 (bit 1)

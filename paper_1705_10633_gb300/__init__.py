@@ -86,6 +86,7 @@ def lib():
     L.bpmf_info.argtypes = [vp, i32, P(i64), P(i64), P(i64), P(i64), P(C.c_double), P(i64),
                             P(i32)]
     L.bpmf_launch_count.argtypes = [vp, P(i64)]
+    L.bpmf_balance_rows.argtypes = [i64, P(i64), i64, P(i32), P(i64), P(i32)]
     L.bpmf_set_row_timing.argtypes = [vp, i32]
     L.bpmf_row_launch_ms.argtypes = [vp, P(C.c_float), P(C.c_float)]
     L.bpmf_row_stats_noalloc.argtypes = [vp, i64, i32, vp, vp, vp, vp]
@@ -281,6 +282,21 @@ def bpmf_info(h, side):
             "balanced": bal.value}
 
 
+def bpmf_balance_rows(degree, grid):
+    """The balanced plan for rows of the given rating counts (longest first) over `grid`
+    CTAs: (order, first) numpy arrays, or None when round-robin is kept.  Host only."""
+    deg = np.ascontiguousarray(degree, dtype=np.int64)
+    n = deg.shape[0]
+    order = np.empty(max(n, 1), dtype=np.int32)
+    first = np.empty(min(n, int(grid)) + 1 if n else 1, dtype=np.int64)
+    planned = C.c_int32()
+    _check(lib().bpmf_balance_rows(n, deg.ctypes.data_as(C.POINTER(C.c_int64)), int(grid),
+                                   order.ctypes.data_as(C.POINTER(C.c_int32)),
+                                   first.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(planned)),
+           "bpmf_balance_rows")
+    return (order[:n], first) if planned.value else None
+
+
 def bpmf_set_row_timing(h, on=True):
     """Record CUDA events around the row kernels of phases run by bpmf_step."""
     _check(lib().bpmf_set_row_timing(h, 1 if on else 0), "bpmf_set_row_timing")
@@ -328,7 +344,7 @@ EXPORTED = ["bpmf_default_params", "bpmf_create", "bpmf_sweep", "bpmf_sweep_batc
             "bpmf_predict",
             "bpmf_get_state", "bpmf_set_state", "bpmf_get_accum", "bpmf_set_accum",
             "bpmf_get_stats", "bpmf_debug_means", "bpmf_status", "bpmf_info", "bpmf_launch_count",
-            "bpmf_set_row_timing", "bpmf_row_launch_ms",
+            "bpmf_set_row_timing", "bpmf_row_launch_ms", "bpmf_balance_rows",
             "bpmf_row_stats_noalloc",
             "bpmf_strerror",
             "bpmf_destroy"]

@@ -340,44 +340,60 @@ int plan_segments(bpmf_ctx* h, DevSide& d, const std::vector<int32_t>& order)
 // 480k x 18k workload's movie launch, while its users are within 2%.
 constexpr double kPlanImbalance = 1.05;
 
+int64_t plan_cost(int64_t degree) { return (degree + 63) / 64 + 2; }
+
+// The plan for n items of the given costs (in the order they would be dealt) over G CTAs:
+// false when round-robin is kept; else pos[p] = the item at place p, CTA c's items at
+// places first[c] .. first[c + 1] - 1 in dealing order.
+bool balance_plan(const std::vector<int64_t>& cost, int64_t G, std::vector<int32_t>& pos,
+                  std::vector<int64_t>& first)
+{
+    const int64_t n = (int64_t)cost.size();
+    if (G < 1 || n <= G) return false;  // one item per CTA at most: nothing to balance
+    int64_t total = 0;
+    std::vector<int64_t> rr((size_t)G, 0);
+    for (int64_t k = 0; k < n; ++k) {
+        rr[(size_t)(k % G)] += cost[(size_t)k];
+        total += cost[(size_t)k];
+    }
+    const int64_t rr_max = *std::max_element(rr.begin(), rr.end());
+    if ((double)rr_max * (double)G <= kPlanImbalance * (double)total) return false;
+    using Load = std::pair<int64_t, int64_t>;  // (work so far, CTA): ties by CTA index
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> least;
+    for (int64_t c = 0; c < G; ++c) least.push({0, c});
+    std::vector<int32_t> owner((size_t)n);
+    for (int64_t k = 0; k < n; ++k) {
+        Load l = least.top();
+        least.pop();
+        owner[(size_t)k] = (int32_t)l.second;
+        l.first += cost[(size_t)k];
+        least.push(l);
+    }
+    first.assign((size_t)G + 1, 0);
+    for (int64_t k = 0; k < n; ++k) ++first[(size_t)owner[(size_t)k] + 1];
+    for (int64_t c = 0; c < G; ++c) first[(size_t)c + 1] += first[(size_t)c];
+    std::vector<int64_t> fill(first.begin(), first.end() - 1);
+    pos.resize((size_t)n);
+    for (int64_t k = 0; k < n; ++k) pos[(size_t)fill[(size_t)owner[(size_t)k]]++] = (int32_t)k;
+    return true;
+}
+
 int plan_long_bin(bpmf_ctx* h, DevSide& d, const std::vector<int32_t>& order)
 {
     d.plan_grid[0] = d.plan_grid[1] = 0;
     const int64_t n = d.n_long;
     if (!h->tc || n == 0) return BPMF_OK;
     std::vector<int64_t> cost((size_t)n);
-    int64_t total = 0;
     for (int64_t k = 0; k < n; ++k) {
         const int32_t row = order[(size_t)(d.n_short + k)];
-        const int64_t deg = d.ptr_h[(size_t)row + 1] - d.ptr_h[(size_t)row];
-        cost[(size_t)k] = (deg + 63) / 64 + 2;
-        total += cost[(size_t)k];
+        cost[(size_t)k] = plan_cost(d.ptr_h[(size_t)row + 1] - d.ptr_h[(size_t)row]);
     }
-    std::vector<int32_t> plan((size_t)n), owner((size_t)n);
-    std::vector<int64_t> first, rr, fill;
+    std::vector<int32_t> pos, plan((size_t)n);
+    std::vector<int64_t> first;
     for (int q = 0; q < 2; ++q) {
         const int64_t G = std::min<int64_t>(n, h->num_sms - q);
-        if (G < 1 || n <= G) continue;  // one row per CTA at most: nothing to balance
-        rr.assign((size_t)G, 0);
-        for (int64_t k = 0; k < n; ++k) rr[(size_t)(k % G)] += cost[(size_t)k];
-        const int64_t rr_max = *std::max_element(rr.begin(), rr.end());
-        if ((double)rr_max * (double)G <= kPlanImbalance * (double)total) continue;
-        using Load = std::pair<int64_t, int64_t>;  // (work so far, CTA): ties by CTA index
-        std::priority_queue<Load, std::vector<Load>, std::greater<Load>> least;
-        for (int64_t c = 0; c < G; ++c) least.push({0, c});
-        for (int64_t k = 0; k < n; ++k) {
-            Load l = least.top();
-            least.pop();
-            owner[(size_t)k] = (int32_t)l.second;
-            l.first += cost[(size_t)k];
-            least.push(l);
-        }
-        first.assign((size_t)G + 1, 0);
-        for (int64_t k = 0; k < n; ++k) ++first[(size_t)owner[(size_t)k] + 1];
-        for (int64_t c = 0; c < G; ++c) first[(size_t)c + 1] += first[(size_t)c];
-        fill.assign(first.begin(), first.end() - 1);
-        for (int64_t k = 0; k < n; ++k)
-            plan[(size_t)fill[(size_t)owner[(size_t)k]]++] = order[(size_t)(d.n_short + k)];
+        if (!balance_plan(cost, G, pos, first)) continue;
+        for (int64_t p = 0; p < n; ++p) plan[(size_t)p] = order[(size_t)(d.n_short + pos[(size_t)p])];
         if (n > d.plan_cap[q]) {
             if (!alloc_n(h, &d.plan_rows[q], (size_t)n)) return BPMF_ENOMEM;
             d.plan_cap[q] = n;
@@ -1262,6 +1278,26 @@ int bpmf_launch_count(bpmf_handle h, int64_t* launches)
 {
     if (!h || !launches) return BPMF_EINVAL;
     *launches = h->launches;
+    return BPMF_OK;
+}
+
+int bpmf_balance_rows(int64_t n, const int64_t* degree, int64_t grid, int32_t* order_out,
+                      int64_t* first_out, int32_t* planned)
+{
+    if (n < 0 || grid < 1 || !planned || (n > 0 && (!degree || !order_out || !first_out)))
+        return BPMF_EINVAL;
+    std::vector<int64_t> cost((size_t)n);
+    for (int64_t k = 0; k < n; ++k) {
+        if (degree[k] < 0) return BPMF_EINVAL;
+        cost[(size_t)k] = plan_cost(degree[k]);
+    }
+    std::vector<int32_t> pos;
+    std::vector<int64_t> first;
+    *planned = balance_plan(cost, std::min<int64_t>(n, grid), pos, first) ? 1 : 0;
+    if (*planned) {
+        std::copy(pos.begin(), pos.end(), order_out);
+        std::copy(first.begin(), first.end(), first_out);
+    }
     return BPMF_OK;
 }
 
