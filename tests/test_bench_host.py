@@ -74,3 +74,9 @@ def test_row_work_figures_match_loop_counts():
     assert bench.row_gram_flops(1, K) == 2 * (K * K + K)
     assert bench.row_gather_bytes(1, 0, K) == 4 + 4 + 2 * 2 * K
     assert bench.row_gather_bytes(0, 1, K) == 2 * 8 + 4 * K + 2 * 2 * K
+
+
+def test_l2_note_states_how_inputs_stand_to_l2():
+    # the ratings are held twice (row and column views), 8 B per rating each
+    assert bench.l2_note(98_959_257).startswith("inputs larger than L2 (ratings CSR+CSC 1.58 GB)")
+    assert bench.l2_note(20_000).startswith("inputs fit in L2")
