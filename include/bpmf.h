@@ -205,6 +205,16 @@ int bpmf_debug_means(bpmf_handle h, int32_t side, float* out);
  * BPMF_ETIMEOUT.  Syncs the handle's stream. */
 int bpmf_status(bpmf_handle h);
 
+/* Host only (no device work, no handle): the degree bins bpmf_create makes for one
+ * side.  ptr: rows + 1 offsets of the side's ratings (ptr[0] = 0, non-decreasing);
+ * rows with at least long_min ratings form the tensor-core bin (long_min <= 0: no such
+ * bin).  order_out (rows entries) receives the short bin, then the long bin, each
+ * longest first with equal degrees in ascending row order (a counting sort, Sec. 4.2's
+ * ordering of items by cost); *n_short the size of the short bin.  BPMF_EINVAL on
+ * rows < 1 or above INT32_MAX, a NULL pointer or malformed offsets. */
+int bpmf_bin_rows(int64_t rows, const int64_t* ptr, int64_t long_min, int32_t* order_out,
+                  int64_t* n_short);
+
 /* Host only (no device work, no handle): the balanced plan bpmf_create makes for
  * the tensor-core rows of a launch of `grid` CTAs.  degree[k] (n entries, >= 0) are
  * the rows' rating counts in the order the kernel deals them (longest first); a row

@@ -87,6 +87,7 @@ def lib():
                             P(i32)]
     L.bpmf_launch_count.argtypes = [vp, P(i64)]
     L.bpmf_balance_rows.argtypes = [i64, P(i64), i64, P(i32), P(i64), P(i32)]
+    L.bpmf_bin_rows.argtypes = [i64, P(i64), i64, P(i32), P(i64)]
     L.bpmf_set_row_timing.argtypes = [vp, i32]
     L.bpmf_row_launch_ms.argtypes = [vp, P(C.c_float), P(C.c_float)]
     L.bpmf_row_stats_noalloc.argtypes = [vp, i64, i32, vp, vp, vp, vp]
@@ -282,6 +283,20 @@ def bpmf_info(h, side):
             "balanced": bal.value}
 
 
+def bpmf_bin_rows(ptr, long_min):
+    """Degree bins of one side's rows (offsets `ptr`, rows + 1 entries): (order, n_short),
+    the short bin then the long bin (rows of at least long_min ratings), each longest first.
+    Host only."""
+    p = np.ascontiguousarray(ptr, dtype=np.int64)
+    rows = p.shape[0] - 1
+    order = np.empty(max(rows, 1), dtype=np.int32)
+    ns = C.c_int64()
+    _check(lib().bpmf_bin_rows(rows, p.ctypes.data_as(C.POINTER(C.c_int64)), int(long_min),
+                               order.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(ns)),
+           "bpmf_bin_rows")
+    return order[:rows], ns.value
+
+
 def bpmf_balance_rows(degree, grid):
     """The balanced plan for rows of the given rating counts (longest first) over `grid`
     CTAs: (order, first) numpy arrays, or None when round-robin is kept.  Host only."""
@@ -344,7 +359,7 @@ EXPORTED = ["bpmf_default_params", "bpmf_create", "bpmf_sweep", "bpmf_sweep_batc
             "bpmf_predict",
             "bpmf_get_state", "bpmf_set_state", "bpmf_get_accum", "bpmf_set_accum",
             "bpmf_get_stats", "bpmf_debug_means", "bpmf_status", "bpmf_info", "bpmf_launch_count",
-            "bpmf_set_row_timing", "bpmf_row_launch_ms", "bpmf_balance_rows",
+            "bpmf_set_row_timing", "bpmf_row_launch_ms", "bpmf_bin_rows", "bpmf_balance_rows",
             "bpmf_row_stats_noalloc",
             "bpmf_strerror",
             "bpmf_destroy"]

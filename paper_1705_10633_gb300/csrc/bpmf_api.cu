@@ -1281,6 +1281,18 @@ int bpmf_launch_count(bpmf_handle h, int64_t* launches)
     return BPMF_OK;
 }
 
+int bpmf_bin_rows(int64_t rows, const int64_t* ptr, int64_t long_min, int32_t* order_out,
+                  int64_t* n_short)
+{
+    if (rows < 1 || rows > (int64_t)INT32_MAX || !ptr || !order_out || !n_short) return BPMF_EINVAL;
+    if (!valid_ptr(rows, ptr)) return BPMF_EINVAL;
+    std::vector<int32_t> order;
+    int64_t nl = 0, lr = 0;
+    bin_rows(rows, ptr, long_min > 0 ? long_min : INT64_MAX, order, n_short, &nl, &lr);
+    std::copy(order.begin(), order.end(), order_out);
+    return BPMF_OK;
+}
+
 int bpmf_balance_rows(int64_t n, const int64_t* degree, int64_t grid, int32_t* order_out,
                       int64_t* first_out, int32_t* planned)
 {

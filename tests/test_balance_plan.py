@@ -1,11 +1,12 @@
-"""Host logic of the balanced row plan (no GPU).
+"""Host logic of the degree bins and of the balanced row plan (no GPU).
 
 bpmf_create deals each side's tensor-core rows (48 ratings or more when K pads to 64) to
 the CTAs of the persistent kernel.  Round-robin in longest-first order is kept unless it
 would leave the busiest CTA more than 5% above the mean; then every row, longest first,
 goes to the CTA with the least work so far (list scheduling over Sec. 4.2's item cost: a
-fixed part plus a part per rating; here 64-rating stages plus two).  bpmf_balance_rows
-runs the same host routine without a device, so these properties are checked on CPU.
+fixed part plus a part per rating; here 64-rating stages plus two).  bpmf_bin_rows and
+bpmf_balance_rows run the same host routines without a device, so these properties are
+checked on CPU.
 """
 import numpy as np
 import pytest
@@ -103,3 +104,29 @@ def test_invalid_arguments(bp):
     with pytest.raises(bp.BpmfError) as ei:
         bp.bpmf_balance_rows(np.array([5, 3]), 0)
     assert ei.value.code == bp.BPMF_EINVAL
+
+
+@pytest.mark.parametrize("long_min", [48, 1, 0, 10_000])
+def test_degree_bins_match_a_stable_sort(bp, long_min):
+    # the bins every row phase launches from: short bin then long bin, each longest first,
+    # equal degrees in ascending row order -- against numpy's stable sort
+    rng = np.random.default_rng(5)
+    deg = np.concatenate([rng.integers(0, 120, 3000), rng.integers(900, 1100, 40),
+                          np.zeros(7, dtype=np.int64)])
+    rng.shuffle(deg)
+    ptr = np.concatenate([[0], np.cumsum(deg)])
+    order, n_short = bp.bpmf_bin_rows(ptr, long_min)
+    lm = long_min if long_min > 0 else np.iinfo(np.int64).max
+    rows = np.arange(len(deg))
+    short, long_ = rows[deg < lm], rows[deg >= lm]
+    ref = np.concatenate([short[np.argsort(-deg[short], kind="stable")],
+                          long_[np.argsort(-deg[long_], kind="stable")]])
+    assert n_short == len(short)
+    np.testing.assert_array_equal(order, ref)
+
+
+def test_degree_bins_reject_malformed_offsets(bp):
+    for ptr in ([1, 2, 3], [0, 5, 4], [0]):
+        with pytest.raises(bp.BpmfError) as ei:
+            bp.bpmf_bin_rows(np.array(ptr), 48)
+        assert ei.value.code == bp.BPMF_EINVAL
