@@ -136,7 +136,7 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------
-# algorithmic work per phase (stated in the design doc)
+# algorithmic work per phase
 # ----------------------------------------------------------------------------
 def row_alu_flops(rows, K):
     """CUDA-core work per row: Cholesky K^3/3, forward and back substitution K^2
