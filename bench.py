@@ -338,8 +338,10 @@ def run_native(args):
     n_short = int(info_d["n_short"])
     short_ratings = int(deg[:n_short].sum())
     n_long, long_ratings = dom_rows - n_short, nnz - short_ratings
-    t_cc = float(np.mean([a for a, _ in launch_ms[dom]])) / 1e3
-    t_tc = float(np.mean([b for _, b in launch_ms[dom]])) / 1e3
+    t_cc = float(np.mean([a for a, _, _ in launch_ms[dom]])) / 1e3
+    t_gram = float(np.mean([b for _, b, _ in launch_ms[dom]])) / 1e3
+    t_chol = float(np.mean([c for _, _, c in launch_ms[dom]])) / 1e3
+    t_tc = t_gram + t_chol
     if tc_path and n_long > 0:
         kern, t_dom, units = "rows_tc_kernel", t_tc, (n_long, long_ratings)
         alu = row_alu_flops(n_long, K)
@@ -360,6 +362,8 @@ def run_native(args):
     roofline = {"bound": "alu",
                 "kernel": "%s (%s: %d rows, %d ratings)" % (kern, dom, units[0], units[1]),
                 "launch_ms": round(t_dom * 1e3, 4),
+                **({"gram_ms": round(t_gram * 1e3, 4), "chol_ms": round(t_chol * 1e3, 4)}
+                   if tc_path and n_long > 0 else {}),
                 "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / fp32_peak, 4),
                 "traffic": TRAFFIC.get(prob.name, {}).get(dom),

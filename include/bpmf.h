@@ -246,12 +246,14 @@ int bpmf_launch_count(bpmf_handle h, int64_t* launches);
 /*
  * Launch timing of the row phases run by bpmf_step (not inside bpmf_sweep, whose sweeps
  * may be a captured CUDA graph).  on != 0: each row phase records CUDA events on the
- * handle's stream around its CUDA-core launches and its tensor-core launch.
+ * handle's stream around its CUDA-core launches and around each of the two launches
+ * of the tensor-core route (the Gram kernel, then the factorisation kernel).
  * bpmf_row_launch_ms waits for the last timed row phase and returns each part's
- * milliseconds, -1 for a part that did not launch (or when timing is off).
+ * milliseconds (host pointers, all three required), -1 for a part that did not
+ * launch (or when timing is off).
  */
 int bpmf_set_row_timing(bpmf_handle h, int32_t on);
-int bpmf_row_launch_ms(bpmf_handle h, float* cuda_core_ms, float* tensor_core_ms);
+int bpmf_row_launch_ms(bpmf_handle h, float* cuda_core_ms, float* gram_ms, float* chol_ms);
 
 /*
  * Row statistics of a device matrix, computed without allocating any memory.

@@ -89,7 +89,7 @@ def lib():
     L.bpmf_balance_rows.argtypes = [i64, P(i64), i64, P(i32), P(i64), P(i32)]
     L.bpmf_bin_rows.argtypes = [i64, P(i64), i64, P(i32), P(i64)]
     L.bpmf_set_row_timing.argtypes = [vp, i32]
-    L.bpmf_row_launch_ms.argtypes = [vp, P(C.c_float), P(C.c_float)]
+    L.bpmf_row_launch_ms.argtypes = [vp, P(C.c_float), P(C.c_float), P(C.c_float)]
     L.bpmf_row_stats_noalloc.argtypes = [vp, i64, i32, vp, vp, vp, vp]
     L.bpmf_strerror.argtypes = [C.c_int]
     L.bpmf_strerror.restype = C.c_char_p
@@ -318,11 +318,11 @@ def bpmf_set_row_timing(h, on=True):
 
 
 def bpmf_row_launch_ms(h):
-    """(CUDA-core ms, tensor-core ms) of the last timed row phase; -1 for a part that did
-    not launch."""
-    a, b = C.c_float(), C.c_float()
-    _check(lib().bpmf_row_launch_ms(h, C.byref(a), C.byref(b)), "bpmf_row_launch_ms")
-    return a.value, b.value
+    """(CUDA-core ms, Gram ms, factorisation ms) of the last timed row phase; -1 for a
+    part that did not launch."""
+    a, b, c = C.c_float(), C.c_float(), C.c_float()
+    _check(lib().bpmf_row_launch_ms(h, C.byref(a), C.byref(b), C.byref(c)), "bpmf_row_launch_ms")
+    return a.value, b.value, c.value
 
 
 def bpmf_launch_count(h):

@@ -105,12 +105,17 @@ struct bpmf_ctx {
     int pred_blocks = 1;
     Control* ctl = nullptr;
     std::vector<void*> allocs;
+    std::vector<size_t> alloc_bytes;
     int64_t bytes = 0;
     int64_t launches = 0;  // kernels launched by the phases
     // bpmf_set_row_timing: events around the row kernels of phases run by bpmf_step
     bool row_timing = false;
-    cudaEvent_t tev[3] = {nullptr, nullptr, nullptr};
-    int timed_parts = 0;  // bit 0: CUDA-core launches recorded, bit 1: tensor-core launch
+    cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int timed_parts = 0;  // bit 0: CUDA-core launches recorded, bit 1: tensor-core launches
+    // scratch of the tensor-core route: one slot (precision and right-hand side) per row
+    // of the larger long bin
+    float* gram = nullptr;
+    int64_t gram_cap = 0;
 };
 
 namespace {
@@ -130,6 +135,7 @@ void* dalloc(bpmf_ctx* h, size_t bytes)
     }
     if (p) {
         h->allocs.push_back(p);
+        h->alloc_bytes.push_back(bytes);
         h->bytes += (int64_t)bytes;
     }
     return p;
@@ -155,6 +161,21 @@ void temp_free(void* p, void* ctx)
     if (!p) return;
     if (h->p.free) h->p.free(p, (void*)h->stream, h->p.alloc_ctx);
     else cudaFree(p);
+}
+
+// Release one allocation made by dalloc before the handle is destroyed.
+void dfree(bpmf_ctx* h, void* p)
+{
+    if (!p) return;
+    for (size_t k = 0; k < h->allocs.size(); ++k) {
+        if (h->allocs[k] != p) continue;
+        h->allocs.erase(h->allocs.begin() + (std::ptrdiff_t)k);
+        h->bytes -= (int64_t)h->alloc_bytes[k];
+        h->alloc_bytes.erase(h->alloc_bytes.begin() + (std::ptrdiff_t)k);
+        if (h->p.free) h->p.free(p, (void*)h->stream, h->p.alloc_ctx);
+        else cudaFree(p);
+        return;
+    }
 }
 
 template <class T>
@@ -418,6 +439,16 @@ int bin_side(bpmf_ctx* h, DevSide& d, std::vector<int32_t>& order)
 {
     bin_rows(d.rows, d.ptr_h.data(), h->tc ? h->long_min : INT64_MAX, order, &d.n_short, &d.n_long,
              &d.long_ratings);
+    if (h->tc && d.n_long > h->gram_cap) {
+        // the scratch grows to the longest long bin; the old one is no longer referenced
+        // (the stream is idle here: binning waits for it)
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BPMF_ECUDA;
+        dfree(h, h->gram);
+        h->gram = nullptr;
+        h->gram_cap = 0;
+        if (!alloc_n(h, &h->gram, (size_t)d.n_long * kGramSlotFloats)) return BPMF_ENOMEM;
+        h->gram_cap = d.n_long;
+    }
     cudaError_t e = cudaMemcpyAsync(d.bin_rows, order.data(), sizeof(int32_t) * d.rows,
                                     cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return BPMF_ECUDA;
@@ -432,10 +463,11 @@ int sync_status(bpmf_ctx* h)
     cudaError_t e = cudaMemcpyAsync(&c, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return BPMF_ECUDA;
+    // a timed-out wait comes first: the launches after it may report what it left behind
+    if (c.status & kStatusTimeout) return BPMF_ETIMEOUT;
     if (c.status & kStatusNotPD) return BPMF_ENOTPD;
     if (c.status & kStatusNaN) return BPMF_ENAN;
     if (c.status & kStatusGamma) return BPMF_EGAMMA;
-    if (c.status & kStatusTimeout) return BPMF_ETIMEOUT;
     return BPMF_OK;
 }
 
@@ -543,11 +575,17 @@ int phase_rows(bpmf_ctx* h, int s, bool timed = false)
             a.cta_first = d.plan_first[q];
             a.plan_grid = grid;
         }
+    a.gram = h->gram;
     if (e == cudaSuccess && a.nrows > 0) {
         h->launches += 1;
-        e = launch_rows_tc(a, d.long_ratings, h->long_shape_degree, h->row_sms, h->stream);
+        e = launch_rows_gram(a, h->row_sms, h->stream);
     }
     if (e == cudaSuccess && timed) e = cudaEventRecord(h->tev[2], h->stream);
+    if (e == cudaSuccess && a.nrows > 0) {
+        h->launches += 1;
+        e = launch_rows_chol(a, h->row_sms, h->stream);
+    }
+    if (e == cudaSuccess && timed) e = cudaEventRecord(h->tev[3], h->stream);
     return cuda_rc(e);
 }
 
@@ -1027,10 +1065,11 @@ int read_rmse(bpmf_ctx* h, double* rmse_sample, double* rmse_avg)
     if (e != cudaSuccess) return BPMF_ECUDA;
     if (rmse_sample) *rmse_sample = c.rmse_sample;
     if (rmse_avg) *rmse_avg = c.rmse_avg;
+    // a timed-out wait comes first: the launches after it may report what it left behind
+    if (c.status & kStatusTimeout) return BPMF_ETIMEOUT;
     if (c.status & kStatusNotPD) return BPMF_ENOTPD;
     if (c.status & kStatusNaN) return BPMF_ENAN;
     if (c.status & kStatusGamma) return BPMF_EGAMMA;
-    if (c.status & kStatusTimeout) return BPMF_ETIMEOUT;
     return BPMF_OK;
 }
 
@@ -1257,20 +1296,24 @@ int bpmf_set_row_timing(bpmf_handle h, int32_t on)
     return BPMF_OK;
 }
 
-int bpmf_row_launch_ms(bpmf_handle h, float* cuda_core_ms, float* tensor_core_ms)
+int bpmf_row_launch_ms(bpmf_handle h, float* cuda_core_ms, float* gram_ms, float* chol_ms)
 {
-    if (!h || !cuda_core_ms || !tensor_core_ms) return BPMF_EINVAL;
-    *cuda_core_ms = *tensor_core_ms = -1.f;
+    if (!h || !cuda_core_ms || !gram_ms || !chol_ms) return BPMF_EINVAL;
+    *cuda_core_ms = *gram_ms = *chol_ms = -1.f;
     if (!h->row_timing || !h->timed_parts) return BPMF_OK;
-    if (cudaEventSynchronize(h->tev[2]) != cudaSuccess) return BPMF_ECUDA;
-    float a = 0.f, b = 0.f;
+    if (cudaEventSynchronize(h->tev[3]) != cudaSuccess) return BPMF_ECUDA;
+    float a = 0.f, b = 0.f, c = 0.f;
     if (cudaEventElapsedTime(&a, h->tev[0], h->tev[1]) != cudaSuccess ||
-        cudaEventElapsedTime(&b, h->tev[1], h->tev[2]) != cudaSuccess) {
+        cudaEventElapsedTime(&b, h->tev[1], h->tev[2]) != cudaSuccess ||
+        cudaEventElapsedTime(&c, h->tev[2], h->tev[3]) != cudaSuccess) {
         cudaGetLastError();
         return BPMF_ECUDA;
     }
     if (h->timed_parts & 1) *cuda_core_ms = a;
-    if (h->timed_parts & 2) *tensor_core_ms = b;
+    if (h->timed_parts & 2) {
+        *gram_ms = b;
+        *chol_ms = c;
+    }
     return BPMF_OK;
 }
 

@@ -56,6 +56,10 @@ struct RowArgs {
     // order and samples the row
     const Segment* segs;
     int64_t nsegs;
+    // tensor-core route (kp == 64): the Gram kernel writes each row's precision and
+    // right-hand side to slot p of `gram` (p = the row's place in `rows`), the
+    // factorisation kernel reads them back
+    float* gram;
     int64_t nsplit;
     float* part;
     unsigned int* seg_done;
@@ -165,10 +169,16 @@ cudaError_t build_csc_device(const int64_t* csr_ptr, const int32_t* csr_col, con
                              int64_t M, int64_t N, int64_t nnz, int64_t* csc_ptr, int32_t* csc_row,
                              float* csc_val, const TempAlloc& tmp, cudaStream_t s);
 
-// nratings: ratings of the rows in a.rows; rows averaging shape_degree ratings or more
-// take the CTA shape with more gather stages.
-cudaError_t launch_rows_tc(const RowArgs& a, int64_t nratings, int64_t shape_degree, int num_sms,
-                           cudaStream_t s);
+// One slot of the tensor-core route's scratch (K = 64): the lower triangle of
+// Lambda_i in float4 chunks, chunk column c (columns 4c .. 4c + 3) holding rows
+// 4c .. 63 consecutively from float4 gram_chunk_offset(c), then b_i (64 floats).
+constexpr int kGramChunks = 544;
+constexpr int kGramSlotFloats = 4 * kGramChunks + 64;
+__host__ __device__ constexpr int gram_chunk_offset(int c) { return c * (66 - 2 * c); }
+// Gram kernel (A3 on tensor cores): Lambda_i and b_i of the rows in a.rows into a.gram.
+cudaError_t launch_rows_gram(const RowArgs& a, int num_sms, cudaStream_t s);
+// Factorisation kernel (A4, A5): reads a.gram, writes the rows' new factors.
+cudaError_t launch_rows_chol(const RowArgs& a, int num_sms, cudaStream_t s);
 // FP16 hi/lo split of a factor matrix (after init or set_state).
 cudaError_t launch_split_factors(const float* X, int64_t rows, int ld, __half* Xh, __half* Xl,
                                  int bf16, cudaStream_t s);

@@ -1,0 +1,90 @@
+// k_rows_chol.cu -- factor, solve and sample the long rows whose precision and
+// right-hand side the Gram kernel (k_rows_tc.cu) left in the scratch (Sec. 3.1: a
+// Cholesky factorisation instead of an inverse; Alg. 1: the new vector is the
+// conditional mean plus randomly sampled noise).
+//
+// One warp per row, twelve warps per CTA, one CTA per SM, rows dealt round-robin
+// over all warps of the grid (every row costs the same at K = 64).  Lane l loads
+// rows l and 32 + l of Lambda_i from the row's scratch slot straight into
+// registers (coalesced 16-B loads: the slot stores each float4 column chunk's rows
+// consecutively), then runs the shifted right-looking factorisation with the
+// forward solve fused, Philox noise and the back solve (rows_common.cuh), and
+// stores the FP32 row and its 16-bit split.
+#include "bpmf_internal.cuh"
+#include "philox.cuh"
+#include "rows_common.cuh"
+
+namespace bpmf {
+namespace {
+
+constexpr int kCholWarps = 12;
+// per warp: L^T (64 x 64, sw64 layout), the column buffers (2 x 64), 1 / diag (64),
+// noise (64)
+constexpr int kCholWarpFloats = 64 * 64 + 128 + 64 + 64;
+constexpr size_t kCholSmemBytes = (size_t)kCholWarps * kCholWarpFloats * 4;
+static_assert(kCholSmemBytes <= 232448, "shared memory");
+
+}  // namespace
+
+__global__ void __launch_bounds__(kCholWarps * 32, 1) rows_chol_kernel(RowArgs a)
+{
+    extern __shared__ __align__(16) float chol_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* M = chol_smem + warp * kCholWarpFloats;
+    float* cbuf = M + 4096;
+    float* dinv = cbuf + 128;
+    float* zb = dinv + 64;
+    const uint32_t sweep = (uint32_t)a.ctl->sweep;
+    // a Gram launch that gave up on a wait left its slots unfinished: nothing to factor
+    if (*reinterpret_cast<volatile unsigned int*>(&a.ctl->status) & kStatusTimeout) return;
+    bool bad = false;
+    const int64_t W = (int64_t)gridDim.x * kCholWarps;
+    for (int64_t p = (int64_t)blockIdx.x * kCholWarps + warp; p < a.nrows; p += W) {
+        const int row = __ldg(a.rows + p);
+        const float4* src = reinterpret_cast<const float4*>(a.gram + p * kGramSlotFloats);
+        float a1[32], a2[64];
+        // row lane: chunk columns c <= lane / 4; row 32 + lane: c <= 8 + lane / 4 (the
+        // rest of each row lies above the diagonal and is never used)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (4 * c <= lane) v = __ldg(src + gram_chunk_offset(c) + lane - 4 * c);
+            a1[4 * c + 0] = v.x;
+            a1[4 * c + 1] = v.y;
+            a1[4 * c + 2] = v.z;
+            a1[4 * c + 3] = v.w;
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (4 * c <= 32 + lane) v = __ldg(src + gram_chunk_offset(c) + 32 + lane - 4 * c);
+            a2[4 * c + 0] = v.x;
+            a2[4 * c + 1] = v.y;
+            a2[4 * c + 2] = v.z;
+            a2[4 * c + 3] = v.w;
+        }
+        const float* bsrc = a.gram + p * kGramSlotFloats + 4 * kGramChunks;
+        const float b1 = __ldg(bsrc + lane), b2 = __ldg(bsrc + 32 + lane);
+        __syncwarp();  // every lane's back solve of the previous row is done with M
+        float x1, x2, m1, m2;
+        factor_solve_sample_rl64(a1, a2, b1, b2, M, cbuf, dinv, zb, lane, a.K, a.seed,
+                                 (uint32_t)row, sweep, a.c3, a.means != nullptr, x1, x2, m1, m2,
+                                 bad);
+        store_row_panels(a, row, lane, x1, x2, m1, m2);
+    }
+    if (bad && lane == 0) atomicOr(&a.ctl->status, kStatusNotPD);
+}
+
+cudaError_t launch_rows_chol(const RowArgs& a, int num_sms, cudaStream_t s)
+{
+    if (a.nrows <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(rows_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kCholSmemBytes);
+    if (e != cudaSuccess) return e;
+    const int64_t need = (a.nrows + kCholWarps - 1) / kCholWarps;
+    const int64_t grid = need < num_sms ? need : num_sms;
+    rows_chol_kernel<<<(unsigned)grid, kCholWarps * 32, kCholSmemBytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace bpmf

@@ -1,40 +1,45 @@
-// k_rows_tc.cu -- per-row conditional update with the Gram on the 5th-generation
-// tensor cores (tcgen05, accumulators in TMEM), for rows with many ratings.
+// k_rows_tc.cu -- the Gram and right-hand side of each long row on the
+// 5th-generation tensor cores (tcgen05, accumulators in TMEM).
 //
 // The Gram sum_c y_c y_c^T of a row is a dense contraction over its ratings
-// (the "K x K outer product" of Sec. 3.1).  The other side's factors are kept
-// as an FP16 split y = h + l (|l| <= 2^-11 |h|) and the ratings as r = r_hi +
-// r_lo; one M = 128, N = 144 MMA per 16 ratings computes
-//     D = [H^T ; L^T] . [H | L | R]
-// whose column blocks 0..63 and 64..127, summed over both row halves, give
-// (H + L)^T (H + L) (FP32-class accuracy at the FP16 tensor rate), and whose
-// columns 128, 129 give (H + L)^T r.  A and B are the same three 64-wide
-// 128B-swizzled atoms of a stage (h rows, l rows, and the ratings in the first
-// two columns of an otherwise zero atom), so each k-block reads them once.
+// (the "K x K outer product" of Sec. 3.1).  The other side's factors are kept as
+// an FP16 split y = h + l (|l| <= 2^-11 |h|) and the ratings as r = r_hi + r_lo.
+// One M = 128, N = 80 MMA per 16 ratings computes
+//     D = [L^T ; H^T] . [H | R]
+// (A = the l and h rows, B = the h rows and the split ratings), so TMEM lanes
+// 0..63 hold L^T H and L^T r, lanes 64..127 hold H^T H and H^T r, and
+//     (H + L)^T (H + L) = H^T H + L^T H + (L^T H)^T + L^T L,
+// where the last term (2^-22 relative) is dropped.  A stage is three 64-wide
+// 128B-swizzled MN-major atoms (l rows, h rows, ratings in the first two columns
+// of an otherwise zero atom); A starts at the l atom, B at the h atom.
 //
-// One CTA per SM, persistent over the rows of the long bin (12 or 16 warps, by shape).
-// The rows, longest first, are dealt round-robin to the CTAs, or by the host's balanced
-// plan (each row to the CTA with the least work so far) where round-robin would leave
-// one CTA well above the mean (a few rows of 2.7e5 ratings among thousands of shorter
-// ones).  Warp roles:
-//   warp 0       MMA issuer (one lane) and TMEM owner (512 columns)
-//   warp 1       prefetch: row descriptors (row, first, last rating) into a
-//                ring, and every stage's rating indices and values into a
-//                second ring, far ahead of use (cp.async, mbarrier completion)
-//   warps 2-3    gather (with warps 8-9 in the long-row shape): cp.async of the
-//                128-B h and l rows of each rating into 128B-swizzled tiles
-//                (MN-major operand layout); they never wait for their copies,
-//                the stage barrier completes when they land
-//   warps 4-7    drain: TMEM -> shared Lambda_i += alpha Gram (the buffer starts
-//                from Lambda_X), b_i
-//   the rest     one row each: Cholesky, solves, Philox noise, store
-// Stages of 64 ratings flow producer -> MMA through mbarriers; accumulators
-// (3 TMEM slots of 144 columns) MMA -> drain; Lambda buffers (one per Cholesky warp) drain ->
-// Cholesky.  A long row is accumulated in chunks of 16 stages, each in a fresh
-// TMEM accumulator that the drain adds into the row's FP32 buffer: the tensor
-// core's accumulation rounding then grows with the chunk length only, not with
-// the row's degree (rows here reach 2.7e5 ratings).  Every wait is bounded in time; a timeout sets a status bit, the
-// CTA stops its loops, waits for its own copies and MMAs, frees TMEM and exits.
+// This kernel only forms Lambda_i = Lambda_X + alpha Gram and b_i = Lambda_X mu_X +
+// alpha (H + L)^T r and writes them to the row's slot of the scratch (layout in
+// bpmf_internal.cuh); k_rows_chol.cu factors them.  Keeping the factorisation out
+// of this kernel leaves the SM's issue slots and shared memory to the gather and
+// the tensor core, and the factorisation kernel runs with every warp of the SM.
+//
+// One CTA per SM, persistent over the rows (dealt round-robin, or by the host's
+// balanced plan where round-robin would be uneven).  Warp roles (16 warps):
+//   warp 0        MMA issuer (one lane) and TMEM owner (4 accumulators)
+//   warp 1        prefetch: row descriptors (row, first, last rating, slot) into a
+//                 ring, and every stage's rating indices and values into a second
+//                 ring, far ahead of use (cp.async, mbarrier completion)
+//   warps 2-3, 12-13   gather: cp.async of the 128-B h and l rows of each rating
+//                 into the swizzled atoms; the stage barrier completes when they land
+//   warps 4-7     drain group 0 (rows 0, 2, 4, ... of the CTA), warps 8-11 drain
+//                 group 1 (rows 1, 3, ...): TMEM -> registers, summed over the row's
+//                 accumulation chunks; at the row's end the L^T H rows go through a
+//                 shared staging buffer so the H^T H rows can add L^T H and its
+//                 transpose, add Lambda_X and store the packed lower triangle
+//   warps 14-15   idle (they give their registers to the drain warps)
+// Stages of 64 ratings flow producer -> MMA through mbarriers; accumulators MMA ->
+// drain (two per drain group).  A long row is accumulated in chunks of 16 stages,
+// each in a fresh accumulator that the drain adds into its registers: the tensor
+// core's accumulation rounding grows with the chunk length only, not with the row's
+// degree (rows here reach 2.7e5 ratings).  Every wait is bounded in time; a timeout
+// sets a status bit, the CTA stops its loops, waits for its own copies and MMAs,
+// frees TMEM and exits.
 #include "bpmf_internal.cuh"
 #include "philox.cuh"
 #include "rows_common.cuh"
@@ -44,71 +49,52 @@ namespace {
 
 constexpr int kKT = 64;
 constexpr int kStageRatings = 64;
-constexpr int kNAcc = 3;
-constexpr int kChunkStages = 16;  // stages per TMEM accumulation before it is flushed
-constexpr int kRowRing = 32;   // row descriptors in flight
-constexpr int kIdxRing = 8;    // stages of rating indices / values in flight
+constexpr int kChunkStages = 16;   // stages per TMEM accumulation before it is drained
+constexpr int kRowRing = 32;       // row descriptors in flight
+constexpr int kIdxRing = 8;        // stages of rating indices / values in flight
+constexpr int kGroups = 2;         // drain groups; rows alternate between them
+constexpr int kSlotsPerGroup = 2;  // TMEM accumulators per drain group
+constexpr int kNumAcc = kGroups * kSlotsPerGroup;
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kAccStride = 160;  // 144 columns used
+constexpr uint32_t kAccStride = 128;  // 80 columns used
+constexpr int kN = 80;                // MMA N: 64 h columns + the ratings atom's first 16
 
-constexpr uint32_t kTileBytes = kStageRatings * 128;        // 64 ratings x 64 halves
-constexpr uint32_t kRBytes = kTileBytes;                    // ratings atom (2 of 64 columns)
-constexpr uint32_t kStageBytes = 2 * kTileBytes + kRBytes;  // 24 KB (1 KB multiple)
-// A Lambda buffer: the lower triangle of the 64 x 64 precision in the XOR-swizzled
-// layout sw64 (row stride 64, 16-B chunks permuted by row & 7), then b (64 floats).
-constexpr uint32_t kLamFloats = 64 * 64 + 64;
-constexpr uint32_t kCholScratchFloats = 2 * 64 + 64 + 64;
+constexpr uint32_t kTileBytes = kStageRatings * 128;  // one atom: 64 ratings x 64 halves
+constexpr uint32_t kStageBytes = 3 * kTileBytes;      // l, h, ratings (24 KB)
+constexpr int kNStage = 7;
+constexpr int kGatherWarps = 4;
+constexpr int kGather = 32 * kGatherWarps;
+constexpr int kWarps = 16;
+constexpr int kThreads = kWarps * 32;
+constexpr uint32_t kStagingFloats = 64 * 64 + 64;  // L^T H rows (sw64 layout) and L^T r
 
-// Two shapes of the CTA, chosen per launch by the rows' mean degree:
-//   NCHOL Cholesky warps (and Lambda buffers), NSTAGE gather stages and EXTRA gather
-//   warps beside warps 2-3.
-// Rows of a few hundred ratings need many rows in factorisation at once (8, 3, 0);
-// rows of thousands of ratings, whose gathered rows come partly from HBM, need
-// more copies in flight and more threads issuing them, and few rows in factorisation
-// (2, 7, 2).  Warps: 0 MMA, 1 prefetch, 2-3 gather, 4-7 drain (TMEM lane quarters
-// 0-3), 8 .. 7 + EXTRA gather, then the Cholesky warps.  Registers after setmaxnreg:
-// producers kProdRegs, drain kDrainRegs, Cholesky kCholRegs.
-template <int NCHOL, int NSTAGE, int EXTRA>
-struct TcShape {
-    static constexpr int kNChol = NCHOL;
-    static constexpr int kNStage = NSTAGE;
-    static constexpr int kGather = 64 + 32 * EXTRA;  // gather threads
-    static constexpr int kCholWarp0 = 8 + EXTRA;
-    static constexpr int kThreads = (8 + EXTRA + NCHOL) * 32;
-    static_assert(kGather == 64 || kGather == 128, "gather threads");
-    static constexpr uint32_t kOffStages = 0;
-    static constexpr uint32_t kOffLam = kOffStages + NSTAGE * kStageBytes;
-    static constexpr uint32_t kOffChol = kOffLam + NCHOL * kLamFloats * 4;
-    static constexpr uint32_t kOffRtmp = kOffChol + NCHOL * kCholScratchFloats * 4;
-    static constexpr uint32_t kOffRowRing = kOffRtmp + 64 * 4;          // kRowRing x 32 B
-    static constexpr uint32_t kOffIdxRing = kOffRowRing + kRowRing * 32;  // kIdxRing x (64 idx + 64 val)
-    static constexpr uint32_t kOffBars = kOffIdxRing + kIdxRing * 512;
-    static constexpr int kNumBars = 2 * NSTAGE + 2 * kNAcc + 2 * NCHOL + 2 * kRowRing + 2 * kIdxRing + 1;
-    static constexpr uint32_t kOffMisc = kOffBars + kNumBars * 8;
-    static constexpr uint32_t kSmemBytes = kOffMisc + 16 + 1024;  // + alignment slack
-    // the launch gives 65536 / kThreads registers a thread (128 or 168)
-    static constexpr int kProdRegs = NCHOL == 8 ? 72 : 96;
-    static constexpr int kDrainRegs = NCHOL == 8 ? 96 : 128;
-    static constexpr int kCholRegs = NCHOL == 8 ? 168 : 176;
-    static_assert(kSmemBytes <= 232448, "shared memory");
-    static_assert(32 * ((4 + EXTRA) * kProdRegs + 4 * kDrainRegs + NCHOL * kCholRegs) <=
-                      kThreads * (65536 / kThreads / 8 * 8),
-                  "registers");
-};
-using ShapeShortRows = TcShape<8, 3, 0>;
-using ShapeLongRows = TcShape<2, 7, 2>;
-// The BF16 Gram gathers half the bytes (h rows only): its long rows run better with
-// four factorisation warps and 64 gather threads (measured: movie launch 5.00 against
-// 5.73 ms with the shape above, which takes the FP16 split's from 6.08 to 5.87 ms).
-using ShapeLongRowsBf16 = TcShape<4, 6, 0>;
+constexpr uint32_t kOffStages = 0;
+constexpr uint32_t kOffStaging = kOffStages + kNStage * kStageBytes;
+constexpr uint32_t kOffPrior = kOffStaging + kGroups * kStagingFloats * 4;  // packed Lambda_X, Lambda_X mu_X
+constexpr uint32_t kOffRowRing = kOffPrior + kGramSlotFloats * 4;            // kRowRing x 32 B
+constexpr uint32_t kOffIdxRing = kOffRowRing + kRowRing * 32;                // kIdxRing x (64 idx + 64 val)
+constexpr uint32_t kOffBars = kOffIdxRing + kIdxRing * 512;
+constexpr int kNumBars = 2 * kNStage + 2 * kNumAcc + 2 * kRowRing + 2 * kIdxRing + 1;
+constexpr uint32_t kOffMisc = kOffBars + kNumBars * 8;
+constexpr uint32_t kSmemBytes = kOffMisc + 16 + 1024;  // + alignment slack
+static_assert(kSmemBytes <= 232448, "shared memory");
+static_assert(kNumAcc * kAccStride <= kTmemCols, "TMEM columns");
+// Registers: the launch gives 128 a thread.  Each SM sub-partition holds warps w, w + 4,
+// w + 8, w + 12 -- one producer or idle warp, two drain warps and one gather or idle
+// warp -- and setmaxnreg moves registers within it: producer, gather and idle warps
+// drop to kProdRegs, drain warps rise to kDrainRegs.
+constexpr int kLaunchRegs = 128;
+constexpr int kProdRegs = 80;
+constexpr int kDrainRegs = 176;
+static_assert(2 * kProdRegs + 2 * kDrainRegs <= 4 * kLaunchRegs, "registers per sub-partition");
 
-// Instruction descriptor of kind::f16: D = F32, A = B = F16, both MN-major.
+// Instruction descriptor of kind::f16: D = F32, A = B = F16 (or BF16), both MN-major.
 constexpr uint32_t make_idesc(int M, int N)
 {
     return (1u << 4) | (0u << 7) | (0u << 10) | (1u << 15) | (1u << 16) |
            ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-constexpr uint32_t kIdesc = make_idesc(128, 144);
+constexpr uint32_t kIdesc = make_idesc(128, kN);
 constexpr uint32_t kIdescBf16 = kIdesc | (1u << 7) | (1u << 10);  // A and B in BF16
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -159,12 +145,17 @@ struct WaitCtx {
 
 // Wait for the phase of `bar` with parity `parity`; false after the time limit
 // (which also raises the CTA's abort flag and the status bit) or once aborted.
+// kBackoff: a role that tolerates latency (the drain, the producers) sleeps briefly
+// between polls, so its spinning does not take issue slots from the MMA issuer that
+// shares its SM sub-partition.
+template <bool kBackoff = false>
 __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, const WaitCtx& w)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (kBackoff) __nanosleep(64);
         if ((it & 31u) == 0) {
             if (*w.abort_flag) return false;
             if ((int64_t)(globaltimer_ns() - t0) > w.timeout_ns) {
@@ -255,64 +246,28 @@ __device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t& a, uint32_t& 
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+
 }  // namespace
 
-// One drain thread's share of a TMEM accumulator: row m of the Gram is the sum of
-// accumulator columns c and 64 + c; 16 of each per round, added into the row's
-// lower-triangle chunks (the buffer starts from the prior precision).  Warps
-// whose rows end before column 32 stop after two rounds; the trip count is
-// warp-uniform, as the collective loads require.
-__device__ __forceinline__ void drain_rows(uint32_t taddr, float* L, int m, int quarter, float alpha)
+template <bool kBf16>
+__global__ void __launch_bounds__(kThreads, 1) rows_gram_kernel(RowArgs a)
 {
-    const int ngroups = (quarter & 1) ? 4 : 2;
-#pragma unroll 1
-    for (int h = 0; h < ngroups; ++h) {
-        uint32_t g[16], e[16];
-        TMEM_LD16(taddr + 16 * h, g);
-        TMEM_LD16(taddr + 64 + 16 * h, e);
-        tmem_wait_ld();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int cc = 4 * h + q;
-            if (4 * cc <= m) {
-                float4* p = chunk_ptr(L, m, cc);
-                float4 v = *p;
-                v.x = fmaf(alpha, __uint_as_float(g[4 * q + 0]) + __uint_as_float(e[4 * q + 0]), v.x);
-                v.y = fmaf(alpha, __uint_as_float(g[4 * q + 1]) + __uint_as_float(e[4 * q + 1]), v.y);
-                v.z = fmaf(alpha, __uint_as_float(g[4 * q + 2]) + __uint_as_float(e[4 * q + 2]), v.z);
-                v.w = fmaf(alpha, __uint_as_float(g[4 * q + 3]) + __uint_as_float(e[4 * q + 3]), v.w);
-                *p = v;
-            }
-        }
-    }
-}
-
-template <class Shape, bool kBf16>
-__global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
-{
-    constexpr int kNChol = Shape::kNChol, kNStage = Shape::kNStage, kThreads = Shape::kThreads;
-    constexpr uint32_t kOffStages = Shape::kOffStages, kOffLam = Shape::kOffLam;
-    constexpr uint32_t kOffChol = Shape::kOffChol, kOffRtmp = Shape::kOffRtmp;
-    constexpr uint32_t kOffRowRing = Shape::kOffRowRing, kOffIdxRing = Shape::kOffIdxRing;
-    constexpr uint32_t kOffBars = Shape::kOffBars, kOffMisc = Shape::kOffMisc;
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(sm);
-    float* lam_bufs = reinterpret_cast<float*>(sm + kOffLam);
-    float* chol_scratch = reinterpret_cast<float*>(sm + kOffChol);
-    float* rtmp = reinterpret_cast<float*>(sm + kOffRtmp);
-    long long* row_ring = reinterpret_cast<long long*>(sm + kOffRowRing);  // [row, p0, p1, -]
+    float* staging = reinterpret_cast<float*>(sm + kOffStaging);
+    float4* prior4 = reinterpret_cast<float4*>(sm + kOffPrior);
+    float* prior_mu = reinterpret_cast<float*>(sm + kOffPrior) + 4 * kGramChunks;
+    long long* row_ring = reinterpret_cast<long long*>(sm + kOffRowRing);  // [row, p0, p1, slot]
     const int* idx_ring = reinterpret_cast<const int*>(sm + kOffIdxRing);
     const float* val_ring = reinterpret_cast<const float*>(sm + kOffIdxRing + 256);
     const uint32_t bars = sbase + kOffBars;
     const uint32_t bar_stage_full = bars;
     const uint32_t bar_stage_empty = bar_stage_full + 8 * kNStage;
     const uint32_t bar_acc_full = bar_stage_empty + 8 * kNStage;
-    const uint32_t bar_acc_empty = bar_acc_full + 8 * kNAcc;
-    const uint32_t bar_lam_full = bar_acc_empty + 8 * kNAcc;
-    const uint32_t bar_lam_empty = bar_lam_full + 8 * kNChol;
-    const uint32_t bar_row_full = bar_lam_empty + 8 * kNChol;
+    const uint32_t bar_acc_empty = bar_acc_full + 8 * kNumAcc;
+    const uint32_t bar_row_full = bar_acc_empty + 8 * kNumAcc;
     const uint32_t bar_row_empty = bar_row_full + 8 * kRowRing;
     const uint32_t bar_idx_full = bar_row_empty + 8 * kRowRing;
     const uint32_t bar_idx_empty = bar_idx_full + 8 * kIdxRing;
@@ -323,8 +278,8 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int G = gridDim.x;
-    // rows of this CTA, longest first: a.rows[first + j] for j < nj under a balanced
-    // plan made for this grid, else a.rows[blockIdx.x + j * G]
+    // rows of this CTA, longest first: places first .. first + nj - 1 of a.rows under a
+    // balanced plan made for this grid, else places blockIdx.x + j * G
     const bool planned = a.cta_first != nullptr && a.plan_grid == (int64_t)G;
     const int64_t first = planned ? __ldg(a.cta_first + blockIdx.x) : 0;
     const int64_t nj = planned ? __ldg(a.cta_first + blockIdx.x + 1) - first
@@ -332,31 +287,32 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
     const WaitCtx wc{abort_flag, a.timeout_ns, a.ctl};
 
     // ---- set-up: zero the ratings atoms (and the l atoms, which the BF16 Gram leaves
-    // unused), barriers, TMEM
-    for (uint32_t e = tid; e < kNStage * kRBytes / 16; e += kThreads) {
-        const uint32_t s = e / (kRBytes / 16), o = e % (kRBytes / 16);
+    // unused), the prior precision packed like a scratch slot, barriers, TMEM
+    for (uint32_t e = tid; e < kNStage * kTileBytes / 16; e += kThreads) {
+        const uint32_t s = e / (kTileBytes / 16), o = e % (kTileBytes / 16);
         *reinterpret_cast<uint4*>(sm + kOffStages + s * kStageBytes + 2 * kTileBytes + 16 * o) =
             make_uint4(0u, 0u, 0u, 0u);
         if (kBf16)
-            *reinterpret_cast<uint4*>(sm + kOffStages + s * kStageBytes + kTileBytes + 16 * o) =
+            *reinterpret_cast<uint4*>(sm + kOffStages + s * kStageBytes + 16 * o) =
                 make_uint4(0u, 0u, 0u, 0u);
     }
-    // every precision buffer starts from the prior precision
-    for (int b = 0; b < kNChol; ++b)
-        fill_lower_sw64(lam_bufs + b * kLamFloats, reinterpret_cast<const float4*>(a.lam_ct), tid,
-                        kThreads);
+    {
+        // Lambda_X comes chunk-transposed (float4 (i, 4c..4c+3) at c * 64 + i)
+        const float4* lam_ct = reinterpret_cast<const float4*>(a.lam_ct);
+        for (int e = tid; e < 1024; e += kThreads) {
+            const int i = e & 63, c = e >> 6;
+            if (4 * c <= i) prior4[gram_chunk_offset(c) + i - 4 * c] = __ldg(lam_ct + c * 64 + i);
+        }
+        for (int e = tid; e < 64; e += kThreads) prior_mu[e] = __ldg(a.lammu + e);
+    }
     if (tid == 0) {
         for (int s = 0; s < kNStage; ++s) {
-            mbar_init(bar_stage_full + 8 * s, Shape::kGather);
+            mbar_init(bar_stage_full + 8 * s, kGather);
             mbar_init(bar_stage_empty + 8 * s, 1);
         }
-        for (int s = 0; s < kNAcc; ++s) {
+        for (int s = 0; s < kNumAcc; ++s) {
             mbar_init(bar_acc_full + 8 * s, 1);
             mbar_init(bar_acc_empty + 8 * s, 128);
-        }
-        for (int s = 0; s < kNChol; ++s) {
-            mbar_init(bar_lam_full + 8 * s, 128);
-            mbar_init(bar_lam_empty + 8 * s, 32);
         }
         for (int s = 0; s < kRowRing; ++s) {
             mbar_init(bar_row_full + 8 * s, 1);
@@ -364,7 +320,7 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
         }
         for (int s = 0; s < kIdxRing; ++s) {
             mbar_init(bar_idx_full + 8 * s, 32);
-            mbar_init(bar_idx_empty + 8 * s, Shape::kGather);
+            mbar_init(bar_idx_empty + 8 * s, kGather);
         }
         mbar_init(bar_final, 1);
         *abort_flag = 0;
@@ -383,53 +339,43 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const uint32_t sweep = (uint32_t)a.ctl->sweep;
     constexpr int64_t kChunkRatings = (int64_t)kChunkStages * kStageRatings;
 
-    // ======================= gather (warps 2-3 and the extra gather warps) ==========
+    // ======================= gather (warps 2-3, 12-13) =======================
     // gt: this thread's index among the kGather gather threads
-    constexpr int kGatherN = Shape::kGather;
-    constexpr int kRps = kGatherN / 16, kRpsB = kGatherN / 8;  // ratings per copy round
-    constexpr int kCopies = kBf16 ? 512 / kGatherN : 1024 / kGatherN;
+    constexpr int kRps = kGather / 16, kRpsB = kGather / 8;  // ratings per copy round
+    constexpr int kCopies = kBf16 ? 512 / kGather : 1024 / kGather;
     auto gather_role = [&](const int gt) {
         uint32_t g = 0;
         bool ok = true;
         for (int64_t j = 0; j < nj && ok; ++j) {
             const int rs = (int)(j % kRowRing);
-            if (!wait_bounded(bar_row_full + 8 * rs, (uint32_t)((j / kRowRing) & 1), wc)) break;
+            if (!wait_bounded<true>(bar_row_full + 8 * rs, (uint32_t)((j / kRowRing) & 1), wc)) break;
             const int64_t p0 = row_ring[4 * rs + 1], p1 = row_ring[4 * rs + 2];
             for (int64_t base = p0; base < p1; base += kStageRatings, ++g) {
                 const uint32_t is = g % kIdxRing, s = g % kNStage;
-                if (!wait_bounded(bar_idx_full + 8 * is, (g / kIdxRing) & 1u, wc) ||
-                    !wait_bounded(bar_stage_empty + 8 * s, ((g / kNStage) & 1u) ^ 1u, wc)) {
+                if (!wait_bounded<true>(bar_idx_full + 8 * is, (g / kIdxRing) & 1u, wc) ||
+                    !wait_bounded<true>(bar_stage_empty + 8 * s, ((g / kNStage) & 1u) ^ 1u, wc)) {
                     ok = false;
                     break;
                 }
                 const int cnt = (int)min((int64_t)kStageRatings, p1 - base);
                 // this thread's rows (-1 past the row's end), read before the slot is
                 // released: FP16 split, rating (gt >> 4) + kRps k, 16-B chunk gt & 15 of
-                // its h and l rows; BF16, rating (gt >> 3) + kRpsB k, chunk gt & 7 of its
-                // h row (kRps = gather threads / 16 ratings per round)
+                // its l and h rows; BF16, rating (gt >> 3) + kRpsB k, chunk gt & 7 of its
+                // h row
                 int cols[kCopies];
-                if constexpr (!kBf16) {
 #pragma unroll
-                    for (int k = 0; k < kCopies; ++k) {
-                        const int qq = (gt >> 4) + kRps * k;
-                        cols[k] = qq < cnt ? idx_ring[is * 128 + qq] : -1;
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < kCopies; ++k) {
-                        const int qq = (gt >> 3) + kRpsB * k;
-                        cols[k] = qq < cnt ? idx_ring[is * 128 + qq] : -1;
-                    }
+                for (int k = 0; k < kCopies; ++k) {
+                    const int qq = kBf16 ? (gt >> 3) + kRpsB * k : (gt >> 4) + kRps * k;
+                    cols[k] = qq < cnt ? idx_ring[is * 128 + qq] : -1;
                 }
                 // the first 64 threads also carry the stage's 64 rating values
                 const float rv = gt < 64 && gt < cnt ? val_ring[is * 128 + gt] : 0.f;
                 mbar_arrive(bar_idx_empty + 8 * is);
-                const uint32_t sH = sbase + kOffStages + s * kStageBytes;
-                const uint32_t sL = sH + kTileBytes;
-                const uint32_t sR = sL + kTileBytes;
+                const uint32_t sL = sbase + kOffStages + s * kStageBytes;
+                const uint32_t sH = sL + kTileBytes;
+                const uint32_t sR = sH + kTileBytes;
                 if constexpr (!kBf16) {
                     const int c = gt & 15, ch = c & 7;
                     const __half* Ysrc = (c >> 3) ? a.Yl : a.Yh;
@@ -472,32 +418,40 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
         cp_async_wait_all();
     };
 
-    if (warp < 4) {
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(Shape::kProdRegs) : "memory");
+    if (warp < 4 || warp >= 12) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kProdRegs) : "memory");
         if (warp == 0) {
             // ======================= MMA issuer =======================
             if (lane == 0) {
                 constexpr uint32_t idesc = kBf16 ? kIdescBf16 : kIdesc;
-                uint32_t g = 0, u = 0;  // stages consumed, accumulation chunks issued
+                // stage ring position and phase kept as counters (no division in the loop)
+                uint32_t st = 0, st_phase = 0;
+                uint32_t uc0 = 0, uc1 = 0;  // accumulation chunks issued per drain group
+                const uint32_t stage0 = sbase + kOffStages;
+                const uint64_t adesc0 = sdesc(stage0, kTileBytes, 1024, 2);
+                const uint64_t bdesc0 = sdesc(stage0 + kTileBytes, kTileBytes, 1024, 2);
                 bool ok = true;
                 for (int64_t j = 0; j < nj && ok; ++j) {
                     const int rs = (int)(j % kRowRing);
                     if (!wait_bounded(bar_row_full + 8 * rs, (uint32_t)((j / kRowRing) & 1), wc)) break;
-                    const int64_t p0 = row_ring[4 * rs + 1], p1 = row_ring[4 * rs + 2];
+                    const int64_t p0 = row_ring[4 * rs + 1];
+                    const int32_t n = (int32_t)(row_ring[4 * rs + 2] - p0);  // ratings of the row
+                    const int grp = (int)(j & 1);
                     // a long row is summed in chunks of kChunkStages stages, each in a
-                    // fresh TMEM accumulator that the drain adds into the row's buffer
-                    for (int64_t c0 = p0; c0 < p1 && ok; c0 += kChunkRatings, ++u) {
-                        const uint32_t slot = u % kNAcc;
-                        if (!wait_bounded(bar_acc_empty + 8 * slot, ((u / kNAcc) & 1u) ^ 1u, wc)) {
+                    // fresh accumulator of the row's drain group
+                    for (int32_t c0 = 0; c0 < n && ok; c0 += (int32_t)kChunkRatings) {
+                        const uint32_t u = grp ? uc1++ : uc0++;
+                        const uint32_t slot = grp * kSlotsPerGroup + u % kSlotsPerGroup;
+                        if (!wait_bounded(bar_acc_empty + 8 * slot,
+                                          ((u / kSlotsPerGroup) & 1u) ^ 1u, wc)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
                         const uint32_t dgram = tmem_base + slot * kAccStride;
-                        const int64_t c1 = min(p1, c0 + kChunkRatings);
-                        for (int64_t base = c0; base < c1; base += kStageRatings, ++g) {
-                            const uint32_t s = g % kNStage;
-                            if (!wait_bounded(bar_stage_full + 8 * s, (g / kNStage) & 1u, wc)) {
+                        const int32_t c1 = min(n, c0 + (int32_t)kChunkRatings);
+                        for (int32_t base = c0; base < c1; base += kStageRatings) {
+                            if (!wait_bounded(bar_stage_full + 8 * st, st_phase, wc)) {
                                 ok = false;
                                 break;
                             }
@@ -505,18 +459,21 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
                             // stores) and is read by the tensor core through the async proxy
                             fence_proxy_async();
                             tc_fence_after();
-                            const int cnt = (int)min((int64_t)kStageRatings, p1 - base);
-                            const uint32_t sH = sbase + kOffStages + s * kStageBytes;
-                            for (int kb = 0; kb < (cnt + 15) / 16; ++kb) {
-                                // A = [H^T; L^T] (M = 128: atoms 0, 1), B = [H | L | R]
-                                // (N = 144: atoms 0, 1 and the first 16 columns of 2):
-                                // one descriptor, atoms kTileBytes apart, 16 ratings
-                                // (16 x 128 B rows) per k-block
-                                const uint64_t desc = sdesc(sH + kb * 2048, kTileBytes, 1024, 2);
-                                const uint32_t acc = (base > c0 || kb > 0) ? 1u : 0u;
-                                tc_mma(dgram, desc, desc, idesc, acc);
+                            // A = [L^T; H^T] (M = 128: the l and h atoms), B = [H | R]
+                            // (N = 80: the h atom and the ratings atom's first 16
+                            // columns); 16 ratings (16 x 128-B rows) per k-block, a k-block
+                            // 2048 B further (128 in the descriptor's address field)
+                            const uint64_t soff = (uint64_t)((st * kStageBytes) >> 4);
+                            const int nkb = (min(kStageRatings, c1 - base) + 15) >> 4;
+                            const uint32_t acc0 = base > c0 ? 1u : 0u;
+                            tc_mma(dgram, adesc0 + soff, bdesc0 + soff, idesc, acc0);
+                            for (int kb = 1; kb < nkb; ++kb)
+                                tc_mma(dgram, adesc0 + soff + 128 * kb, bdesc0 + soff + 128 * kb, idesc, 1u);
+                            tc_commit(bar_stage_empty + 8 * st);
+                            if (++st == kNStage) {
+                                st = 0;
+                                st_phase ^= 1u;
                             }
-                            tc_commit(bar_stage_empty + 8 * s);
                         }
                         if (ok) tc_commit(bar_acc_full + 8 * slot);
                     }
@@ -536,9 +493,10 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
                 // descriptors of the next 32 rows, one row per lane (independent loads)
                 const int64_t jj = j0 + lane;
                 int my_row = -1;
-                long long my_p0 = 0, my_p1 = 0;
+                long long my_p0 = 0, my_p1 = 0, my_slot = 0;
                 if (jj < nj) {
-                    my_row = __ldg(a.rows + (planned ? first + jj : blockIdx.x + jj * G));
+                    my_slot = planned ? first + jj : blockIdx.x + jj * G;
+                    my_row = __ldg(a.rows + my_slot);
                     my_p0 = __ldg(a.ptr + my_row);
                     my_p1 = __ldg(a.ptr + my_row + 1);
                 }
@@ -548,8 +506,9 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
                     const int row = __shfl_sync(kFullMask, my_row, r);
                     const long long p0 = __shfl_sync(kFullMask, my_p0, r);
                     const long long p1 = __shfl_sync(kFullMask, my_p1, r);
+                    const long long slot = __shfl_sync(kFullMask, my_slot, r);
                     const int rs = (int)(j % kRowRing);
-                    bool w = wait_bounded(bar_row_empty + 8 * rs, (uint32_t)((j / kRowRing) & 1) ^ 1u, wc);
+                    bool w = wait_bounded<true>(bar_row_empty + 8 * rs, (uint32_t)((j / kRowRing) & 1) ^ 1u, wc);
                     if (!__all_sync(kFullMask, w)) {
                         ok = false;
                         break;
@@ -558,11 +517,12 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
                         row_ring[4 * rs + 0] = row;
                         row_ring[4 * rs + 1] = p0;
                         row_ring[4 * rs + 2] = p1;
+                        row_ring[4 * rs + 3] = slot;
                         mbar_arrive(bar_row_full + 8 * rs);
                     }
                     for (long long base = p0; base < p1; base += kStageRatings, ++g) {
                         const uint32_t is = g % kIdxRing;
-                        w = wait_bounded(bar_idx_empty + 8 * is, ((g / kIdxRing) & 1u) ^ 1u, wc);
+                        w = wait_bounded<true>(bar_idx_empty + 8 * is, ((g / kIdxRing) & 1u) ^ 1u, wc);
                         if (!__all_sync(kFullMask, w)) {
                             ok = false;
                             break;
@@ -578,105 +538,101 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
                 }
             }
             cp_async_wait_all();
-        } else {
-            gather_role(tid - 64);
+        } else if (warp < 14) {
+            gather_role(warp < 4 ? tid - 64 : 64 + tid - 384);
         }
-    } else if (warp < 8) {
-        // ======================= TMEM drain =======================
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(Shape::kDrainRegs) : "memory");
-        const int quarter = warp & 3;
-        const int m = 32 * (quarter & 1) + lane;  // row of Lambda this thread serves
+    } else {
+        // ======================= TMEM drain (warps 4-7: group 0, 8-11: group 1) ===========
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kDrainRegs) : "memory");
+        const int grp = (warp - 4) >> 2;
+        const int q = warp & 3;       // TMEM lane quarter: lanes 32q .. 32q + 31
+        const bool hh = q >= 2;       // H^T [H | R] rows (else L^T [H | R] rows)
+        const int m = 32 * (q & 1) + lane;  // row of the Gram this thread serves
+        const uint32_t bar_id = 1 + grp;
+        float* T = staging + grp * kStagingFloats;
         const float alpha = a.alpha;
-        uint32_t u = 0;  // accumulation chunks drained
-        bool live = true;
-        for (int64_t j = 0; j < nj && live; ++j) {
+        uint32_t u = 0;  // accumulation chunks drained by this group
+        for (int64_t j = grp; j < nj; j += kGroups) {
             const int rs = (int)(j % kRowRing);
-            const int b = (int)(j % kNChol);
-            bool ok = wait_bounded(bar_row_full + 8 * rs, (uint32_t)((j / kRowRing) & 1), wc);
-            if (bar_any(1, 128, !ok || *abort_flag != 0)) {
+            bool ok = wait_bounded<true>(bar_row_full + 8 * rs, (uint32_t)((j / kRowRing) & 1), wc);
+            if (bar_any(bar_id, 128, !ok || *abort_flag != 0)) {
                 *abort_flag = 1;
                 break;
             }
             const int64_t p0 = row_ring[4 * rs + 1], p1 = row_ring[4 * rs + 2];
-            float* L = lam_bufs + b * kLamFloats;
+            const int64_t slot_out = row_ring[4 * rs + 3];
+            float acc[64];
+#pragma unroll
+            for (int i = 0; i < 64; ++i) acc[i] = 0.f;
             float rsum = 0.f;
+            bool live = true;
             for (int64_t c0 = p0; c0 < p1; c0 += kChunkRatings, ++u) {
-                const uint32_t slot = u % kNAcc;
-                const bool first = c0 == p0;
-                // wait outcomes are made uniform over the 128 drain threads before any
+                const uint32_t slot = grp * kSlotsPerGroup + u % kSlotsPerGroup;
+                // wait outcomes are made uniform over the group's 128 threads before any
                 // warp-collective (tcgen05.ld) or group barrier depends on them
-                ok = wait_bounded(bar_acc_full + 8 * slot, (u / kNAcc) & 1u, wc);
-                if (bar_any(1, 128, !ok)) {
+                ok = wait_bounded<true>(bar_acc_full + 8 * slot, (u / kSlotsPerGroup) & 1u, wc);
+                if (bar_any(bar_id, 128, !ok)) {
                     *abort_flag = 1;
                     live = false;
                     break;
                 }
-                if (first) {
-                    ok = wait_bounded(bar_lam_empty + 8 * b, (uint32_t)((j / kNChol) & 1) ^ 1u, wc);
-                    if (bar_any(1, 128, !ok)) {
-                        *abort_flag = 1;
-                        live = false;
-                        break;
+                tc_fence_after();
+                const uint32_t taddr = tmem_base + ((uint32_t)(32 * q) << 16) + slot * kAccStride;
+                // H^T H rows below 32 need columns 0..31 only (their lower triangle); the
+                // L^T H rows need all 64 (their transpose fills the H^T H rows' triangle)
+                const int ngroups = (hh && (q & 1) == 0) ? 1 : 2;
+#pragma unroll
+                for (int hgrp = 0; hgrp < 2; ++hgrp) {
+                    if (hgrp < ngroups) {  // warp-uniform
+                        uint32_t v0[16], v1[16];
+                        TMEM_LD16(taddr + 32 * hgrp, v0);
+                        TMEM_LD16(taddr + 32 * hgrp + 16, v1);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            acc[32 * hgrp + i] += __uint_as_float(v0[i]);
+                            acc[32 * hgrp + 16 + i] += __uint_as_float(v1[i]);
+                        }
                     }
                 }
-                tc_fence_after();
-                const uint32_t taddr = tmem_base + ((uint32_t)(32 * quarter) << 16) + slot * kAccStride;
-                // The accumulator holds H^T (H + L) in its top 64 lanes and L^T (H + L) in
-                // its bottom 64; their sum is the chunk's Gram (H + L is the FP16 split of
-                // the other side's rows).  Both halves add into the row's buffer, which
-                // starts from the prior precision, the bottom first; only chunks on or
-                // below the diagonal are formed.
                 uint32_t r0, r1;
-                tmem_ld2(taddr + 128, r0, r1);
-                if (quarter >= 2) drain_rows(taddr, L, m, quarter, alpha);
-                named_bar(1, 128);
-                if (quarter < 2) drain_rows(taddr, L, m, quarter, alpha);
+                tmem_ld2(taddr + 64, r0, r1);
                 tmem_wait_ld();
+                rsum += __uint_as_float(r0) + __uint_as_float(r1);
                 tc_fence_before();
                 mbar_arrive(bar_acc_empty + 8 * slot);
-                rsum += __uint_as_float(r0) + __uint_as_float(r1);
-                named_bar(1, 128);
             }
             if (!live) break;
-            if (quarter >= 2) rtmp[m] = rsum;
-            named_bar(1, 128);
-            if (quarter < 2) L[4096 + m] = fmaf(alpha, rsum + rtmp[m], __ldg(a.lammu + m));
-            mbar_arrive(bar_lam_full + 8 * b);
-            named_bar(1, 128);  // rtmp is reused by the next row
+            // ---- the row's end: L^T H rows to the staging buffer, then each H^T H row
+            // m adds (L^T H)[m][c] + (L^T H)[c][m] over its lower triangle
+            if (!hh) {
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    *chunk_ptr(T, m, c) = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+                T[4096 + m] = rsum;
+            }
+            named_bar(bar_id, 128);
+            if (hh) {
+                float4* out = reinterpret_cast<float4*>(a.gram + slot_out * kGramSlotFloats);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    if (4 * c <= m) {
+                        const float4 t = ld_chunk(T, m, c);
+                        const float4 px = prior4[gram_chunk_offset(c) + m - 4 * c];
+                        float4 o;
+                        o.x = fmaf(alpha, acc[4 * c + 0] + t.x + T[sw64(4 * c + 0, m)], px.x);
+                        o.y = fmaf(alpha, acc[4 * c + 1] + t.y + T[sw64(4 * c + 1, m)], px.y);
+                        o.z = fmaf(alpha, acc[4 * c + 2] + t.z + T[sw64(4 * c + 2, m)], px.z);
+                        o.w = fmaf(alpha, acc[4 * c + 3] + t.w + T[sw64(4 * c + 3, m)], px.w);
+                        out[gram_chunk_offset(c) + m - 4 * c] = o;
+                    }
+                }
+                reinterpret_cast<float*>(out)[4 * kGramChunks + m] =
+                    fmaf(alpha, rsum + T[4096 + m], prior_mu[m]);
+            }
+            named_bar(bar_id, 128);  // the staging buffer is reused by the group's next row
+            if (q == 0 && lane == 0) mbar_arrive(bar_row_empty + 8 * rs);
         }
-    } else if (warp < Shape::kCholWarp0) {
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(Shape::kProdRegs) : "memory");
-        gather_role(64 + tid - 256);
-    } else {
-        // ======================= Cholesky, solve, sample =======================
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(Shape::kCholRegs) : "memory");
-        const int cw = warp - Shape::kCholWarp0;
-        float* scratch = chol_scratch + cw * kCholScratchFloats;
-        float* colbuf = scratch;
-        float* dinv = scratch + 128;
-        float* zb = scratch + 192;
-        bool bad = false;
-        for (int64_t j = cw; j < nj; j += kNChol) {
-            if (__any_sync(kFullMask, *abort_flag != 0)) break;  // warp-uniform
-            const bool ok = wait_bounded(bar_lam_full + 8 * cw, (uint32_t)((j / kNChol) & 1), wc);
-            if (!__all_sync(kFullMask, ok)) break;
-            // the row descriptor was published before this row's stages existed
-            const int rs = (int)(j % kRowRing);
-            const int row = (int)row_ring[4 * rs + 0];
-            float* L = lam_bufs + cw * kLamFloats;
-            float x1, x2, m1, m2;
-            factor_solve_sample_rl64(L, L + 4096, colbuf, dinv, zb, lane, a.K, a.seed, (uint32_t)row,
-                                     sweep, a.c3, a.means != nullptr, x1, x2, m1, m2, bad);
-            store_row_panels(a, row, lane, x1, x2, m1, m2);
-            __syncwarp();  // every lane is done reading L
-            // the buffer goes back holding the prior precision, which the drain
-            // accumulates into
-            fill_lower_sw64(L, reinterpret_cast<const float4*>(a.lam_ct), lane, 32);
-            __syncwarp();
-            mbar_arrive(bar_lam_empty + 8 * cw);
-            if (lane == 0) mbar_arrive(bar_row_empty + 8 * rs);
-        }
-        if (bad && lane == 0) atomicOr(&a.ctl->status, kStatusNotPD);
     }
 
     tc_fence_before();
@@ -689,38 +645,31 @@ __global__ void __launch_bounds__(Shape::kThreads, 1) rows_tc_kernel(RowArgs a)
     }
 }
 
-template <class Shape, bool kBf16>
-cudaError_t launch_shape(const RowArgs& a, int num_sms, cudaStream_t s)
+template <bool kBf16>
+static cudaError_t launch_gram(const RowArgs& a, int num_sms, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(rows_tc_kernel<Shape, kBf16>,
+    cudaError_t e = cudaFuncSetAttribute(rows_gram_kernel<kBf16>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Shape::kSmemBytes);
+                                         (int)kSmemBytes);
     if (e != cudaSuccess) return e;
     // setmaxnreg.inc takes registers that other warps released from what the CTA was
     // launched with (the compiled count times the threads): if the split's total were
-    // above that, the Cholesky warps' increase would never be granted.  Refuse the
-    // launch instead (the compiled count can sit below the launch bound).
+    // above that, the drain warps' increase would never be granted.  Refuse the launch
+    // instead (the compiled count can sit below the launch bound).
     cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, rows_tc_kernel<Shape, kBf16>);
+    e = cudaFuncGetAttributes(&fa, rows_gram_kernel<kBf16>);
     if (e != cudaSuccess) return e;
-    const long split = 32L * ((4 + Shape::kCholWarp0 - 8) * Shape::kProdRegs +
-                              4 * Shape::kDrainRegs + Shape::kNChol * Shape::kCholRegs);
-    if (split > (long)fa.numRegs * Shape::kThreads) return cudaErrorInvalidConfiguration;
-    int64_t grid = a.nrows < num_sms ? a.nrows : num_sms;
-    rows_tc_kernel<Shape, kBf16><<<(unsigned)grid, Shape::kThreads, Shape::kSmemBytes, s>>>(a);
+    const long split = 32L * (8 * kProdRegs + 8 * kDrainRegs);
+    if (split > (long)fa.numRegs * kThreads) return cudaErrorInvalidConfiguration;
+    const int64_t grid = a.nrows < num_sms ? a.nrows : num_sms;
+    rows_gram_kernel<kBf16><<<(unsigned)grid, kThreads, kSmemBytes, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_rows_tc(const RowArgs& a, int64_t nratings, int64_t shape_degree, int num_sms,
-                           cudaStream_t s)
+cudaError_t launch_rows_gram(const RowArgs& a, int num_sms, cudaStream_t s)
 {
     if (a.nrows <= 0) return cudaSuccess;
-    const bool longrows = nratings >= shape_degree * a.nrows;
-    if (a.bf16)
-        return longrows ? launch_shape<ShapeLongRowsBf16, true>(a, num_sms, s)
-                        : launch_shape<ShapeShortRows, true>(a, num_sms, s);
-    return longrows ? launch_shape<ShapeLongRows, false>(a, num_sms, s)
-                    : launch_shape<ShapeShortRows, false>(a, num_sms, s);
+    return a.bf16 ? launch_gram<true>(a, num_sms, s) : launch_gram<false>(a, num_sms, s);
 }
 
 __global__ void split_factors_kernel(const float* __restrict__ X, int64_t n, __half* __restrict__ Xh,

@@ -411,27 +411,15 @@ __device__ __forceinline__ void chol_shifted_steps(float (&a1)[32], float (&a2)[
     }
 }
 
-// Lower-triangle chunks (4c <= i) of a sw64 matrix set from a chunk-transposed copy
-// in global memory (float4 (i, 4c..4c+3) at c * 64 + i) by `nthreads` threads:
-// consecutive threads take consecutive rows, so the loads coalesce and the stores
-// are conflict-free.
-__device__ __forceinline__ void fill_lower_sw64(float* M, const float4* src_ct, int t, int nthreads)
-{
-#pragma unroll 4
-    for (int e = t; e < 1024; e += nthreads) {
-        const int i = e & 63, c = e >> 6;
-        if (4 * c <= i) *chunk_ptr(M, i, c) = __ldg(src_ct + c * 64 + i);
-    }
-}
-
-// Factor / solve / sample for K = 64: Lambda_i in shared memory (sw64 layout, lower
-// triangle valid, the rest scratch; overwritten with the strictly lower part of L,
-// transposed), b_i in bv.  Lane l owns
-// rows r1 = l and r2 = 32 + l; the factorization runs in four spans of 16 columns
-// so the register rows shrink as they finish (eight spans of 8 cut the FMAs by a
-// tenth but, as more code beside the kernel's other roles, ran slower in the kernel),
-// then x = L^{-T}(y + z).
-__device__ __forceinline__ void factor_solve_sample_rl64(float* M, const float* bv, float* cbuf,
+// Factor / solve / sample for K = 64.  Lane l holds rows r1 = l (a1: columns 0..31)
+// and r2 = 32 + l (a2: columns 0..63) of Lambda_i in registers -- entries above the
+// diagonal are never used -- and its entries b1 = b_i[r1], b2 = b_i[r2].  M is the
+// warp's 64 x 64 buffer in the sw64 layout; it receives the strictly lower part of
+// L, transposed, for the back solve (its previous contents are ignored).  The
+// factorisation runs in four spans of 16 columns so the register rows shrink as
+// they finish, then x = L^{-T}(y + z).
+__device__ __forceinline__ void factor_solve_sample_rl64(float (&a1)[32], float (&a2)[64], float b1,
+                                                         float b2, float* M, float* cbuf,
                                                          float* dinv, float* zb, int lane, int K,
                                                          uint64_t seed, uint32_t row,
                                                          uint32_t sweep, uint32_t c3,
@@ -439,20 +427,6 @@ __device__ __forceinline__ void factor_solve_sample_rl64(float* M, const float* 
                                                          float& m1, float& m2, bool& bad)
 {
     const int r1 = lane, r2 = 32 + lane;
-    float a1[32], a2[64];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const float4 u = ld_chunk(M, r1, c);
-        a1[4 * c + 0] = u.x; a1[4 * c + 1] = u.y; a1[4 * c + 2] = u.z; a1[4 * c + 3] = u.w;
-    }
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-        const float4 v = ld_chunk(M, r2, c);
-        a2[4 * c + 0] = v.x; a2[4 * c + 1] = v.y; a2[4 * c + 2] = v.z; a2[4 * c + 3] = v.w;
-    }
-    float b1 = bv[r1];
-    float b2 = bv[r2];
-    __syncwarp();  // every lane has its rows before L overwrites them
     float l1, l2;
     chol_pivot<true>(0, a1[0], a2[0], b1, b2, l1, l2, M, cbuf, dinv, lane, bad);
     chol_shifted_steps<32, 64>(a1, a2, b1, b2, l1, l2, 0, 16, M, cbuf, dinv, lane, bad);

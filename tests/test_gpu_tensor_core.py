@@ -160,21 +160,22 @@ def test_full_size_config3_sampled_rows(bp, config3):
 
 def test_row_launch_timing(bp):
     # users below the tensor-core threshold on the CUDA-core kernel, the rest on the
-    # tensor-core kernel: both parts timed by the library's events when on, -1 when off
+    # tensor-core route (Gram kernel, then factorisation kernel): every part timed by
+    # the library's events when on, -1 when off
     prob = workloads.random_small(400, 200, 64, 20000, seed=61)
     deg = np.diff(prob.csr_ptr)
     assert (deg < 48).sum() > 0 and (deg >= 48).sum() > 0
     h = bp.create_from_problem(prob, stream=bp.torch_stream())
     try:
-        assert bp.bpmf_row_launch_ms(h) == (-1.0, -1.0)
+        assert bp.bpmf_row_launch_ms(h) == (-1.0, -1.0, -1.0)
         bp.bpmf_set_row_timing(h, True)
         bp.bpmf_step(h, bp.BPMF_PHASE_ROWS_USER)
-        cc, tc = bp.bpmf_row_launch_ms(h)
-        assert cc > 0 and tc > 0
+        cc, gram, chol = bp.bpmf_row_launch_ms(h)
+        assert cc > 0 and gram > 0 and chol > 0
         bp.bpmf_sweep(h, 2)  # sweeps record nothing: the last timed phase stays
-        assert bp.bpmf_row_launch_ms(h) == (cc, tc)
+        assert bp.bpmf_row_launch_ms(h) == (cc, gram, chol)
         bp.bpmf_set_row_timing(h, False)
-        assert bp.bpmf_row_launch_ms(h) == (-1.0, -1.0)
+        assert bp.bpmf_row_launch_ms(h) == (-1.0, -1.0, -1.0)
         assert bp.bpmf_status(h) == 0
     finally:
         bp.bpmf_destroy(h)
