@@ -412,14 +412,15 @@ int plan_long_bin(bpmf_ctx* h, DevSide& d, const std::vector<int32_t>& order)
     std::vector<int32_t> pos, plan((size_t)n);
     std::vector<int64_t> first;
     for (int q = 0; q < 2; ++q) {
-        const int64_t G = std::min<int64_t>(n, h->num_sms - q);
+        const int64_t G = std::min<int64_t>(n, (int64_t)kGramCtasPerSm * (h->num_sms - q));
         if (!balance_plan(cost, G, pos, first)) continue;
         for (int64_t p = 0; p < n; ++p) plan[(size_t)p] = order[(size_t)(d.n_short + pos[(size_t)p])];
         if (n > d.plan_cap[q]) {
             if (!alloc_n(h, &d.plan_rows[q], (size_t)n)) return BPMF_ENOMEM;
             d.plan_cap[q] = n;
         }
-        if (!d.plan_first[q] && !alloc_n(h, &d.plan_first[q], (size_t)h->num_sms + 1))
+        // CTA offsets for the largest grid a Gram launch can have
+        if (!d.plan_first[q] && !alloc_n(h, &d.plan_first[q], (size_t)kGramCtasPerSm * h->num_sms + 1))
             return BPMF_ENOMEM;
         cudaError_t e = cudaMemcpyAsync(d.plan_rows[q], plan.data(), sizeof(int32_t) * n,
                                         cudaMemcpyHostToDevice, h->stream);
@@ -568,7 +569,7 @@ int phase_rows(bpmf_ctx* h, int s, bool timed = false)
     a.nsegs = a.nsplit = a.nrank_one = 0;
     a.rows = d.bin_rows + d.n_short;
     a.nrows = d.n_long;
-    const int64_t grid = std::min<int64_t>(d.n_long, h->row_sms);  // the launch's CTAs
+    const int64_t grid = std::min<int64_t>(d.n_long, (int64_t)kGramCtasPerSm * h->row_sms);  // the Gram launch's CTAs
     for (int q = 0; q < 2; ++q)
         if (d.plan_grid[q] > 0 && d.plan_grid[q] == grid) {
             a.rows = d.plan_rows[q];

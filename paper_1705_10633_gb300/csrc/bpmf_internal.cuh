@@ -176,6 +176,9 @@ constexpr int kGramChunks = 544;
 constexpr int kGramSlotFloats = 4 * kGramChunks + 64;
 __host__ __device__ constexpr int gram_chunk_offset(int c) { return c * (66 - 2 * c); }
 // Gram kernel (A3 on tensor cores): Lambda_i and b_i of the rows in a.rows into a.gram.
+// It runs kGramCtasPerSm persistent CTAs per SM (grid = that many times num_sms, at
+// most one CTA per row); a balanced plan of the rows must be made for that grid.
+constexpr int kGramCtasPerSm = 2;
 cudaError_t launch_rows_gram(const RowArgs& a, int num_sms, cudaStream_t s);
 // Factorisation kernel (A4, A5): reads a.gram, writes the rows' new factors.
 cudaError_t launch_rows_chol(const RowArgs& a, int num_sms, cudaStream_t s);

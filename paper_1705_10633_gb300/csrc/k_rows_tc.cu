@@ -19,27 +19,26 @@
 // of this kernel leaves the SM's issue slots and shared memory to the gather and
 // the tensor core, and the factorisation kernel runs with every warp of the SM.
 //
-// One CTA per SM, persistent over the rows (dealt round-robin, or by the host's
-// balanced plan where round-robin would be uneven).  Warp roles (16 warps):
-//   warp 0        MMA issuer (one lane) and TMEM owner (4 accumulators)
+// Two CTAs per SM (each with half of the SM's TMEM and shared memory), persistent
+// over the rows (dealt round-robin, or by the host's balanced plan where round-robin
+// would be uneven).  Each CTA is one pipeline; two of them keep the tensor core busy
+// while one MMA issuer waits for a stage or commits.  Warp roles (8 warps):
+//   warp 0        MMA issuer (one lane) and TMEM owner (2 accumulators)
 //   warp 1        prefetch: row descriptors (row, first, last rating, slot) into a
 //                 ring, and every stage's rating indices and values into a second
 //                 ring, far ahead of use (cp.async, mbarrier completion)
-//   warps 2-3, 12-13   gather: cp.async of the 128-B h and l rows of each rating
-//                 into the swizzled atoms; the stage barrier completes when they land
-//   warps 4-7     drain group 0 (rows 0, 2, 4, ... of the CTA), warps 8-11 drain
-//                 group 1 (rows 1, 3, ...): TMEM -> registers, summed over the row's
-//                 accumulation chunks; at the row's end the L^T H rows go through a
-//                 shared staging buffer so the H^T H rows can add L^T H and its
-//                 transpose, add Lambda_X and store the packed lower triangle
-//   warps 14-15   idle (they give their registers to the drain warps)
+//   warps 2-3     gather: cp.async of the 128-B h and l rows of each rating into the
+//                 swizzled atoms; the stage barrier completes when they land
+//   warps 4-7     drain (TMEM lane quarters 0-3): TMEM -> registers, summed over the
+//                 row's accumulation chunks; at the row's end the L^T H rows go
+//                 through a shared staging buffer so the H^T H rows can add L^T H and
+//                 its transpose, add Lambda_X and store the packed lower triangle
 // Stages of 64 ratings flow producer -> MMA through mbarriers; accumulators MMA ->
-// drain (two per drain group).  A long row is accumulated in chunks of 16 stages,
-// each in a fresh accumulator that the drain adds into its registers: the tensor
-// core's accumulation rounding grows with the chunk length only, not with the row's
-// degree (rows here reach 2.7e5 ratings).  Every wait is bounded in time; a timeout
-// sets a status bit, the CTA stops its loops, waits for its own copies and MMAs,
-// frees TMEM and exits.
+// drain.  A long row is accumulated in chunks of 16 stages, each in a fresh
+// accumulator that the drain adds into its registers: the tensor core's accumulation
+// rounding grows with the chunk length only, not with the row's degree (rows here
+// reach 2.7e5 ratings).  Every wait is bounded in time; a timeout sets a status bit,
+// the CTA stops its loops, waits for its own copies and MMAs, frees TMEM and exits.
 #include "bpmf_internal.cuh"
 #include "philox.cuh"
 #include "rows_common.cuh"
@@ -52,19 +51,19 @@ constexpr int kStageRatings = 64;
 constexpr int kChunkStages = 16;   // stages per TMEM accumulation before it is drained
 constexpr int kRowRing = 32;       // row descriptors in flight
 constexpr int kIdxRing = 8;        // stages of rating indices / values in flight
-constexpr int kGroups = 2;         // drain groups; rows alternate between them
+constexpr int kGroups = 1;         // drain groups of a CTA
 constexpr int kSlotsPerGroup = 2;  // TMEM accumulators per drain group
 constexpr int kNumAcc = kGroups * kSlotsPerGroup;
-constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kTmemCols = 256;  // half of the SM's TMEM: two CTAs share an SM
 constexpr uint32_t kAccStride = 128;  // 80 columns used
 constexpr int kN = 80;                // MMA N: 64 h columns + the ratings atom's first 16
 
 constexpr uint32_t kTileBytes = kStageRatings * 128;  // one atom: 64 ratings x 64 halves
 constexpr uint32_t kStageBytes = 3 * kTileBytes;      // l, h, ratings (24 KB)
-constexpr int kNStage = 7;
-constexpr int kGatherWarps = 4;
+constexpr int kNStage = 3;
+constexpr int kGatherWarps = 2;
 constexpr int kGather = 32 * kGatherWarps;
-constexpr int kWarps = 16;
+constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr uint32_t kStagingFloats = 64 * 64 + 64;  // L^T H rows (sw64 layout) and L^T r
 
@@ -77,16 +76,16 @@ constexpr uint32_t kOffBars = kOffIdxRing + kIdxRing * 512;
 constexpr int kNumBars = 2 * kNStage + 2 * kNumAcc + 2 * kRowRing + 2 * kIdxRing + 1;
 constexpr uint32_t kOffMisc = kOffBars + kNumBars * 8;
 constexpr uint32_t kSmemBytes = kOffMisc + 16 + 1024;  // + alignment slack
-static_assert(kSmemBytes <= 232448, "shared memory");
+static_assert(kGramCtasPerSm * (kSmemBytes + 1024) <= 233472, "shared memory of the SM's CTAs");
 static_assert(kNumAcc * kAccStride <= kTmemCols, "TMEM columns");
-// Registers: the launch gives 128 a thread.  Each SM sub-partition holds warps w, w + 4,
-// w + 8, w + 12 -- one producer or idle warp, two drain warps and one gather or idle
-// warp -- and setmaxnreg moves registers within it: producer, gather and idle warps
-// drop to kProdRegs, drain warps rise to kDrainRegs.
+// Registers: the launch gives 128 a thread (two CTAs of 256 threads fill the register
+// file).  Each SM sub-partition holds one producer warp (MMA, prefetch or gather) and one
+// drain warp of the CTA, and setmaxnreg moves registers between them: producers drop to
+// kProdRegs, drain warps rise to kDrainRegs.
 constexpr int kLaunchRegs = 128;
 constexpr int kProdRegs = 80;
 constexpr int kDrainRegs = 176;
-static_assert(2 * kProdRegs + 2 * kDrainRegs <= 4 * kLaunchRegs, "registers per sub-partition");
+static_assert(kProdRegs + kDrainRegs <= 2 * kLaunchRegs, "registers per sub-partition");
 
 // Instruction descriptor of kind::f16: D = F32, A = B = F16 (or BF16), both MN-major.
 constexpr uint32_t make_idesc(int M, int N)
@@ -250,7 +249,7 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 }  // namespace
 
 template <bool kBf16>
-__global__ void __launch_bounds__(kThreads, 1) rows_gram_kernel(RowArgs a)
+__global__ void __launch_bounds__(kThreads, kGramCtasPerSm) rows_gram_kernel(RowArgs a)
 {
     extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) &
@@ -341,7 +340,7 @@ __global__ void __launch_bounds__(kThreads, 1) rows_gram_kernel(RowArgs a)
     const uint32_t tmem_base = *tmem_slot;
     constexpr int64_t kChunkRatings = (int64_t)kChunkStages * kStageRatings;
 
-    // ======================= gather (warps 2-3, 12-13) =======================
+    // ======================= gather (warps 2-3) =======================
     // gt: this thread's index among the kGather gather threads
     constexpr int kRps = kGather / 16, kRpsB = kGather / 8;  // ratings per copy round
     constexpr int kCopies = kBf16 ? 512 / kGather : 1024 / kGather;
@@ -418,7 +417,7 @@ __global__ void __launch_bounds__(kThreads, 1) rows_gram_kernel(RowArgs a)
         cp_async_wait_all();
     };
 
-    if (warp < 4 || warp >= 12) {
+    if (warp < 4) {
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kProdRegs) : "memory");
         if (warp == 0) {
             // ======================= MMA issuer =======================
@@ -436,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1) rows_gram_kernel(RowArgs a)
                     if (!wait_bounded(bar_row_full + 8 * rs, (uint32_t)((j / kRowRing) & 1), wc)) break;
                     const int64_t p0 = row_ring[4 * rs + 1];
                     const int32_t n = (int32_t)(row_ring[4 * rs + 2] - p0);  // ratings of the row
-                    const int grp = (int)(j & 1);
+                    const int grp = (int)(j % kGroups);
                     // a long row is summed in chunks of kChunkStages stages, each in a
                     // fresh accumulator of the row's drain group
                     for (int32_t c0 = 0; c0 < n && ok; c0 += (int32_t)kChunkRatings) {
@@ -538,11 +537,11 @@ __global__ void __launch_bounds__(kThreads, 1) rows_gram_kernel(RowArgs a)
                 }
             }
             cp_async_wait_all();
-        } else if (warp < 14) {
-            gather_role(warp < 4 ? tid - 64 : 64 + tid - 384);
+        } else {
+            gather_role(tid - 64);
         }
     } else {
-        // ======================= TMEM drain (warps 4-7: group 0, 8-11: group 1) ===========
+        // ======================= TMEM drain (warps 4-7) =======================
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kDrainRegs) : "memory");
         const int grp = (warp - 4) >> 2;
         const int q = warp & 3;       // TMEM lane quarter: lanes 32q .. 32q + 31
@@ -659,9 +658,10 @@ static cudaError_t launch_gram(const RowArgs& a, int num_sms, cudaStream_t s)
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, rows_gram_kernel<kBf16>);
     if (e != cudaSuccess) return e;
-    const long split = 32L * (8 * kProdRegs + 8 * kDrainRegs);
+    const long split = 32L * (4 * kProdRegs + 4 * kDrainRegs);
     if (split > (long)fa.numRegs * kThreads) return cudaErrorInvalidConfiguration;
-    const int64_t grid = a.nrows < num_sms ? a.nrows : num_sms;
+    const int64_t ctas = (int64_t)kGramCtasPerSm * num_sms;
+    const int64_t grid = a.nrows < ctas ? a.nrows : ctas;
     rows_gram_kernel<kBf16><<<(unsigned)grid, kThreads, kSmemBytes, s>>>(a);
     return cudaGetLastError();
 }

@@ -15,6 +15,10 @@ from test_gpu_parity import ROW_TOL, assert_worst, full_size_sampled_rows, rowwi
 
 pytestmark = pytest.mark.gpu
 
+# CTAs per SM of the tensor-core Gram launch (its grid, and so the grids its balanced
+# plans are made for)
+GRAM_CTAS_PER_SM = 2
+
 
 @pytest.fixture(scope="module")
 def bp():
@@ -52,13 +56,13 @@ def test_long_row_shape_parity(bp):
 
 
 def test_balanced_row_plan_parity_and_identity(bp):
-    """Tensor-core rows dealt to the CTAs by the balanced plan (each row, longest first, to
-    the CTA with the least work so far).  2,000 users with ~60 ratings and 160 with ~1,060:
-    round-robin would give a few CTAs two of the long rows (the busiest 1.27x the mean), so
-    the user side gets a plan for both launch grids; the movie side (within 4%) keeps
-    round-robin.  Parity with the oracle, and bpmf_sweep (one SM left to the hyper steps)
-    bit-identical to phase-by-phase stepping (every SM): a row's result does not depend on
-    which CTA takes it."""
+    """Tensor-core rows dealt to the CTAs of the Gram launch by the balanced plan (each row,
+    longest first, to the CTA with the least work so far).  2,000 users with ~60 ratings and
+    160 with ~1,060: round-robin would give a few CTAs two of the long rows, so the user
+    side gets a plan for both launch grids; the movie side gets one exactly where
+    bpmf_balance_rows finds round-robin uneven for that grid.  Parity with the oracle, and
+    bpmf_sweep (one SM left to the hyper steps) bit-identical to phase-by-phase stepping
+    (every SM): a row's result does not depend on which CTA takes it."""
     import torch
     prob = workloads.random_small(2000, 1200, 64, 120000, seed=77, n_test=300, long_rows=160,
                                   long_deg=1000)
@@ -66,8 +70,15 @@ def test_balanced_row_plan_parity_and_identity(bp):
     a = bp.create_from_problem(prob, stream=sa.cuda_stream)
     b = bp.create_from_problem(prob, stream=sb.cuda_stream)
     try:
-        assert bp.bpmf_info(a, 0)["balanced"] == 3 and bp.bpmf_info(a, 1)["balanced"] == 0
-        assert bp.bpmf_info(a, 0)["n_long"] > 2 * torch.cuda.get_device_properties(0).multi_processor_count
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+        assert bp.bpmf_info(a, 0)["balanced"] == 3
+        assert bp.bpmf_info(a, 0)["n_long"] > GRAM_CTAS_PER_SM * nsm
+        # the movie side's long bin, longest first, against the two grids of a Gram launch
+        vdeg = np.sort(prob.col_degrees())[::-1]
+        vdeg = vdeg[:bp.bpmf_info(a, 1)["n_long"]].astype(np.int64)
+        want = sum(bit for bit, g in ((1, GRAM_CTAS_PER_SM * nsm), (2, GRAM_CTAS_PER_SM * (nsm - 1)))
+                   if bp.bpmf_balance_rows(vdeg, g) is not None)
+        assert bp.bpmf_info(a, 1)["balanced"] == want
         ra = bp.bpmf_sweep(a, 2)
         seq = (bp.BPMF_PHASE_HYPER_MOVIE, bp.BPMF_PHASE_ROWS_MOVIE, bp.BPMF_PHASE_HYPER_USER,
                bp.BPMF_PHASE_ROWS_USER, bp.BPMF_PHASE_PREDICT, bp.BPMF_PHASE_ADVANCE)
