@@ -416,7 +416,7 @@ __device__ __forceinline__ void chol_shifted_steps(float (&a1)[32], float (&a2)[
 // diagonal are never used -- and its entries b1 = b_i[r1], b2 = b_i[r2].  M is the
 // warp's 64 x 64 buffer in the sw64 layout; it receives the strictly lower part of
 // L, transposed, for the back solve (its previous contents are ignored).  The
-// factorisation runs in four spans of 16 columns so the register rows shrink as
+// factorisation runs in eight spans of 8 columns so the register rows shrink as
 // they finish, then x = L^{-T}(y + z).
 __device__ __forceinline__ void factor_solve_sample_rl64(float (&a1)[32], float (&a2)[64], float b1,
                                                          float b2, float* M, float* cbuf,
@@ -429,10 +429,14 @@ __device__ __forceinline__ void factor_solve_sample_rl64(float (&a1)[32], float 
     const int r1 = lane, r2 = 32 + lane;
     float l1, l2;
     chol_pivot<true>(0, a1[0], a2[0], b1, b2, l1, l2, M, cbuf, dinv, lane, bad);
-    chol_shifted_steps<32, 64>(a1, a2, b1, b2, l1, l2, 0, 16, M, cbuf, dinv, lane, bad);
-    chol_shifted_steps<16, 48>(a1, a2, b1, b2, l1, l2, 16, 32, M, cbuf, dinv, lane, bad);
-    chol_shifted_steps<0, 32>(a1, a2, b1, b2, l1, l2, 32, 48, M, cbuf, dinv, lane, bad);
-    chol_shifted_steps<0, 16>(a1, a2, b1, b2, l1, l2, 48, 64, M, cbuf, dinv, lane, bad);
+    chol_shifted_steps<32, 64>(a1, a2, b1, b2, l1, l2, 0, 8, M, cbuf, dinv, lane, bad);
+    chol_shifted_steps<24, 56>(a1, a2, b1, b2, l1, l2, 8, 16, M, cbuf, dinv, lane, bad);
+    chol_shifted_steps<16, 48>(a1, a2, b1, b2, l1, l2, 16, 24, M, cbuf, dinv, lane, bad);
+    chol_shifted_steps<8, 40>(a1, a2, b1, b2, l1, l2, 24, 32, M, cbuf, dinv, lane, bad);
+    chol_shifted_steps<0, 32>(a1, a2, b1, b2, l1, l2, 32, 40, M, cbuf, dinv, lane, bad);
+    chol_shifted_steps<0, 24>(a1, a2, b1, b2, l1, l2, 40, 48, M, cbuf, dinv, lane, bad);
+    chol_shifted_steps<0, 16>(a1, a2, b1, b2, l1, l2, 48, 56, M, cbuf, dinv, lane, bad);
+    chol_shifted_steps<0, 8>(a1, a2, b1, b2, l1, l2, 56, 64, M, cbuf, dinv, lane, bad);
     // ---- noise z (zero beyond K)
     if (lane < 16) {
         const float4 z4 = normals4_f32(seed, (uint32_t)lane, row, sweep, c3);
