@@ -18,9 +18,8 @@ namespace bpmf {
 namespace {
 
 constexpr int kCholWarps = 12;
-// per warp: L^T (64 x 64, sw64 layout), the column buffers (2 x 64), 1 / diag (64),
-// noise (64)
-constexpr int kCholWarpFloats = 64 * 64 + 128 + 64 + 64;
+// per warp: L^T (64 x kLtLd), the column buffers (2 x 64), 1 / diag (64), noise (64)
+constexpr int kCholWarpFloats = 64 * kLtLd + 128 + 64 + 64;
 constexpr size_t kCholSmemBytes = (size_t)kCholWarps * kCholWarpFloats * 4;
 static_assert(kCholSmemBytes <= 232448, "shared memory");
 
@@ -31,7 +30,7 @@ __global__ void __launch_bounds__(kCholWarps * 32, 1) rows_chol_kernel(RowArgs a
     extern __shared__ __align__(16) float chol_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* M = chol_smem + warp * kCholWarpFloats;
-    float* cbuf = M + 4096;
+    float* cbuf = M + 64 * kLtLd;
     float* dinv = cbuf + 128;
     float* zb = dinv + 64;
     const uint32_t sweep = (uint32_t)a.ctl->sweep;

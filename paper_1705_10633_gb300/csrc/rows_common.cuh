@@ -319,6 +319,11 @@ __device__ __forceinline__ float4 ld_chunk(const float* M, int i, int c)
 }
 
 
+// The K = 64 factor's transpose L^T in a warp's buffer: element (j, r) at j * kLtLd + r.
+// The padded row (68 floats) keeps the back solve's float4 loads of 32 different rows
+// at the minimum of four wavefronts, and a pivot's row store is one index add.
+constexpr int kLtLd = 68;
+
 // Pivot work of column j of a right-looking Cholesky with the forward solve fused,
 // for K = 64 with lane l owning rows r1 = l and r2 = 32 + l; p1 / p2 are the lane's
 // entries A[r1][j] / A[r2][j] after the updates of columns 0 .. j-1.  Gives the
@@ -327,39 +332,38 @@ __device__ __forceinline__ float4 ld_chunk(const float* M, int i, int c)
 // writes 1 / L[j][j] to dinv, column j of L transposed into row j of M (a
 // conflict-free row store) and into the column buffer of j's parity.  Branch-free
 // apart from the predicated stores.  HAS1 = false once the rows r1 are finished.
+// A pivot that is not positive and finite is not caught here: 1 / L[j][j] then comes
+// out non-positive, infinite or NaN, which the caller checks once per row.
 template <bool HAS1>
 __device__ __forceinline__ void chol_pivot(int j, float p1, float p2, float& b1, float& b2,
                                            float& l1, float& l2, float* M, float* cbuf,
-                                           float* dinv, int lane, bool& bad)
+                                           float* dinv, int lane)
 {
     const int r1 = lane, r2 = 32 + lane;
     const int owner = j & 31;
-    float piv = __shfl_sync(kFullMask, (HAS1 && j < 32) ? p1 : p2, owner);
+    const float piv = __shfl_sync(kFullMask, (HAS1 && j < 32) ? p1 : p2, owner);
     const float bk = __shfl_sync(kFullMask, (HAS1 && j < 32) ? b1 : b2, owner);
-    if (!(piv > 0.f && piv < INFINITY)) {  // also catches NaN
-        bad = true;
-        piv = 1.f;
-    }
     const float rinv = rsqrtf(piv);
     const float yk = bk * rinv;
     if (lane == 0) dinv[j] = rinv;
-    float* cb = cbuf + (j & 1) * 64;
+    float* cb = cbuf + (j & 1) * 64 - j - 1;
+    float* mrow = M + j * kLtLd;
     l1 = 0.f;
     if (HAS1) {
         const bool below = r1 > j;
         l1 = below ? p1 * rinv : 0.f;
         b1 = below ? fmaf(-l1, yk, b1) : (r1 == j ? yk : b1);
         if (below) {
-            M[sw64(j, r1)] = l1;
-            cb[r1 - j - 1] = l1;
+            mrow[r1] = l1;
+            cb[r1] = l1;
         }
     }
     const bool below2 = r2 > j;
     l2 = below2 ? p2 * rinv : 0.f;
     b2 = below2 ? fmaf(-l2, yk, b2) : (r2 == j ? yk : b2);
     if (below2) {
-        M[sw64(j, r2)] = l2;
-        cb[r2 - j - 1] = l2;
+        mrow[r2] = l2;
+        cb[r2] = l2;
     }
 }
 
@@ -379,7 +383,7 @@ template <int N1, int N2>
 __device__ __forceinline__ void chol_shifted_steps(float (&a1)[32], float (&a2)[64], float& b1,
                                                    float& b2, float& l1, float& l2, int k0,
                                                    int k1, float* M, float* cbuf, float* dinv,
-                                                   int lane, bool& bad)
+                                                   int lane)
 {
     static_assert(N1 % 4 == 0 && N2 % 4 == 0 && N2 > 0, "step shape");
 #pragma unroll 1
@@ -402,7 +406,7 @@ __device__ __forceinline__ void chol_shifted_steps(float (&a1)[32], float (&a2)[
                 if (t + 1 < N1) a1[t] = fmaf(-l1, cv[u], a1[t + 1]);
             }
             if ((t4 == 4 || (t4 == 0 && N2 == 4)) && k + 1 < 64)
-                chol_pivot<(N1 > 1)>(k + 1, n1, n2, b1, b2, nl1, nl2, M, cbuf, dinv, lane, bad);
+                chol_pivot<(N1 > 1)>(k + 1, n1, n2, b1, b2, nl1, nl2, M, cbuf, dinv, lane);
         }
         if (N1 > 1) a1[0] = n1;
         a2[0] = n2;
@@ -414,8 +418,9 @@ __device__ __forceinline__ void chol_shifted_steps(float (&a1)[32], float (&a2)[
 // Factor / solve / sample for K = 64.  Lane l holds rows r1 = l (a1: columns 0..31)
 // and r2 = 32 + l (a2: columns 0..63) of Lambda_i in registers -- entries above the
 // diagonal are never used -- and its entries b1 = b_i[r1], b2 = b_i[r2].  M is the
-// warp's 64 x 64 buffer in the sw64 layout; it receives the strictly lower part of
-// L, transposed, for the back solve (its previous contents are ignored).  The
+// warp's 64 x kLtLd buffer; it receives the strictly lower part of L, transposed,
+// for the back solve (its previous contents are ignored).  bad is set when a pivot
+// was not positive and finite (Lambda_i not positive definite in FP32).  The
 // factorisation runs in eight spans of 8 columns so the register rows shrink as
 // they finish, then x = L^{-T}(y + z).
 __device__ __forceinline__ void factor_solve_sample_rl64(float (&a1)[32], float (&a2)[64], float b1,
@@ -428,15 +433,21 @@ __device__ __forceinline__ void factor_solve_sample_rl64(float (&a1)[32], float 
 {
     const int r1 = lane, r2 = 32 + lane;
     float l1, l2;
-    chol_pivot<true>(0, a1[0], a2[0], b1, b2, l1, l2, M, cbuf, dinv, lane, bad);
-    chol_shifted_steps<32, 64>(a1, a2, b1, b2, l1, l2, 0, 8, M, cbuf, dinv, lane, bad);
-    chol_shifted_steps<24, 56>(a1, a2, b1, b2, l1, l2, 8, 16, M, cbuf, dinv, lane, bad);
-    chol_shifted_steps<16, 48>(a1, a2, b1, b2, l1, l2, 16, 24, M, cbuf, dinv, lane, bad);
-    chol_shifted_steps<8, 40>(a1, a2, b1, b2, l1, l2, 24, 32, M, cbuf, dinv, lane, bad);
-    chol_shifted_steps<0, 32>(a1, a2, b1, b2, l1, l2, 32, 40, M, cbuf, dinv, lane, bad);
-    chol_shifted_steps<0, 24>(a1, a2, b1, b2, l1, l2, 40, 48, M, cbuf, dinv, lane, bad);
-    chol_shifted_steps<0, 16>(a1, a2, b1, b2, l1, l2, 48, 56, M, cbuf, dinv, lane, bad);
-    chol_shifted_steps<0, 8>(a1, a2, b1, b2, l1, l2, 56, 64, M, cbuf, dinv, lane, bad);
+    chol_pivot<true>(0, a1[0], a2[0], b1, b2, l1, l2, M, cbuf, dinv, lane);
+    chol_shifted_steps<32, 64>(a1, a2, b1, b2, l1, l2, 0, 8, M, cbuf, dinv, lane);
+    chol_shifted_steps<24, 56>(a1, a2, b1, b2, l1, l2, 8, 16, M, cbuf, dinv, lane);
+    chol_shifted_steps<16, 48>(a1, a2, b1, b2, l1, l2, 16, 24, M, cbuf, dinv, lane);
+    chol_shifted_steps<8, 40>(a1, a2, b1, b2, l1, l2, 24, 32, M, cbuf, dinv, lane);
+    chol_shifted_steps<0, 32>(a1, a2, b1, b2, l1, l2, 32, 40, M, cbuf, dinv, lane);
+    chol_shifted_steps<0, 24>(a1, a2, b1, b2, l1, l2, 40, 48, M, cbuf, dinv, lane);
+    chol_shifted_steps<0, 16>(a1, a2, b1, b2, l1, l2, 48, 56, M, cbuf, dinv, lane);
+    chol_shifted_steps<0, 8>(a1, a2, b1, b2, l1, l2, 56, 64, M, cbuf, dinv, lane);
+    // every pivot's 1 / L[j][j] is in dinv (the last step began with a warp sync): it is
+    // positive and finite exactly when the pivot was
+    {
+        const float d1 = dinv[r1], d2 = dinv[r2];
+        if (!(d1 > 0.f && d1 < INFINITY && d2 > 0.f && d2 < INFINITY)) bad = true;  // and NaN
+    }
     // ---- noise z (zero beyond K)
     if (lane < 16) {
         const float4 z4 = normals4_f32(seed, (uint32_t)lane, row, sweep, c3);
@@ -456,7 +467,8 @@ __device__ __forceinline__ void factor_solve_sample_rl64(float (&a1)[32], float 
     // a row on or below i is computed and dropped.
 #pragma unroll 1
     for (int g = 15; g >= 0; --g) {
-        const float4 A1 = ld_chunk(M, r1, g), A2 = ld_chunk(M, r2, g);
+        const float4 A1 = *reinterpret_cast<const float4*>(M + r1 * kLtLd + 4 * g);
+        const float4 A2 = *reinterpret_cast<const float4*>(M + r2 * kLtLd + 4 * g);
         const float4 D = *reinterpret_cast<const float4*>(dinv + 4 * g);
         const float l1v[4] = {A1.x, A1.y, A1.z, A1.w};
         const float l2v[4] = {A2.x, A2.y, A2.z, A2.w};

@@ -190,3 +190,24 @@ def test_row_launch_timing(bp):
         assert bp.bpmf_status(h) == 0
     finally:
         bp.bpmf_destroy(h)
+
+
+def test_non_finite_factor_row_sets_not_pd_on_tensor_route(bp):
+    """A non-finite row of the other side reaches the tensor-core route's Gram; the
+    factorisation kernel then sees a pivot that is not positive and finite and raises
+    the not-positive-definite status, without a fault; the context stays usable."""
+    prob = workloads.random_small(300, 200, 64, 20000, seed=9)
+    h = bp.create_from_problem(prob, stream=bp.torch_stream())
+    try:
+        assert bp.bpmf_info(h, 0)["n_long"] > 0
+        U, V, hyper, s = bp.bpmf_get_state(h, prob.M, prob.N, prob.K)
+        V[3, :] = np.inf
+        bp.bpmf_set_state(h, U, V, hyper, s)
+        bp.bpmf_step(h, bp.BPMF_PHASE_ROWS_USER)
+        assert bp.bpmf_status(h) == bp.BPMF_ENOTPD
+        h2 = bp.create_from_problem(prob, stream=bp.torch_stream())
+        bp.bpmf_sweep(h2, 1)
+        assert bp.bpmf_status(h2) == 0
+        bp.bpmf_destroy(h2)
+    finally:
+        bp.bpmf_destroy(h)
