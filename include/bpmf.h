@@ -211,7 +211,8 @@ int bpmf_status(bpmf_handle h);
  * bin).  order_out (rows entries) receives the short bin, then the long bin, each
  * longest first with equal degrees in ascending row order (a counting sort, Sec. 4.2's
  * ordering of items by cost); *n_short the size of the short bin.  BPMF_EINVAL on
- * rows < 1 or above INT32_MAX, a NULL pointer or malformed offsets. */
+ * rows < 1 or above INT32_MAX, a row with more than INT32_MAX ratings, a NULL pointer
+ * or malformed offsets; BPMF_ENOMEM if the host sort cannot allocate. */
 int bpmf_bin_rows(int64_t rows, const int64_t* ptr, int64_t long_min, int32_t* order_out,
                   int64_t* n_short);
 
@@ -224,8 +225,9 @@ int bpmf_bin_rows(int64_t rows, const int64_t* ptr, int64_t long_min, int32_t* o
  * order_out[p] (n entries) is the row placed at p and CTA c takes places
  * first_out[c] .. first_out[c + 1] - 1 (first_out: min(n, grid) + 1 entries), each
  * row, longest first, given to the CTA with the least cost so far (ties: lowest
- * CTA); else *planned = 0 and the outputs are not written.  BPMF_EINVAL on a
- * negative n or degree, grid < 1, or a NULL pointer that is needed. */
+ * CTA); else *planned = 0 and the outputs are not written.  BPMF_EINVAL on n or a
+ * degree outside [0, INT32_MAX], grid < 1, or a NULL pointer that is needed;
+ * BPMF_ENOMEM if the host plan cannot allocate. */
 int bpmf_balance_rows(int64_t n, const int64_t* degree, int64_t grid, int32_t* order_out,
                       int64_t* first_out, int32_t* planned);
 
@@ -265,18 +267,23 @@ int bpmf_row_launch_ms(bpmf_handle h, float* cuda_core_ms, float* gram_ms, float
  * writes the same quantities bpmf_get_stats returns:
  *   mean = (1/rows) sum_r x_r,  S = (1/rows) sum_r (x_r - mean)(x_r - mean)^T.
  *   X      : device, rows x ld FP32 with ld = K rounded up to a multiple of 16
- *            (16, 32, 48 or 64); columns K..ld-1 are ignored.
- *   shift  : device, K doubles subtracted before summing for accuracy (any
- *            value near the mean; the handle uses its current mu), or NULL.
- *   mean   : device, K doubles (written).   S : device, K x K doubles (written).
+ *            (16, 32, 48 or 64), 16-byte aligned; columns K..ld-1 are ignored.
+ *   shift  : device, K doubles (8-byte aligned) subtracted before summing for
+ *            accuracy (any value near the mean does; a handle's hyper step uses
+ *            the FP64 mean of the first 256 rows, summed in row order), or NULL
+ *            for zero.
+ *   mean   : device, K doubles (written).   S : device, K x K doubles (written);
+ *            both 8-byte aligned.
  *   stream : cudaStream_t; the call only enqueues work and returns.
  * Scratch lives in a fixed file-scope device array (about 5.4 MB, held on every
- * GPU that loads the library until the process exits); K > 64 or rows outside
- * [1, 2^31 - 1] is rejected with BPMF_EINVAL.  The first call on each device
- * looks up the array's device address (with that device current), so make
- * that first call before any stream capture.  All calls share the one array:
- * calls that overlap on the GPU (other streams, other threads) race and must
- * be serialised by the caller.  Nothing in the array needs to start at zero.
+ * GPU that loads the library until the process exits); K > 64, rows outside
+ * [1, 2^31 - 1] or a misaligned pointer is rejected with BPMF_EINVAL before any
+ * launch.  The first call on each device looks up the array's device address
+ * (with that device current) and keeps it, so make that first call before any
+ * stream capture, and do not call this entry point after cudaDeviceReset in the
+ * same process (the array may then sit elsewhere).  All calls share the one
+ * array: calls that overlap on the GPU (other streams, other threads) race and
+ * must be serialised by the caller.  Nothing in the array needs to start at zero.
  */
 int bpmf_row_stats_noalloc(const float* X, int64_t rows, int32_t K, const double* shift,
                            double* mean, double* S, void* stream);

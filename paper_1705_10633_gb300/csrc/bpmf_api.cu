@@ -720,10 +720,14 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
     if (prm.nu0 == 0.0) prm.nu0 = (double)K;
     if (!(prm.alpha > 0.0) || !(prm.beta0 > 0.0) || !(prm.nu0 >= (double)K)) return BPMF_EINVAL;
     if (prm.order != 0 && prm.order != 1) return BPMF_EINVAL;
-    // the column indices of the row view are checked on the device when it also builds
-    // the column view there (one pass over the uploaded ratings, with the mean)
+    // The column view is always built by the library from the row view: on the device
+    // when the ratings fit 32-bit positions (the column indices of the row view are then
+    // checked there, in one pass with the mean), else on the host.  A column view the
+    // caller passes must equal it entry by entry (rows ascending in each column), else
+    // BPMF_EINVAL: the same ratings in two views that disagree would give a chain of
+    // another matrix.
     if (!valid_ptr(M, csr_ptr)) return BPMF_EINVAL;
-    const bool device_csc = !have_csc && csr_ptr[M] > 0 && csr_ptr[M] < INT32_MAX;
+    const bool device_csc = csr_ptr[M] > 0 && csr_ptr[M] < INT32_MAX;
     if (!device_csc && !valid_csr(M, N, csr_ptr, csr_col)) return BPMF_EINVAL;
     if (have_csc) {
         if (!valid_csr(N, M, csc_ptr, csc_row) || csc_ptr[N] != csr_ptr[M]) return BPMF_EINVAL;
@@ -776,10 +780,27 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
     std::vector<int64_t> cp;
     std::vector<int32_t> ri;
     std::vector<float> cv;
-    // without a caller-supplied CSC the column view is built on the device from the
-    // uploaded CSR (same order as the host counting sort, which serves the rest)
-    if (!have_csc && !device_csc) {
+    // the column view built on the host when it is not built on the device (same order
+    // as the device build); a caller's view is compared with it here
+    if (!device_csc) {
         build_csc(M, N, csr_ptr, csr_col, csr_val, cp, ri, cv);
+        if (have_csc) {
+            const int64_t nz = csr_ptr[M];
+            const bool same = std::equal(cp.begin(), cp.end(), csc_ptr) &&
+                              std::equal(ri.begin(), ri.end(), csc_row) &&
+                              std::equal(cv.begin(), cv.end(), csc_val, [](float a, float b) {
+                                  return memcmp(&a, &b, sizeof(float)) == 0;
+                              }) && (int64_t)ri.size() == nz;
+            if (!same) {
+                bpmf_destroy(h);
+                return BPMF_EINVAL;
+            }
+        }
+    }
+    const int64_t* user_csc_ptr = csc_ptr;
+    const int32_t* user_csc_row = csc_row;
+    const float* user_csc_val = csc_val;
+    if (!device_csc) {
         csc_ptr = cp.data();
         csc_row = ri.data();
         csc_val = cv.data();
@@ -829,6 +850,15 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
             const DevSide& u = h->side[0];
             const TempAlloc tmp{temp_alloc, temp_free, h};
             e = build_csc_device(u.ptr, u.idx, u.val, M, N, h->nnz, d.ptr, d.idx, d.val, tmp, st);
+            if (e == cudaSuccess && have_csc) {
+                bool same = false;
+                e = check_csc_device(d.ptr, d.idx, d.val, user_csc_ptr, user_csc_row, user_csc_val,
+                                     N, h->nnz, h->rbar, tmp, &same, st);
+                if (e == cudaSuccess && !same) {
+                    rc = BPMF_EINVAL;
+                    break;
+                }
+            }
             cp.resize((size_t)N + 1);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(cp.data(), d.ptr, sizeof(int64_t) * (N + 1),
@@ -1330,29 +1360,42 @@ int bpmf_bin_rows(int64_t rows, const int64_t* ptr, int64_t long_min, int32_t* o
 {
     if (rows < 1 || rows > (int64_t)INT32_MAX || !ptr || !order_out || !n_short) return BPMF_EINVAL;
     if (!valid_ptr(rows, ptr)) return BPMF_EINVAL;
-    std::vector<int32_t> order;
-    int64_t nl = 0, lr = 0;
-    bin_rows(rows, ptr, long_min > 0 ? long_min : INT64_MAX, order, n_short, &nl, &lr);
-    std::copy(order.begin(), order.end(), order_out);
+    // the counting sort keeps one counter per degree: a row's degree is bounded like a
+    // row index (the device kernels count ratings of a row in 32 bits too)
+    for (int64_t r = 0; r < rows; ++r)
+        if (ptr[r + 1] - ptr[r] > (int64_t)INT32_MAX) return BPMF_EINVAL;
+    try {
+        std::vector<int32_t> order;
+        int64_t nl = 0, lr = 0;
+        bin_rows(rows, ptr, long_min > 0 ? long_min : INT64_MAX, order, n_short, &nl, &lr);
+        std::copy(order.begin(), order.end(), order_out);
+    } catch (const std::bad_alloc&) {
+        return BPMF_ENOMEM;
+    }
     return BPMF_OK;
 }
 
 int bpmf_balance_rows(int64_t n, const int64_t* degree, int64_t grid, int32_t* order_out,
                       int64_t* first_out, int32_t* planned)
 {
-    if (n < 0 || grid < 1 || !planned || (n > 0 && (!degree || !order_out || !first_out)))
+    if (n < 0 || n > (int64_t)INT32_MAX || grid < 1 || !planned ||
+        (n > 0 && (!degree || !order_out || !first_out)))
         return BPMF_EINVAL;
-    std::vector<int64_t> cost((size_t)n);
-    for (int64_t k = 0; k < n; ++k) {
-        if (degree[k] < 0) return BPMF_EINVAL;
-        cost[(size_t)k] = plan_cost(degree[k]);
-    }
-    std::vector<int32_t> pos;
-    std::vector<int64_t> first;
-    *planned = balance_plan(cost, std::min<int64_t>(n, grid), pos, first) ? 1 : 0;
-    if (*planned) {
-        std::copy(pos.begin(), pos.end(), order_out);
-        std::copy(first.begin(), first.end(), first_out);
+    try {
+        std::vector<int64_t> cost((size_t)n);
+        for (int64_t k = 0; k < n; ++k) {
+            if (degree[k] < 0 || degree[k] > (int64_t)INT32_MAX) return BPMF_EINVAL;
+            cost[(size_t)k] = plan_cost(degree[k]);
+        }
+        std::vector<int32_t> pos;
+        std::vector<int64_t> first;
+        *planned = balance_plan(cost, std::min<int64_t>(n, grid), pos, first) ? 1 : 0;
+        if (*planned) {
+            std::copy(pos.begin(), pos.end(), order_out);
+            std::copy(first.begin(), first.end(), first_out);
+        }
+    } catch (const std::bad_alloc&) {
+        return BPMF_ENOMEM;
     }
     return BPMF_OK;
 }

@@ -168,6 +168,13 @@ struct TempAlloc {
 cudaError_t build_csc_device(const int64_t* csr_ptr, const int32_t* csr_col, const float* csr_val,
                              int64_t M, int64_t N, int64_t nnz, int64_t* csc_ptr, int32_t* csc_row,
                              float* csc_val, const TempAlloc& tmp, cudaStream_t s);
+// *same: whether a caller's column view (host arrays, raw values) equals the one built
+// on the device (values centred by rbar): offsets, row indices (ascending in each
+// column) and values, entry by entry.  Waits for the stream.
+cudaError_t check_csc_device(const int64_t* built_ptr, const int32_t* built_row, const float* built_val,
+                             const int64_t* csc_ptr, const int32_t* csc_row, const float* csc_val,
+                             int64_t N, int64_t nnz, double rbar, const TempAlloc& tmp, bool* same,
+                             cudaStream_t s);
 
 // One slot of the tensor-core route's scratch (K = 64): the lower triangle of
 // Lambda_i in float4 chunks, chunk column c (columns 4c .. 4c + 3) holding rows

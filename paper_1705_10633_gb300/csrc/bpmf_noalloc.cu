@@ -13,7 +13,12 @@
 // library is loaded holds it (kScratchDoubles doubles, about 5.4 MB) until the
 // process exits.  Host code cannot use the array's name as a device address,
 // so the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current) and caches it.
+// cudaGetSymbolAddress (with that device current) and caches it.  The cached
+// address belongs to the device context of that first call: after a
+// cudaDeviceReset in the same process the module is loaded again and the array
+// may move, so the entry point must not be called after a reset.
+#include <stdint.h>
+
 #include <mutex>
 
 #include "bpmf.h"
@@ -86,6 +91,11 @@ extern "C" int bpmf_row_stats_noalloc(const float* X, int64_t rows, int32_t K, c
                                       double* mean, double* S, void* cuda_stream)
 {
     if (!X || !mean || !S) return BPMF_EINVAL;
+    // the reduction reads X a float4 at a time; the FP64 buffers are read and written
+    // as doubles: misaligned pointers are refused here, before any launch
+    if ((reinterpret_cast<uintptr_t>(X) & 15u) != 0 || (reinterpret_cast<uintptr_t>(mean) & 7u) != 0 ||
+        (reinterpret_cast<uintptr_t>(S) & 7u) != 0 || (reinterpret_cast<uintptr_t>(shift) & 7u) != 0)
+        return BPMF_EINVAL;
     if (K < 1 || K > kNoAllocMaxK) return BPMF_EINVAL;  // beyond the static scratch
     if (rows < 1 || rows > (int64_t)INT32_MAX) return BPMF_EINVAL;
     const int kp = (K + 15) / 16 * 16;

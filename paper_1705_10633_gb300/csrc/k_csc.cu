@@ -107,4 +107,60 @@ cudaError_t build_csc_device(const int64_t* csr_ptr, const int32_t* csr_col, con
     return e != cudaSuccess ? e : es;
 }
 
+namespace {
+
+// *bad = 1 where a caller's column view (cp, ci, cv: raw values) differs from the built
+// one (bp, bi, bv: values centred by rbar): the offsets, a row index, or a value once
+// centred the way the built values were
+__global__ void csc_compare_kernel(const int64_t* __restrict__ bp, const int32_t* __restrict__ bi,
+                                   const float* __restrict__ bv, const int64_t* __restrict__ cp,
+                                   const int32_t* __restrict__ ci, const float* __restrict__ cv,
+                                   int64_t N, int64_t nnz, double rbar, unsigned int* bad)
+{
+    const int64_t n = nnz > N + 1 ? nnz : N + 1;
+    bool diff = false;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (e <= N && bp[e] != cp[e]) diff = true;
+        if (e < nnz && (bi[e] != ci[e] || bv[e] != (float)((double)cv[e] - rbar))) diff = true;
+    }
+    if (diff) *bad = 1u;
+}
+
+}  // namespace
+
+cudaError_t check_csc_device(const int64_t* built_ptr, const int32_t* built_row, const float* built_val,
+                             const int64_t* csc_ptr, const int32_t* csc_row, const float* csc_val,
+                             int64_t N, int64_t nnz, double rbar, const TempAlloc& tmp, bool* same,
+                             cudaStream_t s)
+{
+    *same = false;
+    const size_t ptr_bytes = ((sizeof(int64_t) * (size_t)(N + 1)) + 255) & ~(size_t)255;
+    const size_t idx_bytes = ((sizeof(int32_t) * (size_t)nnz) + 255) & ~(size_t)255;
+    char* pool = static_cast<char*>(tmp.alloc(ptr_bytes + 2 * idx_bytes + 256));
+    if (!pool) return cudaErrorMemoryAllocation;
+    int64_t* cp = reinterpret_cast<int64_t*>(pool);
+    int32_t* ci = reinterpret_cast<int32_t*>(pool + ptr_bytes);
+    float* cv = reinterpret_cast<float*>(pool + ptr_bytes + idx_bytes);
+    unsigned int* bad = reinterpret_cast<unsigned int*>(pool + ptr_bytes + 2 * idx_bytes);
+    unsigned int bad_h = 0;
+    cudaError_t e = cudaMemcpyAsync(cp, csc_ptr, sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nnz)
+        e = cudaMemcpyAsync(ci, csc_row, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nnz)
+        e = cudaMemcpyAsync(cv, csc_val, sizeof(float) * nnz, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess) {
+        csc_compare_kernel<<<grid_for(nnz > N + 1 ? nnz : N + 1), 256, 0, s>>>(
+            built_ptr, built_row, built_val, cp, ci, cv, N, nnz, rbar, bad);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad_h, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+    const cudaError_t es = cudaStreamSynchronize(s);  // the scratch is returned below
+    tmp.free(pool);
+    if (e == cudaSuccess) e = es;
+    if (e == cudaSuccess) *same = bad_h == 0;
+    return e;
+}
+
 }  // namespace bpmf

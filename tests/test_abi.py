@@ -124,3 +124,15 @@ def test_set_tuning_and_batch_reject_null(bp):
     arr = (__import__("ctypes").c_void_p * 1)(None)
     assert bp.lib().bpmf_sweep_batch(arr, 1, 1) == bp.BPMF_EINVAL
     assert bp.lib().bpmf_sweep_batch(arr, -1, 1) == bp.BPMF_EINVAL
+
+
+def test_row_stats_noalloc_rejects_misaligned_pointers_on_the_host(bp):
+    # checked before any CUDA call, so no device is needed: the pointers are never used
+    base = 1 << 20
+    for X, mean, S, shift in ((base + 4, base, base, 0), (base + 8, base, base, 0),
+                              (base, base + 4, base, 0), (base, base, base + 2, 0),
+                              (base, base, base, base + 4)):
+        rc = bp.lib().bpmf_row_stats_noalloc(X, 100, 16, shift or None, mean, S, None)
+        assert rc == bp.BPMF_EINVAL
+    assert bp.lib().bpmf_row_stats_noalloc(base, 100, 65, None, base, base, None) == bp.BPMF_EINVAL
+    assert bp.lib().bpmf_row_stats_noalloc(base, 0, 16, None, base, base, None) == bp.BPMF_EINVAL

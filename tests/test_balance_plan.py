@@ -130,3 +130,28 @@ def test_degree_bins_reject_malformed_offsets(bp):
         with pytest.raises(bp.BpmfError) as ei:
             bp.bpmf_bin_rows(np.array(ptr), 48)
         assert ei.value.code == bp.BPMF_EINVAL
+
+
+def test_host_entry_points_reject_oversized_degrees_and_counts(bp):
+    """Counts that would ask the host sort or plan for terabytes, or overflow the
+    32-bit row places, are refused with BPMF_EINVAL before anything is allocated."""
+    import ctypes as C
+    L = bp.lib()
+    ptr = np.array([0, 1 << 40], dtype=np.int64)
+    order = np.zeros(4, dtype=np.int32)
+    n_short = C.c_int64()
+    rc = L.bpmf_bin_rows(1, ptr.ctypes.data_as(C.POINTER(C.c_int64)), 48,
+                         order.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(n_short))
+    assert rc == bp.BPMF_EINVAL
+    deg = np.array([5, 1 << 40, 3], dtype=np.int64)
+    first = np.zeros(4, dtype=np.int64)
+    planned = C.c_int32()
+    rc = L.bpmf_balance_rows(3, deg.ctypes.data_as(C.POINTER(C.c_int64)), 2,
+                             order.ctypes.data_as(C.POINTER(C.c_int32)),
+                             first.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(planned))
+    assert rc == bp.BPMF_EINVAL
+    # n above INT32_MAX is refused before the degree array (3 entries here) is read
+    rc = L.bpmf_balance_rows(1 << 31, deg.ctypes.data_as(C.POINTER(C.c_int64)), 2,
+                             order.ctypes.data_as(C.POINTER(C.c_int32)),
+                             first.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(planned))
+    assert rc == bp.BPMF_EINVAL

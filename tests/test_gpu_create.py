@@ -1,7 +1,8 @@
 """bpmf_create's device-side input pass: the column indices of the row view are range
 checked on the device (BPMF_EINVAL, nothing leaked), and the ratings' mean is an FP64
 sum in a fixed order, equal to the exact mean within rounding and the same on every
-run; with a caller-supplied column view the host checks everything."""
+run; a caller-supplied column view is checked for structure on the host and, entry by
+entry, against the view the library builds from the rows."""
 import math
 
 import numpy as np
@@ -29,7 +30,7 @@ def test_out_of_range_column_is_rejected(bp, bad):
     with pytest.raises(bp.BpmfError) as ei:
         bp.bpmf_create(2, 3, 4, ptr, col, val, stream=bp.torch_stream())
     assert ei.value.code == bp.BPMF_EINVAL
-    # with a caller-supplied column view the same input is refused on the host
+    # with a caller-supplied column view the same input is refused too
     cp = np.array([0, 1, 2, 3], dtype=np.int64)
     cr = np.array([0, 1, 0], dtype=np.int32)
     with pytest.raises(bp.BpmfError) as ei:
@@ -53,3 +54,40 @@ def test_mean_is_exact_within_rounding_and_reproducible(bp):
             bp.bpmf_destroy(h)
     assert got[0] == got[1] == got[2]
     assert abs(got[0] - exact) <= 1e-13 * abs(exact)
+
+
+def test_caller_column_view_must_be_the_transpose(bp):
+    """The column view a caller passes must hold the row view's ratings (rows ascending
+    in each column): the true transpose gives the same chain as no column view; the same
+    structure with its values permuted inside a column, or two row indices swapped, is
+    refused with BPMF_EINVAL."""
+    prob = workloads.random_small(300, 120, 16, 6000, seed=12, n_test=50)
+    cptr, crow, cval = prob.csc()
+    a = bp.create_from_problem(prob, stream=bp.torch_stream())
+    b = bp.bpmf_create(prob.M, prob.N, prob.K, prob.csr_ptr, prob.csr_col, prob.csr_val,
+                       csc_ptr=cptr, csc_row=crow, csc_val=cval,
+                       test_i=prob.test_i, test_j=prob.test_j, test_r=prob.test_r,
+                       params=bp.bpmf_default_params(alpha=prob.alpha, seed=prob.seed,
+                                                     burn_in=prob.burn_in),
+                       stream=bp.torch_stream())
+    try:
+        assert bp.bpmf_sweep(a, 2) == bp.bpmf_sweep(b, 2)
+        sa = bp.bpmf_get_state(a, prob.M, prob.N, prob.K)
+        sb = bp.bpmf_get_state(b, prob.M, prob.N, prob.K)
+        for x, y in zip(sa[:3], sb[:3]):
+            np.testing.assert_array_equal(x, y)
+    finally:
+        bp.bpmf_destroy(a)
+        bp.bpmf_destroy(b)
+    j = int(np.argmax(np.diff(cptr)))  # a column with several ratings
+    lo, hi = int(cptr[j]), int(cptr[j + 1])
+    assert hi - lo >= 2 and cval[lo] != cval[lo + 1]
+    bad_val = cval.copy()
+    bad_val[lo], bad_val[lo + 1] = cval[lo + 1], cval[lo]
+    bad_row = crow.copy()
+    bad_row[lo], bad_row[lo + 1] = crow[lo + 1], crow[lo]
+    for r, v in ((crow, bad_val), (bad_row, cval)):
+        with pytest.raises(bp.BpmfError) as ei:
+            bp.bpmf_create(prob.M, prob.N, prob.K, prob.csr_ptr, prob.csr_col, prob.csr_val,
+                           csc_ptr=cptr, csc_row=r, csc_val=v, stream=bp.torch_stream())
+        assert ei.value.code == bp.BPMF_EINVAL

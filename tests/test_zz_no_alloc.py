@@ -10,6 +10,7 @@ ran the same reduction (same rows, same shift).  This file is collected last.
 import numpy as np
 import pytest
 
+import oracle
 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -58,3 +59,34 @@ def test_row_stats_noalloc_matches_hyper_step_twice():
         bp.bpmf_row_stats_noalloc(Xd.data_ptr(), prob.M, 65, None, mean_d.data_ptr(),
                                   S_d.data_ptr(), stream)
     assert ei.value.code == bp.BPMF_EINVAL
+
+
+def test_row_stats_noalloc_many_rows_without_shift_against_the_oracle():
+    """A side larger than the reduction's block limit (the scratch holds 160 block
+    partials; 400,000 rows would ask for more), summed without a shift (NULL): the
+    mean and scatter match the FP64 oracle's row statistics within the FP32-chunk
+    rounding of the device sums, and a second call gives the same bits."""
+    import torch
+
+    import paper_1705_10633_gb300 as bp
+
+    torch.cuda.set_device(0)
+    stream = bp.torch_stream()
+    M, K = 400_000, 64
+    rng = np.random.default_rng(5)
+    U = (rng.standard_normal((M, K)) * 0.5 + 0.1).astype(np.float32)
+    mean_ref, S_ref = oracle.row_stats(U.astype(np.float64))
+    Xd = torch.from_numpy(U).cuda()
+    outs = []
+    for call in range(2):
+        mean_d = torch.full((K,), float("nan"), dtype=torch.float64, device="cuda")
+        S_d = torch.full((K, K), float("nan"), dtype=torch.float64, device="cuda")
+        bp.bpmf_row_stats_noalloc(Xd.data_ptr(), M, K, None, mean_d.data_ptr(), S_d.data_ptr(),
+                                  stream)
+        torch.cuda.synchronize()
+        outs.append((mean_d.cpu().numpy(), S_d.cpu().numpy()))
+    mean, S = outs[0]
+    # FP32 partial sums of ~1k rows: relative error well below 1e-5 of the scale
+    assert np.abs(mean - mean_ref).max() <= 1e-5 * np.abs(mean_ref).max()
+    assert np.abs(S - S_ref).max() <= 1e-5 * np.abs(S_ref).max()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
