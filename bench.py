@@ -251,9 +251,9 @@ def run_native(args):
             cache = TuningCache(args.tuning_cache) if args.tuning_cache else None
             best, times = autotune(h, prob.M, prob.N, K, stream.cuda_stream, cache=cache,
                                    degrees=(np.diff(prob.csr_ptr), prob.col_degrees()))
-            tuning = {"long_min_degree": best[0], "long_shape_degree": best[1],
-                      "split_degree": best[2], "rank_one_degree": best[3],
-                      "trials_ms": {"%d/%d/%d/%d" % k: round(v, 3) for k, v in sorted(times.items())}}
+            tuning = {"long_min_degree": best[0], "split_degree": best[1],
+                      "rank_one_degree": best[2],
+                      "trials_ms": {"%d/%d/%d" % k: round(v, 3) for k, v in sorted(times.items())}}
         for _ in range(args.warmup):
             bp.bpmf_sweep(h, 1, want_rmse=False)
         torch.cuda.synchronize(dev)

@@ -89,9 +89,6 @@ typedef struct {
     int32_t long_min_degree; /* rows with at least this many ratings use the tensor-core
                                 kernel (K in 49..64); <= 0 = library default (48)      */
     int32_t wait_timeout_ms; /* limit of every device-side wait, <= 0 = 2000 ms         */
-    int32_t long_shape_degree; /* tensor-core launches whose rows average at least this
-                                  many ratings use the CTA shape with more gather stages
-                                  and fewer factorisation warps; <= 0 = default (1024)  */
     int32_t split_degree; /* rows on the CUDA-core kernel with at least this many ratings
                              are split into runs of split_degree / 2 ratings done by
                              separate warps (Sec. 3.2), the partial Gram matrices summed
@@ -111,17 +108,23 @@ typedef struct {
 int bpmf_default_params(bpmf_params* p);
 
 /*
- * Create a chain: copy the ratings (host arrays) to the device, build the
- * column view, bin the rows by degree, and draw the initial factors
- * U, V ~ N(0, 1) from the Philox init streams.
+ * Create a chain: the state Alg. 1 (Sec. 2) iterates on, for the M x N rating
+ * matrix R ~ U V^T of Sec. 1 (users = rows, movies = columns).  Copies the ratings
+ * (host arrays) to the device, builds the column view (the ratings of each movie,
+ * which the movie loop of Alg. 1 walks), bins the rows by degree (Sec. 4.2's
+ * per-item cost) and draws the initial factors U, V ~ N(0, 1) from the Philox
+ * init streams (the paper does not state an initial state).
  *   csr_*        : M + 1 row pointers (csr_ptr[0] = 0), nnz column indices in
  *                  [0, N), nnz values.  Host memory.
- *   csc_*        : the same ratings by column, or all three NULL to have the
- *                  library build them.  Host memory.
+ *   csc_*        : the same ratings by column (rows ascending inside each column),
+ *                  or all three NULL.  The library always builds the column view
+ *                  itself; one passed here must equal it entry by entry, else
+ *                  BPMF_EINVAL.  Host memory.
  *   test_*       : T held-out points (row, column, value), T may be 0.  Host.
  *   cuda_stream  : cudaStream_t for all work of this handle (NULL = default).
  * Errors: BPMF_EINVAL for bad sizes, K outside [1, 64], nu0 < K, pointers out
- * of order or indices out of range; BPMF_ENOMEM; BPMF_ECUDA.
+ * of order, indices out of range or a column view that is not the transpose of
+ * the rows; BPMF_ENOMEM; BPMF_ECUDA.
  */
 int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t* csr_ptr,
                 const int32_t* csr_col, const float* csr_val, const int64_t* csc_ptr,
@@ -154,9 +157,9 @@ int bpmf_sweep(bpmf_handle h, int32_t n_sweeps, double* rmse_sample, double* rms
 int bpmf_sweep_batch(bpmf_handle* hs, int32_t n, int32_t n_sweeps);
 
 /*
- * Change the tuning thresholds of a live handle (long_min_degree, long_shape_degree,
- * split_degree and rank_one_degree of bpmf_params, each with its meaning of 0 and of
- * negative values there): the rows of both sides
+ * Change the tuning thresholds of a live handle (long_min_degree, split_degree and
+ * rank_one_degree of bpmf_params, each with its meaning of 0 and of negative values
+ * there): the rows of both sides
  * are binned and split again (host sort of the degrees kept from bpmf_create,
  * host-to-device copies waited for; the segment arrays grow when a smaller
  * split_degree needs more, the old ones held until bpmf_destroy).  The chain state
@@ -164,25 +167,30 @@ int bpmf_sweep_batch(bpmf_handle* hs, int32_t n, int32_t n_sweeps);
  * between split and whole or between the Gram and rank-one routes, whose results agree
  * within the FP32 tolerance, not bit for bit.  For autotuning.  BPMF_ENOMEM / BPMF_ECUDA leave the handle unusable.
  */
-int bpmf_set_tuning(bpmf_handle h, int32_t long_min_degree, int32_t long_shape_degree,
-                    int32_t split_degree, int32_t rank_one_degree);
+int bpmf_set_tuning(bpmf_handle h, int32_t long_min_degree, int32_t split_degree,
+                    int32_t rank_one_degree);
 
 /* Run one BPMF_PHASE_* step of a sweep (for checking the steps one by one). */
 int bpmf_step(bpmf_handle h, int32_t phase);
 
 /*
  * Predictions r_bar + u_i . v_j of the current sample for n points (clipped
- * under BPMF_CLIP).  where = 0: i, j, out are host arrays; where = 1: device
- * arrays valid on the handle's stream.  BPMF_EINVAL for indices out of range.
+ * under BPMF_CLIP): the "predict rating" step of Alg. 1's last loop (Sec. 2), on
+ * points the caller names.  where = 0: i, j, out are host arrays; where = 1:
+ * device arrays valid on the handle's stream.  BPMF_EINVAL for indices out of
+ * range (checked on the host for where = 0; device indices are the caller's
+ * responsibility).
  */
 int bpmf_predict(bpmf_handle h, int64_t n, const int32_t* i, const int32_t* j, float* out,
                  int32_t where);
 
 /*
- * Chain state, host buffers: U (M x K), V (N x K) FP32, hyper FP64 laid out as
- * [mu_U (K), Lambda_U (K x K), mu_V (K), Lambda_V (K x K)], sweep = number of
- * completed sweeps.  Any pointer may be NULL to skip that part.  Because every
- * random number is a function of (seed, sweep, row), restoring a state and
+ * Chain state, host buffers: the variables Alg. 1 (Sec. 2) carries from one
+ * sampling iteration to the next -- U (M x K), V (N x K) FP32 and the sampled
+ * hyper-parameters in FP64, laid out as [mu_U (K), Lambda_U (K x K), mu_V (K),
+ * Lambda_V (K x K)] -- and sweep = number of completed sweeps.  Any pointer may be
+ * NULL to skip that part.  The paper has no checkpoint step; because every random
+ * number here is a function of (seed, sweep, row), restoring a state and
  * continuing reproduces an uninterrupted chain.
  */
 int bpmf_get_state(bpmf_handle h, float* U, float* V, double* hyper, uint64_t* sweep);
@@ -197,12 +205,17 @@ int bpmf_set_accum(bpmf_handle h, const double* psum, int64_t n_avg);
  * S = (1/n) sum (x - mean)(x - mean)^T (K x K), FP64 host buffers. */
 int bpmf_get_stats(bpmf_handle h, int32_t side, int64_t* n, double* mean, double* S);
 
-/* Conditional means of the last row update of `side` (rows x K FP32, host);
- * needs BPMF_DEBUG_MEANS at create, else BPMF_EINVAL. */
+/* Conditional means of the last row update of `side` (rows x K FP32, host): each
+ * row's update of Alg. 1 (Sec. 2) draws the new vector as this mean "plus randomly
+ * sampled noise"; kept for checking the update against a reference.  Needs
+ * BPMF_DEBUG_MEANS at create, else BPMF_EINVAL. */
 int bpmf_debug_means(bpmf_handle h, int32_t side, float* out);
 
-/* Sticky device status: BPMF_OK, BPMF_ENOTPD, BPMF_ENAN, BPMF_EGAMMA or
- * BPMF_ETIMEOUT.  Syncs the handle's stream. */
+/* Sticky device status: BPMF_OK, BPMF_ETIMEOUT (reported first: later launches may
+ * report what a timed-out one left behind), BPMF_ENOTPD (a precision matrix of Sec.
+ * 3.1's factorisation was not positive definite in FP32), BPMF_ENAN or BPMF_EGAMMA.
+ * The paper has no counterpart; kernels record failures here instead of trapping.
+ * Syncs the handle's stream. */
 int bpmf_status(bpmf_handle h);
 
 /* Host only (no device work, no handle): the degree bins bpmf_create makes for one
@@ -234,11 +247,11 @@ int bpmf_balance_rows(int64_t n, const int64_t* degree, int64_t grid, int32_t* o
 /* Diagnostics: number of rows of `side` on the CUDA-core kernel and on the
  * tensor-core kernel, how many of the former are split and into how many
  * segments, the centring mean, device bytes held, and `balanced`: bit 0 (bit 1)
- * set when the tensor-core rows are dealt to the CTAs of a launch on every SM
- * (on all SMs but one, as bpmf_sweep launches) by the balanced plan -- each row,
- * longest first, to the CTA with the least work so far, made where the plain
- * round-robin order would leave one CTA over 5% above the mean -- instead of
- * round-robin.  NULL outputs are skipped. */
+ * set when the tensor-core rows are dealt to the CTAs of a Gram launch on every SM
+ * (on all SMs but one, as bpmf_sweep launches; two CTAs per SM) by the balanced
+ * plan -- each row, longest first, to the CTA with the least work so far, made
+ * where the plain round-robin order would leave one CTA over 5% above the mean --
+ * instead of round-robin.  NULL outputs are skipped. */
 int bpmf_info(bpmf_handle h, int32_t side, int64_t* n_short, int64_t* n_long, int64_t* n_split,
               int64_t* n_segments, double* rbar, int64_t* device_bytes, int32_t* balanced);
 
@@ -291,7 +304,8 @@ int bpmf_row_stats_noalloc(const float* X, int64_t rows, int32_t K, const double
 /* Human-readable name of a return code (static string). */
 const char* bpmf_strerror(int code);
 
-/* Release everything the handle owns.  NULL-safe. */
+/* Release everything the handle owns (waits for its streams first).  NULL-safe.  The
+ * paper has no counterpart. */
 int bpmf_destroy(bpmf_handle h);
 
 #ifdef __cplusplus

@@ -43,8 +43,8 @@ class bpmf_params(C.Structure):
                 ("seed", C.c_uint64), ("job_id", C.c_uint32), ("burn_in", C.c_int32),
                 ("order", C.c_int32), ("flags", C.c_uint32), ("clip_lo", C.c_double),
                 ("clip_hi", C.c_double), ("long_min_degree", C.c_int32),
-                ("wait_timeout_ms", C.c_int32), ("long_shape_degree", C.c_int32),
-                ("split_degree", C.c_int32), ("rank_one_degree", C.c_int32),
+                ("wait_timeout_ms", C.c_int32), ("split_degree", C.c_int32),
+                ("rank_one_degree", C.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
@@ -74,7 +74,7 @@ def lib():
     L.bpmf_sweep.argtypes = [vp, i32, P(C.c_double), P(C.c_double)]
     L.bpmf_sweep_batch.argtypes = [P(vp), i32, i32]
     L.bpmf_step.argtypes = [vp, i32]
-    L.bpmf_set_tuning.argtypes = [vp, i32, i32, i32, i32]
+    L.bpmf_set_tuning.argtypes = [vp, i32, i32, i32]
     L.bpmf_predict.argtypes = [vp, i64, vp, vp, vp, i32]
     L.bpmf_get_state.argtypes = [vp, vp, vp, vp, P(C.c_uint64)]
     L.bpmf_set_state.argtypes = [vp, vp, vp, vp, C.c_uint64]
@@ -201,12 +201,11 @@ def bpmf_sweep_batch(handles, n_sweeps=1):
     _check(lib().bpmf_sweep_batch(arr, len(handles), int(n_sweeps)), "bpmf_sweep_batch")
 
 
-def bpmf_set_tuning(h, long_min_degree=0, long_shape_degree=0, split_degree=0,
-                    rank_one_degree=0):
+def bpmf_set_tuning(h, long_min_degree=0, split_degree=0, rank_one_degree=0):
     """Re-bin and re-split a live handle's rows under new thresholds (0: library
     defaults; see bpmf_params for negative values)."""
-    _check(lib().bpmf_set_tuning(h, int(long_min_degree), int(long_shape_degree),
-                                 int(split_degree), int(rank_one_degree)), "bpmf_set_tuning")
+    _check(lib().bpmf_set_tuning(h, int(long_min_degree), int(split_degree), int(rank_one_degree)),
+           "bpmf_set_tuning")
 
 
 def bpmf_step(h, phase):

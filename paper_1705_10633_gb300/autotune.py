@@ -1,14 +1,12 @@
 """Autotuner for the row kernels' thresholds, on a job's own data.
 
-The thresholds are the degree from which a row takes the tensor-core kernel
-(below it, the CUDA-core warp-per-row kernel), the mean degree from which a
-tensor-core launch uses the CTA shape with more gather stages and fewer
-factorisation warps, the degree from which a CUDA-core row is split into
-segments done by separate warps, and the degree below which a CUDA-core row takes
-the rank-one route (Sec. 3.1; the GPU analogue of the paper's measured crossover
-between its per-item methods, Sec. 3.2).  At K in 49..64 the first two are tuned
-together (the CUDA-core kernel then holds few rows); below that the split degree
-is tuned first and the rank-one degree second, at the best split.  Each candidate
+The thresholds are the degree from which a row takes the tensor-core route
+(below it, the CUDA-core warp-per-row kernel), the degree from which a CUDA-core
+row is split into segments done by separate warps, and the degree below which a
+CUDA-core row takes the rank-one route (Sec. 3.1; the GPU analogue of the paper's
+measured crossover between its per-item methods, Sec. 3.2).  At K in 49..64 the
+first is tuned (the CUDA-core kernel then holds few rows); below that the split
+degree is tuned first and the rank-one degree second, at the best split.  Each candidate
 is applied to the live handle (`bpmf_set_tuning` bins and splits the rows again),
 the two row phases are run and timed with CUDA events on the handle's stream, and
 the fastest candidate is kept.  The chain's factors, hyper-parameters and sweep
@@ -17,14 +15,12 @@ the chain (the row phases do not touch the running prediction sums).
 """
 from __future__ import annotations
 
-import itertools
 import json
 import os
 
 import numpy as np
 
-LONG_MIN_CANDIDATES = (1, 16, 48, 128)
-SHAPE_CANDIDATES = (256, 1024, 4096, 1 << 30)
+LONG_MIN_CANDIDATES = (1, 16, 24, 48, 128)
 SPLIT_CANDIDATES = (128, 512, 1024, 4096, 1 << 30)
 RANK_ONE_CANDIDATES = (-1, 2, 4)
 
@@ -66,10 +62,9 @@ class TuningCache:
             os.replace(tmp, self.path)
 
 
-def autotune(h, M, N, K, stream, long_min=LONG_MIN_CANDIDATES, shape=SHAPE_CANDIDATES,
-             split=SPLIT_CANDIDATES, rank_one=RANK_ONE_CANDIDATES, reps=2, cache=None,
-             degrees=None):
-    """Returns ((long_min_degree, long_shape_degree, split_degree, rank_one_degree),
+def autotune(h, M, N, K, stream, long_min=LONG_MIN_CANDIDATES, split=SPLIT_CANDIDATES,
+             rank_one=RANK_ONE_CANDIDATES, reps=2, cache=None, degrees=None):
+    """Returns ((long_min_degree, split_degree, rank_one_degree),
     {tuple: ms for one pass of both row phases}).  `stream` is the raw cudaStream_t the
     handle was created with.  0 in a tuple is the library default.  With a `TuningCache`
     and the job's `degrees` (users', movies'), a cached tuning for the same key is applied
@@ -107,15 +102,15 @@ def autotune(h, M, N, K, stream, long_min=LONG_MIN_CANDIDATES, shape=SHAPE_CANDI
 
     try:
         if (K + 15) // 16 * 16 == 64:
-            for lm, sd in itertools.product(long_min, shape):
-                trial((lm, sd, 0, 0))
+            for lm in long_min:
+                trial((lm, 0, 0))
         else:
             for sp in split:
-                trial((0, 0, sp, 0))
-            sp = min(times, key=times.get)[2]
+                trial((0, sp, 0))
+            sp = min(times, key=times.get)[1]
             for r1 in rank_one:
-                if (0, 0, sp, r1) not in times:
-                    trial((0, 0, sp, r1))
+                if (0, sp, r1) not in times:
+                    trial((0, sp, r1))
         best = min(times, key=times.get)
         bp.bpmf_set_tuning(h, *best)
     finally:

@@ -23,7 +23,6 @@ using namespace bpmf;
 namespace {
 
 constexpr int kDefaultLongMinDegree = 48;
-constexpr int kDefaultLongShapeDegree = 1024;
 constexpr int kDefaultSplitDegree = 1024;
 constexpr int kDefaultRankOneDegree = 1;
 constexpr int kDefaultWaitTimeoutMs = 2000;
@@ -75,7 +74,6 @@ struct bpmf_ctx {
     int device = 0;
     int num_sms = 1;
     int64_t long_min = 48;           // binning threshold of the tensor-core kernel
-    int64_t long_shape_degree = 1024;  // mean degree that selects the many-stage CTA shape
     int64_t split_degree = 1024;  // CUDA-core rows with this many ratings are split
     int rank_one_max = 0;  // CUDA-core rows with at most this many ratings: rank-one route
     int row_sms = 1;  // CTAs of the row kernels: all SMs, or all but one while the
@@ -807,7 +805,6 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
     }
     const int64_t long_min = prm.long_min_degree > 0 ? prm.long_min_degree : kDefaultLongMinDegree;
     h->long_min = long_min;
-    h->long_shape_degree = prm.long_shape_degree > 0 ? prm.long_shape_degree : kDefaultLongShapeDegree;
     h->split_degree = prm.split_degree > 0 ? prm.split_degree : kDefaultSplitDegree;
     h->rank_one_max = rank_one_from(prm.rank_one_degree);
     const int64_t* hp[2] = {csr_ptr, device_csc ? nullptr : csc_ptr};
@@ -952,13 +949,12 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
     return BPMF_OK;
 }
 
-int bpmf_set_tuning(bpmf_handle h, int32_t long_min_degree, int32_t long_shape_degree,
-                    int32_t split_degree, int32_t rank_one_degree)
+int bpmf_set_tuning(bpmf_handle h, int32_t long_min_degree, int32_t split_degree,
+                    int32_t rank_one_degree)
 {
     if (!h) return BPMF_EINVAL;
     h->rank_one_max = rank_one_from(rank_one_degree);
     h->long_min = long_min_degree > 0 ? long_min_degree : kDefaultLongMinDegree;
-    h->long_shape_degree = long_shape_degree > 0 ? long_shape_degree : kDefaultLongShapeDegree;
     h->split_degree = split_degree > 0 ? split_degree : kDefaultSplitDegree;
     std::vector<int32_t> order;
     for (int s = 0; s < 2; ++s) {

@@ -119,7 +119,7 @@ def test_product_code_never_touches_the_oracle():
 
 
 def test_set_tuning_and_batch_reject_null(bp):
-    assert bp.lib().bpmf_set_tuning(None, 1, 1, 1, 1) == bp.BPMF_EINVAL
+    assert bp.lib().bpmf_set_tuning(None, 1, 1, 1) == bp.BPMF_EINVAL
     assert bp.lib().bpmf_set_row_timing(None, 1) == bp.BPMF_EINVAL
     arr = (__import__("ctypes").c_void_p * 1)(None)
     assert bp.lib().bpmf_sweep_batch(arr, 1, 1) == bp.BPMF_EINVAL

@@ -24,6 +24,6 @@ def test_cache_round_trip(tmp_path):
     path = str(tmp_path / "tuning.json")
     c = TuningCache(path)
     assert c.get("k") is None
-    c.put("k", (48, 1024, 0, -1))
+    c.put("k", (48, 0, -1))
     c2 = TuningCache(path)
-    assert c2.get("k") == (48, 1024, 0, -1)
+    assert c2.get("k") == (48, 0, -1)

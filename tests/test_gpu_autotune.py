@@ -1,7 +1,7 @@
 """Tuning thresholds: a live handle re-binned by bpmf_set_tuning runs the same chain
 as a handle created with those thresholds; parity with the oracle holds with rows
-split between both kernels and the many-stage CTA shape; the autotuner leaves the
-chain state where it found it and applies a pair from its grid."""
+split between both routes; the autotuner leaves the chain state where it found it and
+applies a candidate from its grid."""
 import numpy as np
 import pytest
 
@@ -25,20 +25,19 @@ def _prob():
                                   long_deg=110)
 
 
-def test_parity_with_mixed_kernels_and_long_shape(bp):
-    # rows below 60 ratings on the CUDA-core kernel, every tensor-core launch in the
-    # many-stage shape (movies average ~270 ratings, the few long users ~110)
-    assert_worst(step_parity(bp, _prob(), sweeps=2, long_min_degree=60, long_shape_degree=50))
+def test_parity_with_mixed_kernels(bp):
+    # rows below 60 ratings on the CUDA-core kernel, the rest (movies average ~270
+    # ratings, the few long users ~110) on the tensor-core route
+    assert_worst(step_parity(bp, _prob(), sweeps=2, long_min_degree=60))
 
 
 def test_set_tuning_equals_creating_with_it(bp):
     import torch
     prob = _prob()
     a = bp.create_from_problem(prob, stream=torch.cuda.Stream().cuda_stream)
-    b = bp.create_from_problem(prob, long_min_degree=60, long_shape_degree=50,
-                               stream=torch.cuda.Stream().cuda_stream)
+    b = bp.create_from_problem(prob, long_min_degree=60, stream=torch.cuda.Stream().cuda_stream)
     try:
-        bp.bpmf_set_tuning(a, 60, 50)
+        bp.bpmf_set_tuning(a, 60)
         assert bp.bpmf_info(a, 0)["n_short"] == bp.bpmf_info(b, 0)["n_short"] > 0
         ra, rb = bp.bpmf_sweep(a, 3), bp.bpmf_sweep(b, 3)
         sa, sb = (bp.bpmf_get_state(x, prob.M, prob.N, prob.K) for x in (a, b))
@@ -60,10 +59,9 @@ def test_autotune_restores_state_and_applies_a_grid_pair(bp):
     try:
         bp.bpmf_sweep(h, 2)
         before = bp.bpmf_get_state(h, prob.M, prob.N, prob.K)
-        best, times = autotune(h, prob.M, prob.N, prob.K, st.cuda_stream, long_min=(1, 60),
-                               shape=(50, 1024))
-        assert best in times and len(times) == 4 and all(t > 0 for t in times.values())
-        assert best[2:] == (0, 0)
+        best, times = autotune(h, prob.M, prob.N, prob.K, st.cuda_stream, long_min=(1, 24, 60))
+        assert best in times and len(times) == 3 and all(t > 0 for t in times.values())
+        assert best[1:] == (0, 0)
         after = bp.bpmf_get_state(h, prob.M, prob.N, prob.K)
         for x, y in zip(before, after):
             np.testing.assert_array_equal(x, y)
@@ -86,13 +84,13 @@ def test_autotune_split_degree_below_k64(bp):
         before = bp.bpmf_get_state(h, prob.M, prob.N, prob.K)
         best, times = autotune(h, prob.M, prob.N, prob.K, st.cuda_stream, split=(32, 1 << 30),
                                rank_one=(-1, 3))
-        sp = min(((0, 0, 32, 0), (0, 0, 1 << 30, 0)), key=times.get)[2]
-        assert sorted(times) == sorted([(0, 0, 32, 0), (0, 0, 1 << 30, 0), (0, 0, sp, -1),
-                                        (0, 0, sp, 3)]) and best in times
+        sp = min(((0, 32, 0), (0, 1 << 30, 0)), key=times.get)[1]
+        assert sorted(times) == sorted([(0, 32, 0), (0, 1 << 30, 0), (0, sp, -1),
+                                        (0, sp, 3)]) and best in times
         after = bp.bpmf_get_state(h, prob.M, prob.N, prob.K)
         for x, y in zip(before, after):
             np.testing.assert_array_equal(x, y)
-        assert (bp.bpmf_info(h, 1)["n_split"] > 0) == (best[2] == 32)
+        assert (bp.bpmf_info(h, 1)["n_split"] > 0) == (best[1] == 32)
         bp.bpmf_sweep(h, 1)
         assert bp.bpmf_status(h) == 0
     finally:

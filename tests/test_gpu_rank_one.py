@@ -97,7 +97,7 @@ def test_set_tuning_moves_rows_between_routes(bp):
         n0 = bp.bpmf_launch_count(a)
         bp.bpmf_step(a, bp.BPMF_PHASE_ROWS_USER)
         one = bp.bpmf_launch_count(a) - n0
-        bp.bpmf_set_tuning(a, 0, 0, 0, 4)
+        bp.bpmf_set_tuning(a, 0, 0, 4)
         n0 = bp.bpmf_launch_count(a)
         bp.bpmf_step(a, bp.BPMF_PHASE_ROWS_USER)
         assert bp.bpmf_launch_count(a) - n0 == one + 1

@@ -82,7 +82,7 @@ def test_split_chain_is_reproducible_and_set_tuning_equals_create(bp, K):
           bp.create_from_problem(prob, split_degree=8, stream=torch.cuda.Stream().cuda_stream),
           bp.create_from_problem(prob, stream=torch.cuda.Stream().cuda_stream)]
     try:
-        bp.bpmf_set_tuning(hs[2], 0, 0, 8)  # grows the segment arrays from none
+        bp.bpmf_set_tuning(hs[2], 0, 8)  # grows the segment arrays from none
         assert bp.bpmf_info(hs[2], 1)["n_segments"] == bp.bpmf_info(hs[0], 1)["n_segments"] > 0
         runs = [(bp.bpmf_sweep(h, 4), bp.bpmf_get_state(h, prob.M, prob.N, K)) for h in hs]
         for r, st in runs[1:]:

@@ -44,11 +44,9 @@ def test_long_rows_tensor_core_parity(bp, K, long_min):
     assert_worst(step_parity(bp, prob, sweeps=2, long_min_degree=long_min))
 
 
-def test_long_row_shape_parity(bp):
-    # 40 movies with ~3,000 ratings each: the movie side's mean degree selects the CTA
-    # shape with 7 gather stages, 128 gather threads and 2 factorisation warps (6, 64 and
-    # 4 under the BF16 Gram); rows span 1-3 chunks of
-    # 1024 ratings (so a row's accumulator is drained more than once)
+def test_long_rows_in_several_chunks_parity(bp):
+    # 40 movies with ~3,000 ratings each: rows span 1-3 accumulation chunks of 1024
+    # ratings, so the drain sums a row's Gram over several TMEM accumulators
     prob = workloads.random_small(8000, 40, 64, 150000, seed=31, n_test=300)
     deg = prob.col_degrees()
     assert deg.mean() >= 1024 and deg.max() > 2048
