@@ -8,6 +8,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+@pytest.fixture(scope="session")
+def config3_problem():
+    """The 480,000 x 18,000, 1e8-rating, K = 64 workload, generated once per session."""
+    import workloads
+    return workloads.config3()
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (runs the sm_103a library)")
     config.addinivalue_line("markers", "slow: long CPU test")

@@ -302,12 +302,13 @@ def test_torch_caching_allocator_hook(bp):
         bp.bpmf_destroy(h)
 
 
-def full_size_sampled_rows(bp, prob):
+def full_size_sampled_rows(bp, prob, flags=0, tol=ROW_TOL):
     """One sweep of a full-size workload, each half-sweep checked on sampled rows (200
     uniform, the 8 longest and 8 shortest) against the oracle started from the GPU's
-    state: statistics, Normal-Wishart draw, factors and conditional means."""
+    state: statistics, Normal-Wishart draw, factors and conditional means (per row,
+    norm-wise within `tol`)."""
     K = prob.K
-    h = bp.create_from_problem(prob, flags=bp.BPMF_DEBUG_MEANS, stream=bp.torch_stream())
+    h = bp.create_from_problem(prob, flags=flags | bp.BPMF_DEBUG_MEANS, stream=bp.torch_stream())
     rng = np.random.default_rng(0)
     try:
         bp.bpmf_sweep(h, 1)  # leave the initial state
@@ -340,8 +341,8 @@ def full_size_sampled_rows(bp, prob):
             em = rowwise_rel(Mg[sample], orc.get_means(side)[sample])
             worst = sorted(zip(ex, deg[sample]), reverse=True)[:5]
             print("side %d worst (err, degree):" % side, [("%.2e" % e, int(d)) for e, d in worst])
-            assert ex.max() <= ROW_TOL, (side, worst)
-            assert em.max() <= ROW_TOL, (side, em.max(), deg[sample[np.argmax(em)]])
+            assert ex.max() <= tol, (side, worst)
+            assert em.max() <= tol, (side, em.max(), deg[sample[np.argmax(em)]])
             orc.set_factors(side, Xg)
         assert bp.bpmf_status(h) == 0
     finally:

@@ -156,15 +156,17 @@ def test_wait_timeout_reports_status_and_context_survives(bp):
         bp.bpmf_destroy(h)
 
 
-@pytest.fixture(scope="module")
-def config3():
-    return workloads.config3()
-
-
-def test_full_size_config3_sampled_rows(bp, config3):
+def test_full_size_config3_sampled_rows(bp, config3_problem):
     """One sweep of the 480,000 x 18,000, 1e8-rating, K = 64 workload (the bench
     configuration), each half-sweep checked on sampled rows against the oracle."""
-    full_size_sampled_rows(bp, config3)
+    full_size_sampled_rows(bp, config3_problem)
+
+
+def test_full_size_config3_sampled_rows_bf16(bp, config3_problem):
+    """The same on the BF16 Gram, where rows of up to 2.7e5 ratings put the most BF16
+    rounding into one precision matrix: sampled rows (the 8 longest among them) within
+    the BF16 path's 1e-2 per row of the FP64 oracle."""
+    full_size_sampled_rows(bp, config3_problem, flags=bp.BPMF_BF16_GRAM, tol=BF16_ROW_TOL)
 
 
 def test_row_launch_timing(bp):
