@@ -72,8 +72,11 @@ def test_row_work_figures_match_loop_counts():
     K = 64
     # one rating adds one outer product (K x K multiply-adds) and one scaled row (K)
     assert bench.row_gram_flops(1, K) == 2 * (K * K + K)
-    assert bench.row_gather_bytes(1, 0, K) == 4 + 4 + 2 * 2 * K
-    assert bench.row_gather_bytes(0, 1, K) == 2 * 8 + 4 * K + 2 * 2 * K
+    # the symmetric count: the lower half of the outer product (K(K+1)/2 multiply-adds)
+    assert bench.row_sym_gram_flops(1, K) == 2 * (K * (K + 1) / 2 + K)
+    # the gathered 16-bit rows: FP16 hi and lo (2 B each per entry), or BF16 alone
+    assert bench.gathered_bytes(1, K) == 2 * 2 * K
+    assert bench.gathered_bytes(1, K, bf16=True) == 2 * K
 
 
 def test_l2_note_states_how_inputs_stand_to_l2():
