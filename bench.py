@@ -4,13 +4,14 @@
 One step = one full Gibbs sweep of Alg. 1 (hyper(V), every movie, hyper(U),
 every user, test predictions + RMSE) over the 480,000 x 18,000 rating matrix
 with 1e8 ratings at K = 64 (synthetic, seeded; ``workloads.config3``).
-value = (M + N) x sweeps / device time, max over ranks, summed over ranks.
+value = (M + N) x sweeps / device time of the slowest rank.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
-Under torchrun (N > 1) every rank runs an independent chain (replicas: the
-sweep itself is not sharded across GPUs here), so scaling is weak.
-``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+Under torchrun (N > 1) the ranks run one chain together: each rank updates a cost-
+balanced range of the rows of both sides and the ranks all-gather the updated rows
+after every half-sweep (NCCL), so the total work is fixed and scaling is strong.
+``--impl reference`` times the FP64 CPU oracle on bounded blocks of the same
 workload on the host cores (rank 0 only) and prints the same metric.
 """
 from __future__ import annotations
@@ -487,6 +488,88 @@ def run_native(args):
         print(json.dumps(out), flush=True)
 
 
+def run_sharded(args):
+    """N > 1 ranks, one chain: each rank updates a cost-balanced range of the rows of
+    both sides and the ranks all-gather the updated rows after every half-sweep
+    (paper_1705_10633_gb300.shard); every rank holds the whole problem.  The total work
+    is one chain whatever N: strong scaling.  value = (M + N) x sweeps / the slowest
+    rank's time."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1705_10633_gb300 as bp
+    from paper_1705_10633_gb300.shard import HandleBackend, ShardedChain
+
+    rank, world, local = dist_env()
+    device_x = args.exchange == "device"
+    torch.cuda.set_device(local if device_x else local % max(1, torch.cuda.device_count()))
+    dist_init(world, "nccl" if device_x else "gloo")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    prob = make_problem(args, 0)  # one chain: every rank builds the same problem
+    K = prob.K
+    flags = bp.BPMF_BF16_GRAM if args.bf16 else 0
+    params = bp.bpmf_default_params(alpha=prob.alpha, seed=prob.seed, burn_in=prob.burn_in,
+                                    flags=flags)
+
+    def sync():
+        torch.cuda.synchronize(dev)
+        barrier(world, dev.index if device_x else None)
+        torch.cuda.synchronize(dev)
+
+    # the handle's stream is torch's current stream, so the collectives (ordered on the
+    # current stream) and the handle's copies and kernels follow one order
+    t_e0 = time.perf_counter()
+    h = bp.bpmf_create(prob.M, prob.N, K, prob.csr_ptr, prob.csr_col, prob.csr_val,
+                       test_i=prob.test_i, test_j=prob.test_j, test_r=prob.test_r, params=params,
+                       stream=bp.torch_stream())
+    try:
+        chain = ShardedChain(HandleBackend(bp, h, prob.M, prob.N, K, prob.degrees(),
+                                           prob.col_degrees(), device=device_x), rank, world)
+        chain.sweep(args.warmup)
+        sync()
+        n0 = bp.bpmf_launch_count(h)
+        clocks = ClockSampler(dev.index)
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        chain.sweep(args.steps)
+        e1.record()
+        sync()
+        clk = clocks.stop()
+        total_ms = e0.elapsed_time(e1)
+        launches = bp.bpmf_launch_count(h) - n0
+        rs, ra = bp.bpmf_sweep(h, 0)  # the RMSE read back ends the end-to-end region
+        t_e1 = time.perf_counter()
+        assert bp.bpmf_status(h) == 0
+    finally:
+        bp.bpmf_destroy(h)
+    max_ms = reduce_over_ranks(total_ms, world, "max", dev.index if device_x else None)
+    value = (prob.M + prob.N) * args.steps / (max_ms / 1e3)
+    e2e_s = reduce_over_ranks(t_e1 - t_e0, world, "max", dev.index if device_x else None)
+    out = {"metric": METRIC % K, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
+           "scaling": "strong", "vs_baseline": None,
+           "dtype": "bf16-gram/f32" if args.bf16 else "f32", "data": "synthetic",
+           "config": {"workload": prob.name, "M": prob.M, "N": prob.N, "K": K, "nnz": prob.nnz,
+                      "test": prob.T, "l2": l2_note(prob.nnz),
+                      "parallelism": "sharded rows x%d (%s all-gather after each half-sweep)"
+                                     % (world, "NCCL" if device_x else "gloo host"),
+                      "ranges": {"users": chain.ranges[0], "movies": chain.ranges[1]},
+                      "rmse_sample": finite_or_none(rs), "rmse_avg": finite_or_none(ra)},
+           "clocks": clk, "gpu_launches": int(launches),
+           "e2e": {"value": round((prob.M + prob.N) * (args.warmup + args.steps) / e2e_s, 1),
+                   "unit": UNIT,
+                   "h2d_bytes_per_step": int(8 * (prob.M + 1) + 8 * prob.nnz + 12 * prob.T)
+                                         // (args.warmup + args.steps),
+                   "d2h_bytes_per_step": 16 // (args.warmup + args.steps),
+                   "note": "wall clock of bpmf_create from host arrays, the warm-up and timed "
+                           "sweeps with their exchanges, and the RMSE read back; slowest rank"}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    dist.destroy_process_group()
+
+
 def run_e2e(args, prob, bp, torch, dev, stream, world, local):
     """Whole job through the public C ABI from host buffers: create (host -> device
     copies of the ratings and test set, column view, bins, initial draw), then
@@ -782,6 +865,9 @@ def main(argv=None):
                     help="the same for --impl reference (one oracle step per bench step)")
     ap.add_argument("--log-jsonl", default=None,
                     help="append one JSON record per sweep (sweep, RMSEs, time) after the run")
+    ap.add_argument("--exchange", choices=["device", "host"], default="device",
+                    help="N > 1: all-gather device rows over NCCL (one GPU per rank), or host "
+                         "copies over gloo (ranks may then share a GPU)")
     ap.add_argument("--fig3", action="store_true",
                     help="row update time against degree for every route (the paper's Fig. 3)")
     args = ap.parse_args(argv)
@@ -799,6 +885,8 @@ def main(argv=None):
         run_batched(args)
     elif args.config == 5:
         run_serving(args)
+    elif dist_env()[1] > 1:
+        run_sharded(args)
     else:
         run_native(args)
 

@@ -218,6 +218,35 @@ int bpmf_debug_means(bpmf_handle h, int32_t side, float* out);
  * Syncs the handle's stream. */
 int bpmf_status(bpmf_handle h);
 
+/*
+ * Sharded sweeps (one process per GPU; Sec. 4.2 and 4.3 of the paper spread the items
+ * over nodes by a per-item cost of a fixed part plus a part per rating, and send the
+ * updated items to the nodes that need them after each half-sweep):
+ *
+ * bpmf_set_shard restricts the row phases of `side` to rows [row_begin, row_end)
+ * (every row again with [0, rows)); the rows are binned and planned again (host sort
+ * of the degrees kept from bpmf_create, host-to-device copies waited for).  The hyper
+ * step still reduces over every row of the side and the prediction step over every
+ * test point, so every shard must hold the whole side before them: a caller exchanges
+ * the rows each shard updated after every row phase (bpmf_get_rows, a collective of its
+ * own, bpmf_put_rows).  A row's update depends only on the other side, the side's
+ * hyper-parameters and (seed, sweep, row), so shards that exchange this way run the
+ * same chain, bit for bit, as one handle over all rows.  BPMF_EINVAL for a bad side or
+ * range.
+ *
+ * bpmf_get_rows copies rows [row_begin, row_end) of U (side 0) or V (side 1) to out,
+ * packed (K floats a row); bpmf_put_rows overwrites them from in and refreshes their
+ * 16-bit copies for the tensor-core Gram.  where = 0: host buffer (the call waits for
+ * the copy); where = 1: device buffer, the copy ordered on the handle's stream.  The
+ * paper's exchange uses MPI or GASPI between nodes; here the caller's collective (NCCL,
+ * or gloo on host copies) moves the rows.
+ */
+int bpmf_set_shard(bpmf_handle h, int32_t side, int64_t row_begin, int64_t row_end);
+int bpmf_get_rows(bpmf_handle h, int32_t side, int64_t row_begin, int64_t row_end, float* out,
+                  int32_t where);
+int bpmf_put_rows(bpmf_handle h, int32_t side, int64_t row_begin, int64_t row_end,
+                  const float* in, int32_t where);
+
 /* Host only (no device work, no handle): the degree bins bpmf_create makes for one
  * side.  ptr: rows + 1 offsets of the side's ratings (ptr[0] = 0, non-decreasing);
  * rows with at least long_min ratings form the tensor-core bin (long_min <= 0: no such

@@ -91,6 +91,9 @@ def lib():
     L.bpmf_set_row_timing.argtypes = [vp, i32]
     L.bpmf_row_launch_ms.argtypes = [vp, P(C.c_float), P(C.c_float), P(C.c_float)]
     L.bpmf_row_stats_noalloc.argtypes = [vp, i64, i32, vp, vp, vp, vp]
+    L.bpmf_set_shard.argtypes = [vp, i32, i64, i64]
+    L.bpmf_get_rows.argtypes = [vp, i32, i64, i64, vp, i32]
+    L.bpmf_put_rows.argtypes = [vp, i32, i64, i64, vp, i32]
     L.bpmf_strerror.argtypes = [C.c_int]
     L.bpmf_strerror.restype = C.c_char_p
     L.bpmf_destroy.argtypes = [vp]
@@ -337,6 +340,36 @@ def bpmf_row_stats_noalloc(X_ptr, rows, K, shift_ptr, mean_ptr, S_ptr, stream=No
            "bpmf_row_stats_noalloc")
 
 
+def bpmf_set_shard(h, side, row_begin, row_end):
+    """Restrict the row phases of `side` to rows [row_begin, row_end)."""
+    _check(lib().bpmf_set_shard(h, int(side), int(row_begin), int(row_end)), "bpmf_set_shard")
+
+
+def bpmf_get_rows(h, side, row_begin, row_end, K, out_ptr=None):
+    """Rows [row_begin, row_end) of U (side 0) or V (side 1): a new host array, or into the
+    device buffer at out_ptr (K floats a row, ordered on the handle's stream)."""
+    if out_ptr is not None:
+        _check(lib().bpmf_get_rows(h, int(side), int(row_begin), int(row_end), out_ptr, 1),
+               "bpmf_get_rows")
+        return None
+    out = np.empty((max(int(row_end) - int(row_begin), 0), int(K)), dtype=np.float32)
+    _check(lib().bpmf_get_rows(h, int(side), int(row_begin), int(row_end), _ptr(out), 0),
+           "bpmf_get_rows")
+    return out
+
+
+def bpmf_put_rows(h, side, row_begin, row_end, rows=None, in_ptr=None):
+    """Overwrite rows [row_begin, row_end) of U or V from a host array (n x K) or from the
+    device buffer at in_ptr."""
+    if in_ptr is not None:
+        _check(lib().bpmf_put_rows(h, int(side), int(row_begin), int(row_end), in_ptr, 1),
+               "bpmf_put_rows")
+        return
+    rows = np.ascontiguousarray(rows, dtype=np.float32)
+    _check(lib().bpmf_put_rows(h, int(side), int(row_begin), int(row_end), _ptr(rows), 0),
+           "bpmf_put_rows")
+
+
 def bpmf_destroy(h):
     if h:
         _check(lib().bpmf_destroy(h), "bpmf_destroy")
@@ -359,6 +392,6 @@ EXPORTED = ["bpmf_default_params", "bpmf_create", "bpmf_sweep", "bpmf_sweep_batc
             "bpmf_get_state", "bpmf_set_state", "bpmf_get_accum", "bpmf_set_accum",
             "bpmf_get_stats", "bpmf_debug_means", "bpmf_status", "bpmf_info", "bpmf_launch_count",
             "bpmf_set_row_timing", "bpmf_row_launch_ms", "bpmf_bin_rows", "bpmf_balance_rows",
-            "bpmf_row_stats_noalloc",
+            "bpmf_row_stats_noalloc", "bpmf_set_shard", "bpmf_get_rows", "bpmf_put_rows",
             "bpmf_strerror",
             "bpmf_destroy"]

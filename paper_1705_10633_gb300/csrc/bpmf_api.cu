@@ -29,6 +29,9 @@ constexpr int kDefaultWaitTimeoutMs = 2000;
 
 struct DevSide {
     int64_t rows = 0;
+    // rows this handle updates in its row phases: [shard_lo, shard_hi) (all rows unless
+    // bpmf_set_shard restricted them); the hyper step always reduces over every row
+    int64_t shard_lo = 0, shard_hi = 0;
     int64_t* ptr = nullptr;
     int32_t* idx = nullptr;
     float* val = nullptr;
@@ -436,8 +439,11 @@ int plan_long_bin(bpmf_ctx* h, DevSide& d, const std::vector<int32_t>& order)
 // the split of its long CUDA-core rows and the balanced plan of its tensor-core rows.
 int bin_side(bpmf_ctx* h, DevSide& d, std::vector<int32_t>& order)
 {
-    bin_rows(d.rows, d.ptr_h.data(), h->tc ? h->long_min : INT64_MAX, order, &d.n_short, &d.n_long,
-             &d.long_ratings);
+    // the rows of this handle's shard (every row unless restricted), as global row ids
+    bin_rows(d.shard_hi - d.shard_lo, d.ptr_h.data() + d.shard_lo, h->tc ? h->long_min : INT64_MAX,
+             order, &d.n_short, &d.n_long, &d.long_ratings);
+    if (d.shard_lo)
+        for (int32_t& r : order) r += (int32_t)d.shard_lo;
     if (h->tc && d.n_long > h->gram_cap) {
         // the scratch grows to the longest long bin; the old one is no longer referenced
         // (the stream is idle here: binning waits for it)
@@ -448,7 +454,7 @@ int bin_side(bpmf_ctx* h, DevSide& d, std::vector<int32_t>& order)
         if (!alloc_n(h, &h->gram, (size_t)d.n_long * kGramSlotFloats)) return BPMF_ENOMEM;
         h->gram_cap = d.n_long;
     }
-    cudaError_t e = cudaMemcpyAsync(d.bin_rows, order.data(), sizeof(int32_t) * d.rows,
+    cudaError_t e = cudaMemcpyAsync(d.bin_rows, order.data(), sizeof(int32_t) * order.size(),
                                     cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return BPMF_ECUDA;
     const int rc = plan_segments(h, d, order);  // waits for the stream: `order` may be reused
@@ -818,6 +824,8 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
     for (int s = 0; s < 2 && rc == BPMF_OK; ++s) {
         DevSide& d = h->side[s];
         d.rows = rows[s];
+        d.shard_lo = 0;
+        d.shard_hi = d.rows;
         d.tag_init = tag_word(s == 0 ? kTagInitU : kTagInitV, prm.job_id);
         d.tag_row = tag_word(s == 0 ? kTagRowU : kTagRowV, prm.job_id);
         d.tag_hyper = tag_word(s == 0 ? kTagHyperU : kTagHyperV, prm.job_id);
@@ -1349,6 +1357,68 @@ int bpmf_launch_count(bpmf_handle h, int64_t* launches)
     if (!h || !launches) return BPMF_EINVAL;
     *launches = h->launches;
     return BPMF_OK;
+}
+
+int bpmf_set_shard(bpmf_handle h, int32_t side, int64_t row_begin, int64_t row_end)
+{
+    if (!h || (side != 0 && side != 1)) return BPMF_EINVAL;
+    DevSide& d = h->side[side];
+    if (row_begin < 0 || row_end < row_begin || row_end > d.rows) return BPMF_EINVAL;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {  // no launch may use the old bins
+        cudaGetLastError();
+        return BPMF_ECUDA;
+    }
+    d.shard_lo = row_begin;
+    d.shard_hi = row_end;
+    std::vector<int32_t> order;
+    const int rc = bin_side(h, d, order);
+    // the captured sweep holds the old bins' launch shapes
+    if (h->sweep_graph) cudaGraphExecDestroy(h->sweep_graph);
+    h->sweep_graph = nullptr;
+    h->graph_state = 0;
+    return rc;
+}
+
+int bpmf_get_rows(bpmf_handle h, int32_t side, int64_t row_begin, int64_t row_end, float* out,
+                  int32_t where)
+{
+    if (!h || (side != 0 && side != 1) || (where != 0 && where != 1)) return BPMF_EINVAL;
+    const DevSide& d = h->side[side];
+    if (row_begin < 0 || row_end < row_begin || row_end > d.rows) return BPMF_EINVAL;
+    const int64_t n = row_end - row_begin;
+    if (n == 0) return BPMF_OK;
+    if (!out) return BPMF_EINVAL;
+    cudaError_t e = cudaMemcpy2DAsync(out, sizeof(float) * h->K, d.X + row_begin * h->kp,
+                                      sizeof(float) * h->kp, sizeof(float) * h->K, (size_t)n,
+                                      where ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                      h->stream);
+    if (e == cudaSuccess && where == 0) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) cudaGetLastError();
+    return cuda_rc(e);
+}
+
+int bpmf_put_rows(bpmf_handle h, int32_t side, int64_t row_begin, int64_t row_end, const float* in,
+                  int32_t where)
+{
+    if (!h || (side != 0 && side != 1) || (where != 0 && where != 1)) return BPMF_EINVAL;
+    DevSide& d = h->side[side];
+    if (row_begin < 0 || row_end < row_begin || row_end > d.rows) return BPMF_EINVAL;
+    const int64_t n = row_end - row_begin;
+    if (n == 0) return BPMF_OK;
+    if (!in) return BPMF_EINVAL;
+    // the padding columns K .. kp-1 stay zero; the 16-bit split the other side's Gram
+    // gathers follows the new rows
+    cudaError_t e = cudaMemcpy2DAsync(d.X + row_begin * h->kp, sizeof(float) * h->kp, in,
+                                      sizeof(float) * h->K, sizeof(float) * h->K, (size_t)n,
+                                      where ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                      h->stream);
+    if (e == cudaSuccess && d.Xh)
+        e = launch_split_factors(d.X + row_begin * h->kp, n, h->kp, d.Xh + row_begin * h->kp,
+                                 d.Xl + row_begin * h->kp, (h->p.flags & BPMF_BF16_GRAM) ? 1 : 0,
+                                 h->stream);
+    if (e == cudaSuccess && where == 0) e = cudaStreamSynchronize(h->stream);  // host buffer
+    if (e != cudaSuccess) cudaGetLastError();
+    return cuda_rc(e);
 }
 
 int bpmf_bin_rows(int64_t rows, const int64_t* ptr, int64_t long_min, int32_t* order_out,
