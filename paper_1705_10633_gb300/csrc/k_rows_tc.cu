@@ -22,13 +22,14 @@
 // Two CTAs per SM (each with half of the SM's TMEM and shared memory), persistent
 // over the rows (dealt round-robin, or by the host's balanced plan where round-robin
 // would be uneven).  Each CTA is one pipeline; two of them keep the tensor core busy
-// while one MMA issuer waits for a stage or commits.  Warp roles (8 warps):
+// while one MMA issuer waits for a stage or commits.  Warp roles (12 warps):
 //   warp 0        MMA issuer (one lane) and TMEM owner (2 accumulators)
 //   warp 1        prefetch: row descriptors (row, first, last rating, slot) into a
 //                 ring, and every stage's rating indices and values into a second
 //                 ring, far ahead of use (cp.async, mbarrier completion)
-//   warps 2-3     gather: cp.async of the 128-B h and l rows of each rating into the
+//   warps 2-3, 8-9  gather: cp.async of the 128-B h and l rows of each rating into the
 //                 swizzled atoms; the stage barrier completes when they land
+//   warps 10-11   idle (the last warpgroup's spare warps give their registers away)
 //   warps 4-7     drain (TMEM lane quarters 0-3): TMEM -> registers, summed over the
 //                 row's accumulation chunks; at the row's end the L^T H rows go
 //                 through a shared staging buffer so the H^T H rows can add L^T H and
@@ -61,9 +62,12 @@ constexpr int kN = 80;                // MMA N: 64 h columns + the ratings atom'
 constexpr uint32_t kTileBytes = kStageRatings * 128;  // one atom: 64 ratings x 64 halves
 constexpr uint32_t kStageBytes = 3 * kTileBytes;      // l, h, ratings (24 KB)
 constexpr int kNStage = 3;
-constexpr int kGatherWarps = 2;
+constexpr int kGatherWarps = 4;
 constexpr int kGather = 32 * kGatherWarps;
-constexpr int kWarps = 8;
+constexpr int kWarps = 12;
+// setmaxnreg is executed by whole warpgroups (four consecutive warps): the CTA is made of
+// full ones, and each warpgroup takes one register share
+static_assert(kWarps % 4 == 0, "whole warpgroups");
 constexpr int kThreads = kWarps * 32;
 constexpr uint32_t kStagingFloats = 64 * 64 + 64;  // L^T H rows (sw64 layout) and L^T r
 
@@ -78,14 +82,15 @@ constexpr uint32_t kOffMisc = kOffBars + kNumBars * 8;
 constexpr uint32_t kSmemBytes = kOffMisc + 16 + 1024;  // + alignment slack
 static_assert(kGramCtasPerSm * (kSmemBytes + 1024) <= 233472, "shared memory of the SM's CTAs");
 static_assert(kNumAcc * kAccStride <= kTmemCols, "TMEM columns");
-// Registers: the launch gives 128 a thread (two CTAs of 256 threads fill the register
-// file).  Each SM sub-partition holds one producer warp (MMA, prefetch or gather) and one
-// drain warp of the CTA, and setmaxnreg moves registers between them: producers drop to
+// Registers: the launch gives 80 a thread (two CTAs of 384 threads within the register
+// file).  A warpgroup puts one warp on each SM sub-partition, so a sub-partition holds, of
+// each CTA, two producer or idle warps (warpgroups 0 and 2) and one drain warp (warpgroup 1),
+// and setmaxnreg moves registers between them within it: producers and idle warps drop to
 // kProdRegs, drain warps rise to kDrainRegs.
-constexpr int kLaunchRegs = 128;
-constexpr int kProdRegs = 80;
-constexpr int kDrainRegs = 176;
-static_assert(kProdRegs + kDrainRegs <= 2 * kLaunchRegs, "registers per sub-partition");
+constexpr int kLaunchRegs = 80;
+constexpr int kProdRegs = 48;
+constexpr int kDrainRegs = 144;
+static_assert(2 * kProdRegs + kDrainRegs <= 3 * kLaunchRegs, "registers per sub-partition");
 
 // Instruction descriptor of kind::f16: D = F32, A = B = F16 (or BF16), both MN-major.
 constexpr uint32_t make_idesc(int M, int N)
@@ -340,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, kGramCtasPerSm) rows_gram_kernel(Row
     const uint32_t tmem_base = *tmem_slot;
     constexpr int64_t kChunkRatings = (int64_t)kChunkStages * kStageRatings;
 
-    // ======================= gather (warps 2-3) =======================
+    // ======================= gather (warps 2-3, 8-9) =======================
     // gt: this thread's index among the kGather gather threads
     constexpr int kRps = kGather / 16, kRpsB = kGather / 8;  // ratings per copy round
     constexpr int kCopies = kBf16 ? 512 / kGather : 1024 / kGather;
@@ -417,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, kGramCtasPerSm) rows_gram_kernel(Row
         cp_async_wait_all();
     };
 
-    if (warp < 4) {
+    if (warp < 4 || warp >= 8) {
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kProdRegs) : "memory");
         if (warp == 0) {
             // ======================= MMA issuer =======================
@@ -537,8 +542,8 @@ __global__ void __launch_bounds__(kThreads, kGramCtasPerSm) rows_gram_kernel(Row
                 }
             }
             cp_async_wait_all();
-        } else {
-            gather_role(tid - 64);
+        } else if (warp < 10) {
+            gather_role(warp < 4 ? tid - 64 : 64 + tid - 256);
         }
     } else {
         // ======================= TMEM drain (warps 4-7) =======================
@@ -658,7 +663,7 @@ static cudaError_t launch_gram(const RowArgs& a, int num_sms, cudaStream_t s)
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, rows_gram_kernel<kBf16>);
     if (e != cudaSuccess) return e;
-    const long split = 32L * (4 * kProdRegs + 4 * kDrainRegs);
+    const long split = 32L * (8 * kProdRegs + 4 * kDrainRegs);
     if (split > (long)fa.numRegs * kThreads) return cudaErrorInvalidConfiguration;
     const int64_t ctas = (int64_t)kGramCtasPerSm * num_sms;
     const int64_t grid = a.nrows < ctas ? a.nrows : ctas;
