@@ -710,31 +710,37 @@ def run_batched(args):
 
 def run_serving(args):
     """Serving loop (continuous batching): jobs arrive as a Poisson process (rate
-    args.rate per second for args.duration seconds), each drawn from a pool of
-    config-4-sized problems with its own chain seed, asking for args.job_sweeps sweeps
-    and predictions at 1,000 query points.  The same arrival sequence is served with
-    up to args.slots jobs resident and with one job at a time.  Prints one JSON line
-    (latency percentiles, aggregate rows/s) for each form side by side."""
+    args.rate per second for args.duration seconds), each a fresh problem drawn from
+    config 4's distribution with its own chain seed, asking for args.job_sweeps sweeps
+    and predictions at 1,000 query points.  The same arrival sequence is served three
+    ways: up to args.slots jobs resident under a 150 GB budget (memory never binds),
+    the same slots under a budget that binds (args.mem_budget_gb, by default a quarter
+    of the first run's peak, at least the largest job), and one job at a time.  Prints
+    one JSON line with latency and queue-wait percentiles, aggregate rows/s, peak
+    device memory and how many jobs waited for memory, for each form side by side."""
     import torch
 
+    import paper_1705_10633_gb300 as bp
     import workloads
-    from paper_1705_10633_gb300.serve import Job, Server, latency_percentiles
+    from paper_1705_10633_gb300.serve import Job, Server, latency_percentiles, queue_wait_percentiles
 
     torch.cuda.set_device(0)
-    pool = workloads.config4(seed=5, n_jobs=args.jobs)
     rng = np.random.default_rng(17)
     t, arrivals = 0.0, []
     while True:
         t += rng.exponential(1.0 / args.rate)
         if t > args.duration:
             break
-        prob = pool[int(rng.integers(len(pool)))]
+        prob = workloads.config4_job(rng, 5000 + len(arrivals))
         qi = rng.integers(0, prob.M, 1000).astype(np.int32)
         qj = rng.integers(0, prob.N, 1000).astype(np.int32)
         arrivals.append((t, prob, qi, qj, int(rng.integers(1 << 30))))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    largest = max(bp.bpmf_device_bytes(a[1].M, a[1].N, a[1].K, a[1].csr_ptr, a[1].csr_col,
+                                       len(a[1].test_i), num_sms=sms) for a in arrivals)
 
-    def serve(slots):
-        srv = Server(memory_limit=150e9, max_active=slots, sweeps_per_round=5)
+    def serve(slots, budget):
+        srv = Server(memory_limit=budget, max_active=slots, sweeps_per_round=5)
         futs, t0 = [], time.perf_counter()
         for at, prob, qi, qj, seed in arrivals:
             delay = t0 + at - time.perf_counter()
@@ -746,27 +752,40 @@ def run_serving(args):
         srv.close()
         span = max(r.finished_at for r in res) - min(r.submitted_at for r in res)
         rows = sum((a[1].M + a[1].N) * args.job_sweeps for a in arrivals)
-        lat = latency_percentiles(res)
+        lat, wait = latency_percentiles(res), queue_wait_percentiles(res)
         return {"p50_s": round(lat["p50"], 4), "p99_s": round(lat["p99"], 4),
+                "queue_wait_p50_s": round(wait["p50"], 4),
+                "queue_wait_p99_s": round(wait["p99"], 4),
                 "rows_per_s": round(rows / span, 1), "jobs_per_s": round(len(res) / span, 2),
                 "makespan_s": round(span, 3), "rounds": srv.rounds,
-                "peak_memory_gb": round(srv.peak_memory / 1e9, 3)}, res
+                "memory_budget_gb": round(budget / 1e9, 3),
+                "peak_memory_gb": round(srv.peak_memory / 1e9, 3),
+                "jobs_waited_for_memory": srv.memory_waits}, res
 
-    batched, rb = serve(args.slots)
-    alone, ra = serve(1)
-    same = all(np.array_equal(x.predictions, y.predictions) for x, y in zip(rb, ra))
+    batched, rb = serve(args.slots, 150e9)
+    budget = (args.mem_budget_gb * 1e9 if args.mem_budget_gb
+              else max(largest, 0.25 * batched["peak_memory_gb"] * 1e9))
+    bound, rm = serve(args.slots, budget)
+    alone, ra = serve(1, 150e9)
+    same = all(np.array_equal(x.predictions, y.predictions) and
+               np.array_equal(x.predictions, z.predictions) for x, y, z in zip(rb, ra, rm))
     out = {"metric": "serving job latency p50/p99 (s) and aggregate rows/s",
            "value": batched["p99_s"], "unit": "s (p99 job latency)", "n_gpus": 1,
            "higher_is_better": False, "data": "synthetic",
            "config": {"workload": "config5_poisson", "rate_jobs_per_s": args.rate,
                       "duration_s": args.duration, "jobs": len(arrivals),
                       "sweeps_per_job": args.job_sweeps, "queries_per_job": 1000,
-                      "pool": "%d config-4-sized problems" % len(pool), "slots": args.slots,
-                      "sweeps_per_round": 5, "memory_budget_gb": 150},
-           "batched": batched, "one_at_a_time": alone,
+                      "jobs_from": "each a fresh draw from config 4's distribution",
+                      "rows_per_job_mean": round(float(np.mean([a[1].M + a[1].N
+                                                                for a in arrivals])), 1),
+                      "ratings_per_job_mean": round(float(np.mean([a[1].nnz
+                                                                   for a in arrivals])), 1),
+                      "largest_job_gb": round(largest / 1e9, 3), "slots": args.slots,
+                      "sweeps_per_round": 5},
+           "batched": batched, "batched_memory_bound": bound, "one_at_a_time": alone,
            "p99_ratio_alone_over_batched": round(alone["p99_s"] / batched["p99_s"], 3),
            "rows_per_s_ratio": round(batched["rows_per_s"] / alone["rows_per_s"], 3),
-           "same_predictions_alone_and_in_mix": same}
+           "same_predictions_in_all_three": same}
     print(json.dumps(out), flush=True)
 
 
@@ -845,11 +864,13 @@ def main(argv=None):
     ap.add_argument("--config", type=int, choices=[1, 2, 3, 4, 5], default=3,
                     help="4: batched independent jobs (bpmf_sweep_batch against one at a time); "
                          "5: serving loop with Poisson arrivals")
-    ap.add_argument("--jobs", type=int, default=256, help="jobs of config 4 (pool size for 5)")
+    ap.add_argument("--jobs", type=int, default=256, help="config 4: number of jobs")
     ap.add_argument("--rate", type=float, default=50.0, help="config 5: arrivals per second")
     ap.add_argument("--duration", type=float, default=4.0, help="config 5: arrival window (s)")
     ap.add_argument("--job-sweeps", type=int, default=100, help="config 5: sweeps per job")
     ap.add_argument("--slots", type=int, default=64, help="config 5: jobs resident at once")
+    ap.add_argument("--mem-budget-gb", type=float, default=None,
+                    help="config 5: device memory budget of the memory-bound run")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--bf16", action="store_true",
                     help="BF16-input tensor-core Gram (lower precision; not the headline)")

@@ -247,6 +247,22 @@ int bpmf_get_rows(bpmf_handle h, int32_t side, int64_t row_begin, int64_t row_en
 int bpmf_put_rows(bpmf_handle h, int32_t side, int64_t row_begin, int64_t row_end,
                   const float* in, int32_t where);
 
+/* Host only (no handle, no device work): the device bytes bpmf_create would hold for
+ * this problem (the figure bpmf_info then reports as device_bytes), for admission of
+ * jobs against a memory budget before any allocation.  Arguments as for bpmf_create:
+ * M x N ratings in CSR (csr_ptr: M + 1 offsets; csr_col: the column of each rating,
+ * used for the column view's degrees), K latent dimensions, n_test test points, params
+ * (NULL: defaults; the flags, long_min_degree and split_degree change the bins and the
+ * buffers).  num_sms: SM count of the device the handle will run on (<= 0: the current
+ * device, read with cudaDeviceGetAttribute).  *out_bytes receives the sum of
+ * bpmf_create's allocations, each rounded up to 256 bytes as it rounds them (scratch
+ * that bpmf_create frees before returning is not counted).  BPMF_EINVAL for a NULL
+ * pointer, sizes outside bpmf_create's limits or a column index outside [0, N);
+ * BPMF_ECUDA if the SM count cannot be read; BPMF_ENOMEM if the host cannot allocate. */
+int bpmf_device_bytes(int64_t M, int64_t N, int32_t K, const int64_t* csr_ptr,
+                      const int32_t* csr_col, int64_t n_test, const bpmf_params* params,
+                      int32_t num_sms, int64_t* out_bytes);
+
 /* Host only (no device work, no handle): the degree bins bpmf_create makes for one
  * side.  ptr: rows + 1 offsets of the side's ratings (ptr[0] = 0, non-decreasing);
  * rows with at least long_min ratings form the tensor-core bin (long_min <= 0: no such

@@ -88,6 +88,7 @@ def lib():
     L.bpmf_launch_count.argtypes = [vp, P(i64)]
     L.bpmf_balance_rows.argtypes = [i64, P(i64), i64, P(i32), P(i64), P(i32)]
     L.bpmf_bin_rows.argtypes = [i64, P(i64), i64, P(i32), P(i64)]
+    L.bpmf_device_bytes.argtypes = [i64, i64, i32, vp, vp, i64, P(bpmf_params), i32, P(i64)]
     L.bpmf_set_row_timing.argtypes = [vp, i32]
     L.bpmf_row_launch_ms.argtypes = [vp, P(C.c_float), P(C.c_float), P(C.c_float)]
     L.bpmf_row_stats_noalloc.argtypes = [vp, i64, i32, vp, vp, vp, vp]
@@ -285,6 +286,17 @@ def bpmf_info(h, side):
             "balanced": bal.value}
 
 
+def bpmf_device_bytes(M, N, K, csr_ptr, csr_col, n_test=0, params=None, num_sms=0):
+    """Device bytes bpmf_create would hold for this problem (host only; num_sms <= 0:
+    the current device's SM count)."""
+    p = params if params is not None else bpmf_default_params()
+    a = [np.ascontiguousarray(csr_ptr, dtype=np.int64), np.ascontiguousarray(csr_col, dtype=np.int32)]
+    out = C.c_int64()
+    _check(lib().bpmf_device_bytes(int(M), int(N), int(K), _ptr(a[0]), _ptr(a[1]), int(n_test),
+                                   C.byref(p), int(num_sms), C.byref(out)), "bpmf_device_bytes")
+    return out.value
+
+
 def bpmf_bin_rows(ptr, long_min):
     """Degree bins of one side's rows (offsets `ptr`, rows + 1 entries): (order, n_short),
     the short bin then the long bin (rows of at least long_min ratings), each longest first.
@@ -392,6 +404,7 @@ EXPORTED = ["bpmf_default_params", "bpmf_create", "bpmf_sweep", "bpmf_sweep_batc
             "bpmf_get_state", "bpmf_set_state", "bpmf_get_accum", "bpmf_set_accum",
             "bpmf_get_stats", "bpmf_debug_means", "bpmf_status", "bpmf_info", "bpmf_launch_count",
             "bpmf_set_row_timing", "bpmf_row_launch_ms", "bpmf_bin_rows", "bpmf_balance_rows",
+            "bpmf_device_bytes",
             "bpmf_row_stats_noalloc", "bpmf_set_shard", "bpmf_get_rows", "bpmf_put_rows",
             "bpmf_strerror",
             "bpmf_destroy"]

@@ -304,15 +304,17 @@ int rank_one_from(int32_t v) { return (v > 0 ? v : (v == 0 ? kDefaultRankOneDegr
 // first) with at least split_degree ratings are cut into ceil(d / (split_degree / 2))
 // near-equal runs of consecutive ratings.  Uploads the list (waited for) and zeroes
 // the rows' counters; grows the device arrays when the list outgrows them.
-int plan_segments(bpmf_ctx* h, DevSide& d, const std::vector<int32_t>& order)
+// The segment list itself (host only); returns the number of rows split.
+int64_t build_segments(const int64_t* ptr, const std::vector<int32_t>& order, int64_t n_short,
+                       int64_t split_degree, std::vector<Segment>& segs)
 {
-    std::vector<Segment> segs;
+    segs.clear();
     int64_t nsplit = 0;
-    const int64_t seg_len = h->split_degree / 2 > 0 ? h->split_degree / 2 : 1;
-    for (int64_t r = 0; r < d.n_short; ++r) {
+    const int64_t seg_len = split_degree / 2 > 0 ? split_degree / 2 : 1;
+    for (int64_t r = 0; r < n_short; ++r) {
         const int32_t row = order[(size_t)r];
-        const int64_t p0 = d.ptr_h[(size_t)row], deg = d.ptr_h[(size_t)row + 1] - p0;
-        if (deg < h->split_degree || deg < 2) break;  // the bin is ordered longest first
+        const int64_t p0 = ptr[row], deg = ptr[row + 1] - p0;
+        if (deg < split_degree || deg < 2) break;  // the bin is ordered longest first
         const int64_t n = (deg + seg_len - 1) / seg_len;
         const int32_t first = (int32_t)segs.size();
         for (int64_t t = 0; t < n; ++t)
@@ -320,6 +322,13 @@ int plan_segments(bpmf_ctx* h, DevSide& d, const std::vector<int32_t>& order)
                                    first, (int32_t)n});
         ++nsplit;
     }
+    return nsplit;
+}
+
+int plan_segments(bpmf_ctx* h, DevSide& d, const std::vector<int32_t>& order)
+{
+    std::vector<Segment> segs;
+    const int64_t nsplit = build_segments(d.ptr_h.data(), order, d.n_short, h->split_degree, segs);
     const int64_t nsegs = (int64_t)segs.size();
     if (nsegs > d.seg_cap) {
         if (!alloc_n(h, &d.segs, (size_t)nsegs) ||
@@ -400,16 +409,24 @@ bool balance_plan(const std::vector<int64_t>& cost, int64_t G, std::vector<int32
     return true;
 }
 
+// Plan costs of the long bin's rows (order[n_short ..]), longest first.
+void long_bin_costs(const int64_t* ptr, const std::vector<int32_t>& order, int64_t n_short,
+                    int64_t n_long, std::vector<int64_t>& cost)
+{
+    cost.resize((size_t)n_long);
+    for (int64_t k = 0; k < n_long; ++k) {
+        const int32_t row = order[(size_t)(n_short + k)];
+        cost[(size_t)k] = plan_cost(ptr[row + 1] - ptr[row]);
+    }
+}
+
 int plan_long_bin(bpmf_ctx* h, DevSide& d, const std::vector<int32_t>& order)
 {
     d.plan_grid[0] = d.plan_grid[1] = 0;
     const int64_t n = d.n_long;
     if (!h->tc || n == 0) return BPMF_OK;
-    std::vector<int64_t> cost((size_t)n);
-    for (int64_t k = 0; k < n; ++k) {
-        const int32_t row = order[(size_t)(d.n_short + k)];
-        cost[(size_t)k] = plan_cost(d.ptr_h[(size_t)row + 1] - d.ptr_h[(size_t)row]);
-    }
+    std::vector<int64_t> cost;
+    long_bin_costs(d.ptr_h.data(), order, d.n_short, n, cost);
     std::vector<int32_t> pos, plan((size_t)n);
     std::vector<int64_t> first;
     for (int q = 0; q < 2; ++q) {
@@ -1419,6 +1436,89 @@ int bpmf_put_rows(bpmf_handle h, int32_t side, int64_t row_begin, int64_t row_en
     if (e == cudaSuccess && where == 0) e = cudaStreamSynchronize(h->stream);  // host buffer
     if (e != cudaSuccess) cudaGetLastError();
     return cuda_rc(e);
+}
+
+int bpmf_device_bytes(int64_t M, int64_t N, int32_t K, const int64_t* csr_ptr,
+                      const int32_t* csr_col, int64_t n_test, const bpmf_params* params,
+                      int32_t num_sms, int64_t* out_bytes)
+{
+    if (!out_bytes || M <= 0 || N <= 0 || K < 1 || K > kMaxK || n_test < 0 || !csr_ptr ||
+        M > INT32_MAX || N > INT32_MAX || !valid_ptr(M, csr_ptr))
+        return BPMF_EINVAL;
+    const int64_t nnz = csr_ptr[M];
+    if (nnz > 0 && !csr_col) return BPMF_EINVAL;
+    if (num_sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return BPMF_ECUDA;
+        }
+    }
+    bpmf_params prm;
+    if (params) prm = *params;
+    else bpmf_default_params(&prm);
+    // every size below is one allocation of bpmf_create, rounded as it rounds them
+    auto rb = [](size_t b) -> int64_t {
+        if (b == 0) b = 16;
+        return (int64_t)((b + 255) & ~(size_t)255);
+    };
+    const int kp = (K + 15) / 16 * 16;
+    const bool tc = kp == 64 && !(prm.flags & BPMF_CUDA_CORE_GRAM);
+    const int64_t long_min = prm.long_min_degree > 0 ? prm.long_min_degree : kDefaultLongMinDegree;
+    const int64_t split = prm.split_degree > 0 ? prm.split_degree : kDefaultSplitDegree;
+    std::vector<int64_t> cptr;
+    try {
+        // the column view's offsets, from the column counts
+        cptr.assign((size_t)N + 1, 0);
+        for (int64_t e = 0; e < nnz; ++e) {
+            const int32_t c = csr_col[e];
+            if (c < 0 || c >= N) return BPMF_EINVAL;
+            ++cptr[(size_t)c + 1];
+        }
+        for (int64_t c = 0; c < N; ++c) cptr[(size_t)c + 1] += cptr[(size_t)c];
+        int64_t bytes = 0, gram_rows = 0;
+        std::vector<int32_t> order, pos;
+        std::vector<Segment> segs;
+        std::vector<int64_t> cost, first;
+        for (int s = 0; s < 2; ++s) {
+            const int64_t rows = s == 0 ? M : N;
+            const int64_t* ptr = s == 0 ? csr_ptr : cptr.data();
+            const size_t r = (size_t)rows;
+            bytes += rb(8 * (r + 1)) + 2 * rb(4 * (size_t)nnz) + rb(4 * r * kp) + rb(4 * r) +
+                     rb(8 * (size_t)K) + rb(8 * (size_t)kp) + rb(8 * (size_t)K * K) +
+                     rb(8 * nw_draws_doubles(K)) + rb(4 * 3 * (size_t)kp * kp) + rb(4 * (size_t)kp) +
+                     rb(8 * (size_t)hyper_reduce_blocks(rows, num_sms) * hyper_partial_doubles(kp)) +
+                     rb(8 * hyper_partial_doubles(kp)) + rb(8 * ((size_t)K + (size_t)K * K));
+            if (prm.flags & BPMF_DEBUG_MEANS) bytes += rb(4 * r * kp);
+            if (tc) bytes += 2 * rb(2 * r * kp);
+            int64_t n_short = 0, n_long = 0, long_ratings = 0;
+            bin_rows(rows, ptr, tc ? long_min : INT64_MAX, order, &n_short, &n_long, &long_ratings);
+            const int64_t nsplit = build_segments(ptr, order, n_short, split, segs);
+            if (!segs.empty())
+                bytes += rb(sizeof(Segment) * segs.size()) +
+                         rb(4 * segs.size() * warp_partial_floats(kp));
+            if (nsplit > 0) bytes += rb(sizeof(unsigned int) * (size_t)nsplit);
+            if (tc && n_long > 0) {
+                long_bin_costs(ptr, order, n_short, n_long, cost);
+                for (int q = 0; q < 2; ++q) {
+                    const int64_t G = std::min<int64_t>(n_long, (int64_t)kGramCtasPerSm * (num_sms - q));
+                    if (!balance_plan(cost, G, pos, first)) continue;
+                    bytes += rb(4 * (size_t)n_long) + rb(8 * ((size_t)kGramCtasPerSm * num_sms + 1));
+                }
+                gram_rows = std::max(gram_rows, n_long);
+            }
+            if (s == 0) bytes += rb(8 * (1 + (size_t)kCheckSumBlocks)) + rb(4);
+        }
+        if (gram_rows > 0) bytes += rb(4 * (size_t)gram_rows * kGramSlotFloats);
+        const size_t T = (size_t)n_test;
+        bytes += rb(8 * (size_t)K) + rb(8 * (size_t)K * K) + 3 * rb(4 * T) + rb(8 * T) +
+                 rb(16 * (size_t)predict_blocks(n_test, num_sms)) + rb(sizeof(Control));
+        *out_bytes = bytes;
+    } catch (const std::bad_alloc&) {
+        return BPMF_ENOMEM;
+    }
+    return BPMF_OK;
 }
 
 int bpmf_bin_rows(int64_t rows, const int64_t* ptr, int64_t long_min, int32_t* order_out,

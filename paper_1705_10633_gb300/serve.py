@@ -54,9 +54,11 @@ class JobResult:
 
 
 def estimate_bytes(problem) -> int:
-    """Device bytes a handle for `problem` needs, before it exists: ratings twice
+    """A rough figure of the device bytes a handle for `problem` needs: ratings twice
     (8-byte pointers, 4-byte index and value), FP32 factors and, at K = 64, their two
-    16-bit copies, the test set and its running sums, plus 4 MB of small state."""
+    16-bit copies, the test set and its running sums, plus 4 MB of small state.  For
+    backends that cannot say better; the device backend asks the library
+    (bpmf_device_bytes), which counts every allocation of bpmf_create."""
     kp = (problem.K + 15) // 16 * 16
     rows = problem.M + problem.N
     b = 16 * problem.nnz + 8 * (rows + 2)
@@ -75,12 +77,23 @@ class DeviceBackend:
 
         import paper_1705_10633_gb300 as bp
         self.torch, self.bp = torch, bp
+        self.num_sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+    def _params(self, job: Job):
+        p = job.problem
+        return self.bp.bpmf_default_params(alpha=p.alpha, seed=job.seed, flags=job.flags,
+                                           burn_in=p.burn_in if job.burn_in is None else job.burn_in)
+
+    def estimate(self, job: Job) -> int:
+        """The device bytes bpmf_create will hold for this job (exact, host only)."""
+        p = job.problem
+        return self.bp.bpmf_device_bytes(p.M, p.N, p.K, p.csr_ptr, p.csr_col, len(p.test_i),
+                                         params=self._params(job), num_sms=self.num_sms)
 
     def create(self, job: Job):
         bp, p = self.bp, job.problem
         stream = self.torch.cuda.Stream()
-        params = bp.bpmf_default_params(alpha=p.alpha, seed=job.seed, flags=job.flags,
-                                        burn_in=p.burn_in if job.burn_in is None else job.burn_in)
+        params = self._params(job)
         keep = bp.torch_allocator(params)
         h = bp.bpmf_create(p.M, p.N, p.K, p.csr_ptr, p.csr_col, p.csr_val, test_i=p.test_i,
                            test_j=p.test_j, test_r=p.test_r, params=params,
@@ -131,6 +144,8 @@ class Server:
         self.memory_in_use = 0
         self.peak_memory = 0
         self.rounds = 0
+        self.memory_waits = 0      # jobs that waited at the head of the queue for memory
+        self._mem_blocked = set()  # their futures, until admitted
         self._thread = threading.Thread(target=self._run, name="bpmf-serve", daemon=True)
         self._thread.start()
 
@@ -138,7 +153,8 @@ class Server:
     def submit(self, job: Job) -> cf.Future:
         fut = cf.Future()
         job.submitted_at = time.perf_counter()
-        est = estimate_bytes(job.problem)
+        est = (self.backend.estimate(job) if hasattr(self.backend, "estimate")
+               else estimate_bytes(job.problem))
         with self._cv:
             if self._closing:
                 raise RuntimeError("server is closed")
@@ -159,6 +175,7 @@ class Server:
             for k, (job, f, est) in enumerate(self._pending):
                 if f is fut:
                     del self._pending[k]
+                    self._mem_blocked.discard(fut)
                     fut.cancel()
                     return True
             if any(a["fut"] is fut for a in self._active):
@@ -179,8 +196,12 @@ class Server:
         while self._pending and len(self._active) < self.max_active:
             job, fut, est = self._pending[0]
             if self.memory_in_use + est > self.memory_limit:
+                if fut not in self._mem_blocked:
+                    self._mem_blocked.add(fut)
+                    self.memory_waits += 1
                 break  # arrival order: a large job waits rather than being overtaken
             self._pending.pop(0)
+            self._mem_blocked.discard(fut)
             self.memory_in_use += est
             try:
                 handle = self.backend.create(job)
@@ -262,3 +283,9 @@ class Server:
 def latency_percentiles(results, qs=(50, 99)):
     lat = np.array([r.latency for r in results])
     return {"p%d" % q: float(np.percentile(lat, q)) for q in qs}
+
+
+def queue_wait_percentiles(results, qs=(50, 99)):
+    """Percentiles of the time each job spent queued before admission."""
+    w = np.array([r.admitted_at - r.submitted_at for r in results])
+    return {"p%d" % q: float(np.percentile(w, q)) for q in qs}

@@ -136,3 +136,42 @@ def test_row_stats_noalloc_rejects_misaligned_pointers_on_the_host(bp):
         assert rc == bp.BPMF_EINVAL
     assert bp.lib().bpmf_row_stats_noalloc(base, 100, 65, None, base, base, None) == bp.BPMF_EINVAL
     assert bp.lib().bpmf_row_stats_noalloc(base, 0, 16, None, base, base, None) == bp.BPMF_EINVAL
+
+
+def test_device_bytes_is_host_only_and_follows_the_buffers(bp):
+    """bpmf_device_bytes runs without a GPU when the SM count is given, and moves with
+    the buffers bpmf_create makes: the 16-bit factor copies and per-row scratch of the
+    tensor-core route, the conditional means, the test set; bad input is refused on the
+    host.  (That it equals what bpmf_create holds is checked on the GPU.)"""
+    import workloads
+    prob = workloads.random_small(2000, 600, 64, 50000, seed=7, n_test=200, long_rows=4,
+                                  long_deg=500)
+
+    def nbytes(K=64, n_test=200, **kw):
+        return bp.bpmf_device_bytes(prob.M, prob.N, K, prob.csr_ptr, prob.csr_col, n_test,
+                                    params=bp.bpmf_default_params(**kw), num_sms=152)
+
+    base = nbytes()
+    # rows with at least 48 ratings take the tensor-core route at K = 64: one 8,960-B
+    # scratch slot per row of the larger long bin
+    deg_u = np.diff(prob.csr_ptr)
+    deg_v = np.bincount(prob.csr_col, minlength=prob.N)
+    n_long = max(int((deg_u >= 48).sum()), int((deg_v >= 48).sum()))
+    assert n_long > 0
+    cuda_core = nbytes(flags=bp.BPMF_CUDA_CORE_GRAM)
+    assert base - cuda_core >= n_long * 8960 + 2 * 2 * (prob.M + prob.N) * 64
+    # the conditional means: one FP32 row per row of each side
+    assert nbytes(flags=bp.BPMF_DEBUG_MEANS) - base >= 4 * 64 * (prob.M + prob.N)
+    # K = 16 rows are a quarter of the K = 64 rows and take no tensor-core route
+    assert nbytes(K=16) < cuda_core
+    # each test point: index pair, rating and FP64 running sum
+    assert nbytes(n_test=200 + 64 * 1024) - base >= 20 * 64 * 1024
+    for bad in (dict(K=0), dict(K=65), dict(n_test=-1)):
+        with pytest.raises(bp.BpmfError) as ei:
+            nbytes(**bad)
+        assert ei.value.code == bp.BPMF_EINVAL
+    col = prob.csr_col.copy()
+    col[5] = prob.N  # a column outside [0, N)
+    with pytest.raises(bp.BpmfError) as ei:
+        bp.bpmf_device_bytes(prob.M, prob.N, 64, prob.csr_ptr, col, 0, num_sms=152)
+    assert ei.value.code == bp.BPMF_EINVAL

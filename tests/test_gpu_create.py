@@ -2,7 +2,8 @@
 checked on the device (BPMF_EINVAL, nothing leaked), and the ratings' mean is an FP64
 sum in a fixed order, equal to the exact mean within rounding and the same on every
 run; a caller-supplied column view is checked for structure on the host and, entry by
-entry, against the view the library builds from the rows."""
+entry, against the view the library builds from the rows; bpmf_device_bytes gives, before
+any allocation, the bytes the handle then holds."""
 import math
 
 import numpy as np
@@ -91,3 +92,33 @@ def test_caller_column_view_must_be_the_transpose(bp):
             bp.bpmf_create(prob.M, prob.N, prob.K, prob.csr_ptr, prob.csr_col, prob.csr_val,
                            csc_ptr=cptr, csc_row=r, csc_val=v, stream=bp.torch_stream())
         assert ei.value.code == bp.BPMF_EINVAL
+
+
+@pytest.mark.parametrize("K, flags, kw", [
+    (16, 0, {}),
+    (32, 0, {"split_degree": 64}),           # split rows: segment buffers
+    (64, 0, {}),                             # tensor-core bins, plans and scratch
+    (64, 0x4, {"long_min_degree": 16}),      # BPMF_DEBUG_MEANS, a larger long bin
+    (64, 0x10, {}),                          # BPMF_CUDA_CORE_GRAM: no tensor-core buffers
+])
+def test_device_bytes_is_what_create_holds(bp, K, flags, kw):
+    """bpmf_device_bytes, computed on the host before any allocation, equals the device
+    bytes the handle holds after bpmf_create (the figure a server admits jobs by)."""
+    import torch
+    prob = workloads.random_small(2500, 700, K, 70000, seed=41 + K, n_test=300, empty_rows=3,
+                                  long_rows=5, long_deg=600)
+    params = bp.bpmf_default_params(alpha=float(prob.alpha), seed=3, flags=flags, **kw)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    want = bp.bpmf_device_bytes(prob.M, prob.N, prob.K, prob.csr_ptr, prob.csr_col,
+                                len(prob.test_i), params=params, num_sms=sms)
+    assert want == bp.bpmf_device_bytes(prob.M, prob.N, prob.K, prob.csr_ptr, prob.csr_col,
+                                        len(prob.test_i), params=params)  # current device
+    h = bp.bpmf_create(prob.M, prob.N, prob.K, prob.csr_ptr, prob.csr_col, prob.csr_val,
+                       test_i=prob.test_i, test_j=prob.test_j, test_r=prob.test_r,
+                       params=params, stream=bp.torch_stream())
+    try:
+        assert bp.bpmf_info(h, 0)["device_bytes"] == want
+        if K == 64 and not flags & 0x10:
+            assert bp.bpmf_info(h, 0)["n_long"] > 0
+    finally:
+        bp.bpmf_destroy(h)

@@ -72,6 +72,8 @@ def test_memory_budget_and_arrival_order():
     assert all(be.swept[s] == 7 for s in range(1, 9))
     assert [float(r.predictions[0]) for r in res] == [float(s) for s in range(1, 9)]
     assert srv.memory_in_use == 0 and srv.peak_memory <= 2.5 * one
+    # only the head of the queue is counted, once, while the budget holds it back
+    assert 1 <= srv.memory_waits <= 6 and not srv._mem_blocked
     assert all(r.finished_at >= r.admitted_at >= r.submitted_at for r in res)
     lat = latency_percentiles(res)
     assert 0 <= lat["p50"] <= lat["p99"]

@@ -331,15 +331,18 @@ def config4(seed: int = 3, n_jobs: int = 256) -> list:
     [0.1%, 2%], K drawn from {16, 32, 64}, planted Gaussian ratings (noise sd 0.3),
     1% of the ratings' count as test points.  Job j is seeded with 1000 seed + j."""
     rng = np.random.default_rng(seed)
-    jobs = []
-    for j in range(n_jobs):
-        M = int(round(np.exp(rng.uniform(np.log(1e3), np.log(1e5)))))
-        N = int(round(np.exp(rng.uniform(np.log(500.0), np.log(1e4)))))
-        dens = float(np.exp(rng.uniform(np.log(1e-3), np.log(2e-2))))
-        K = int(rng.choice([16, 32, 64]))
-        nnz = max(1, int(dens * M * N))
-        jobs.append(random_small(M, N, K, nnz, seed=1000 * seed + j, n_test=max(1, nnz // 100)))
-    return jobs
+    return [config4_job(rng, 1000 * seed + j) for j in range(n_jobs)]
+
+
+def config4_job(rng, seed: int) -> Problem:
+    """One job drawn from the distribution of config4: sizes, density and K from `rng`,
+    the ratings from `seed`."""
+    M = int(round(np.exp(rng.uniform(np.log(1e3), np.log(1e5)))))
+    N = int(round(np.exp(rng.uniform(np.log(500.0), np.log(1e4)))))
+    dens = float(np.exp(rng.uniform(np.log(1e-3), np.log(2e-2))))
+    K = int(rng.choice([16, 32, 64]))
+    nnz = max(1, int(dens * M * N))
+    return random_small(M, N, K, nnz, seed=seed, n_test=max(1, nnz // 100))
 
 
 def subsample_rows(prob: Problem, n_rows: int, seed: int = 123) -> Problem:
