@@ -3,13 +3,16 @@
 // Cholesky factorisation instead of an inverse; Alg. 1: the new vector is the
 // conditional mean plus randomly sampled noise).
 //
-// One warp per row, twelve warps per CTA, one CTA per SM, rows dealt round-robin
-// over all warps of the grid (every row costs the same at K = 64).  Lane l loads
-// rows l and 32 + l of Lambda_i from the row's scratch slot straight into
+// One warp per row, eight warps per CTA, one CTA per SM, rows dealt round-robin
+// over all warps of the grid (every row costs the same at K = 64).  Eight warps (two
+// per SM sub-partition) already reach the SM's throughput on this code, which is bound
+// by the shared-memory broadcasts and shuffles of the column steps: twelve were no
+// faster, and eight leave each warp the registers to keep its rows without spills.
+// Lane l loads rows l and 32 + l of Lambda_i from the row's scratch slot straight into
 // registers (coalesced 16-B loads: the slot stores each float4 column chunk's rows
-// consecutively), then runs the shifted right-looking factorisation with the
-// forward solve fused, Philox noise and the back solve (rows_common.cuh), and
-// stores the FP32 row and its 16-bit split.
+// consecutively), then runs the shifted right-looking factorisation with the forward
+// solve fused (two columns a step, with paired FMAs), Philox noise and the back solve
+// (rows_common.cuh), and stores the FP32 row and its 16-bit split.
 #include "bpmf_internal.cuh"
 #include "philox.cuh"
 #include "rows_common.cuh"
@@ -17,7 +20,7 @@
 namespace bpmf {
 namespace {
 
-constexpr int kCholWarps = 12;
+constexpr int kCholWarps = 8;
 // per warp: L^T (64 x kLtLd), the column buffers (2 x 64), 1 / diag (64), noise (64)
 constexpr int kCholWarpFloats = 64 * kLtLd + 128 + 64 + 64;
 constexpr size_t kCholSmemBytes = (size_t)kCholWarps * kCholWarpFloats * 4;
@@ -41,26 +44,22 @@ __global__ void __launch_bounds__(kCholWarps * 32, 1) rows_chol_kernel(RowArgs a
     for (int64_t p = (int64_t)blockIdx.x * kCholWarps + warp; p < a.nrows; p += W) {
         const int row = __ldg(a.rows + p);
         const float4* src = reinterpret_cast<const float4*>(a.gram + p * kGramSlotFloats);
-        float a1[32], a2[64];
+        float2 a1[16], a2[32];  // column pairs
         // row lane: chunk columns c <= lane / 4; row 32 + lane: c <= 8 + lane / 4 (the
         // rest of each row lies above the diagonal and is never used)
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (4 * c <= lane) v = __ldg(src + gram_chunk_offset(c) + lane - 4 * c);
-            a1[4 * c + 0] = v.x;
-            a1[4 * c + 1] = v.y;
-            a1[4 * c + 2] = v.z;
-            a1[4 * c + 3] = v.w;
+            a1[2 * c + 0] = make_float2(v.x, v.y);
+            a1[2 * c + 1] = make_float2(v.z, v.w);
         }
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (4 * c <= 32 + lane) v = __ldg(src + gram_chunk_offset(c) + 32 + lane - 4 * c);
-            a2[4 * c + 0] = v.x;
-            a2[4 * c + 1] = v.y;
-            a2[4 * c + 2] = v.z;
-            a2[4 * c + 3] = v.w;
+            a2[2 * c + 0] = make_float2(v.x, v.y);
+            a2[2 * c + 1] = make_float2(v.z, v.w);
         }
         const float* bsrc = a.gram + p * kGramSlotFloats + 4 * kGramChunks;
         const float b1 = __ldg(bsrc + lane), b2 = __ldg(bsrc + 32 + lane);

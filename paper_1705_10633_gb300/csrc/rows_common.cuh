@@ -330,7 +330,9 @@ constexpr int kLtLd = 68;
 // lane's L[r][j] in l1 / l2 (zero on and above the diagonal), applies y_j to the
 // right-hand side (b_j becomes y_j = b_j / L[j][j], rows below lose L[r][j] y_j),
 // writes 1 / L[j][j] to dinv, column j of L transposed into row j of M (a
-// conflict-free row store) and into the column buffer of j's parity.  Branch-free
+// conflict-free row store) and into the column buffer of j's parity, L[r][j] at
+// position r - (j & ~1): in a step over the columns k, k + 1 (k even) both columns'
+// entries of row k + 2 + t then sit at position t + 2, in aligned pairs.  Branch-free
 // apart from the predicated stores.  HAS1 = false once the rows r1 are finished.
 // A pivot that is not positive and finite is not caught here: 1 / L[j][j] then comes
 // out non-positive, infinite or NaN, which the caller checks once per row.
@@ -346,7 +348,7 @@ __device__ __forceinline__ void chol_pivot(int j, float p1, float p2, float& b1,
     const float rinv = rsqrtf(piv);
     const float yk = bk * rinv;
     if (lane == 0) dinv[j] = rinv;
-    float* cb = cbuf + (j & 1) * 64 - j - 1;
+    float* cb = cbuf + (j & 1) * 64 - (j & ~1);
     float* mrow = M + j * kLtLd;
     l1 = 0.f;
     if (HAS1) {
@@ -367,63 +369,73 @@ __device__ __forceinline__ void chol_pivot(int j, float p1, float p2, float& b1,
     }
 }
 
-// Column steps k0 .. k1 - 1 (the pivot work of column k0 already done: l1 / l2 hold
-// the lane's L[r][k0] and cbuf its column).  The rows are kept in registers
-// "shifted": a1[t] = A[r1][k + t] and a2[t] = A[r2][k + t] at step k, so the update
-// A[r][k+1+t] -= L[r][k] L[k+1+t][k]  also slides each row by one
-// (a[t] = a[t+1] - l c[t]) and every register index stays static in a rolled loop.
-// Lookahead: step k first updates the entries of column k + 1 and does that
-// column's pivot work, then the rest of its update, so the pivot's shuffle /
-// rsqrt / store / sync latency overlaps the bulk of the step's FMAs (same
-// arithmetic, same results).  The column buffer is double-buffered by parity.
-// N1 / N2: entries of a1 / a2 still inside the matrix (N1 = 0 once the rows r1 are
-// finished); entries past the matrix are stale and only ever reach register
-// entries past the matrix.
-template <int N1, int N2>
-__device__ __forceinline__ void chol_shifted_steps(float (&a1)[32], float (&a2)[64], float& b1,
-                                                   float& b2, float& l1, float& l2, int k0,
-                                                   int k1, float* M, float* cbuf, float* dinv,
-                                                   int lane)
+// Column pairs (k, k + 1), k = k0, k0 + 2, .. < k1, all even (the pivot work of
+// column k0 already done: l1 / l2 hold the lane's L[r][k0] and the even buffer its
+// column).  The rows are kept in registers as pairs, "shifted": at pair k,
+// (a[s].x, a[s].y) = (A[r][k + 2s], A[r][k + 2s + 1]).  A pair updates column k + 1
+// by column k and does its pivot work, then the rest of each row twice,
+//   A[r][c] -= L[r][k] L[c][k],  then  A[r][c] -= L[r][k + 1] L[c][k + 1]   (c >= k + 2),
+// the same two roundings in the same order as two single-column steps, each with
+// paired FMAs; reading a[s + 1] into a[s] slides the rows by two, so every register
+// index stays static in a rolled loop.  Lookahead: the second update does column
+// k + 2 first, then that column's pivot work, then the rest, so the pivot's latency
+// overlaps the bulk of the FMAs.  P1 / P2: pairs of a1 / a2 still inside the matrix
+// (P1 = 0 once the rows r1 are finished); pairs past the matrix are stale and only
+// ever reach pairs past the matrix.
+template <int P1, int P2>
+__device__ __forceinline__ void chol_pair_steps(float2 (&a1)[16], float2 (&a2)[32], float& b1,
+                                                float& b2, float& l1, float& l2, int k0, int k1,
+                                                float* M, float* cbuf, float* dinv, int lane)
 {
-    static_assert(N1 % 4 == 0 && N2 % 4 == 0 && N2 > 0, "step shape");
+    static_assert(P1 % 2 == 0 && P2 % 2 == 0 && P2 > 0, "step shape");
 #pragma unroll 1
-    for (int k = k0; k < k1; ++k) {
-        __syncwarp();  // column k of L is in its buffer
-        const float* cb = cbuf + (k & 1) * 64;
-        const float4 c0 = *reinterpret_cast<const float4*>(cb);
-        const float n1 = N1 > 1 ? fmaf(-l1, c0.x, a1[1]) : 0.f;
-        const float n2 = fmaf(-l2, c0.x, a2[1]);
-        float nl1 = 0.f, nl2 = 0.f;
-#pragma unroll
-        for (int t4 = 0; t4 < N2; t4 += 4) {
-            const float4 c = t4 == 0 ? c0 : *reinterpret_cast<const float4*>(cb + t4);
-            const float cv[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int t = t4 + u;
-                if (t == 0) continue;
-                if (t + 1 < N2) a2[t] = fmaf(-l2, cv[u], a2[t + 1]);
-                if (t + 1 < N1) a1[t] = fmaf(-l1, cv[u], a1[t + 1]);
-            }
-            if ((t4 == 4 || (t4 == 0 && N2 == 4)) && k + 1 < 64)
-                chol_pivot<(N1 > 1)>(k + 1, n1, n2, b1, b2, nl1, nl2, M, cbuf, dinv, lane);
+    for (int k = k0; k < k1; k += 2) {
+        __syncwarp();  // column k is in the even buffer
+        const float4* ce = reinterpret_cast<const float4*>(cbuf);
+        const float4* co = reinterpret_cast<const float4*>(cbuf + 64);
+        const float4 e0 = ce[0];  // e0.y = L[k + 1][k]
+        float m1 = 0.f, m2 = 0.f;
+        {
+            const float n1 = P1 > 0 ? fmaf(-l1, e0.y, a1[0].y) : 0.f;
+            const float n2 = fmaf(-l2, e0.y, a2[0].y);
+            chol_pivot<(P1 > 0)>(k + 1, n1, n2, b1, b2, m1, m2, M, cbuf, dinv, lane);
         }
-        if (N1 > 1) a1[0] = n1;
-        a2[0] = n2;
-        l1 = nl1;
-        l2 = nl2;
+        const float2 nl1 = make_float2(-l1, -l1), nl2 = make_float2(-l2, -l2);
+#pragma unroll
+        for (int s = 0; s + 1 < P2; ++s) {
+            const int q = (s + 1) >> 1;  // column k's entries of rows k + 2s + 2, k + 2s + 3
+            const float4 c4 = q == 0 ? e0 : ce[q];
+            const float2 c = ((s + 1) & 1) ? make_float2(c4.z, c4.w) : make_float2(c4.x, c4.y);
+            a2[s] = __ffma2_rn(nl2, c, a2[s + 1]);
+            if (s + 1 < P1) a1[s] = __ffma2_rn(nl1, c, a1[s + 1]);
+        }
+        __syncwarp();  // column k + 1 is in the odd buffer
+        const float2 ml1 = make_float2(-m1, -m1), ml2 = make_float2(-m2, -m2);
+        float q1 = 0.f, q2 = 0.f;
+#pragma unroll
+        for (int s = 0; s + 1 < P2; ++s) {
+            const int q = (s + 1) >> 1;
+            const float4 c4 = co[q];
+            const float2 c = ((s + 1) & 1) ? make_float2(c4.z, c4.w) : make_float2(c4.x, c4.y);
+            a2[s] = __ffma2_rn(ml2, c, a2[s]);
+            if (s + 1 < P1) a1[s] = __ffma2_rn(ml1, c, a1[s]);
+            if (s == 0 && k + 2 < 64)
+                chol_pivot<(P1 > 0)>(k + 2, a1[0].x, a2[0].x, b1, b2, q1, q2, M, cbuf, dinv, lane);
+        }
+        l1 = q1;
+        l2 = q2;
     }
 }
 
 // Factor / solve / sample for K = 64.  Lane l holds rows r1 = l (a1: columns 0..31)
-// and r2 = 32 + l (a2: columns 0..63) of Lambda_i in registers -- entries above the
-// diagonal are never used -- and its entries b1 = b_i[r1], b2 = b_i[r2].  M is the
-// warp's 64 x kLtLd buffer; it receives the strictly lower part of L, transposed,
-// for the back solve (its previous contents are ignored).  bad is set when a pivot
-// was not positive and finite (Lambda_i not positive definite in FP32).  The
-// factorisation runs in eight spans of 8 columns so the register rows shrink as
-// they finish, then x = L^{-T}(y + z).
-__device__ __forceinline__ void factor_solve_sample_rl64(float (&a1)[32], float (&a2)[64], float b1,
+// and r2 = 32 + l (a2: columns 0..63) of Lambda_i in registers, as pairs of columns
+// -- entries above the diagonal are never used -- and its entries b1 = b_i[r1],
+// b2 = b_i[r2].  M is the warp's 64 x kLtLd buffer; it receives the strictly lower
+// part of L, transposed, for the back solve (its previous contents are ignored).
+// bad is set when a pivot was not positive and finite (Lambda_i not positive
+// definite in FP32).  The factorisation runs in eight spans of 8 columns so the
+// register rows shrink as they finish, then x = L^{-T}(y + z).
+__device__ __forceinline__ void factor_solve_sample_rl64(float2 (&a1)[16], float2 (&a2)[32], float b1,
                                                          float b2, float* M, float* cbuf,
                                                          float* dinv, float* zb, int lane, int K,
                                                          uint64_t seed, uint32_t row,
@@ -433,15 +445,15 @@ __device__ __forceinline__ void factor_solve_sample_rl64(float (&a1)[32], float 
 {
     const int r1 = lane, r2 = 32 + lane;
     float l1, l2;
-    chol_pivot<true>(0, a1[0], a2[0], b1, b2, l1, l2, M, cbuf, dinv, lane);
-    chol_shifted_steps<32, 64>(a1, a2, b1, b2, l1, l2, 0, 8, M, cbuf, dinv, lane);
-    chol_shifted_steps<24, 56>(a1, a2, b1, b2, l1, l2, 8, 16, M, cbuf, dinv, lane);
-    chol_shifted_steps<16, 48>(a1, a2, b1, b2, l1, l2, 16, 24, M, cbuf, dinv, lane);
-    chol_shifted_steps<8, 40>(a1, a2, b1, b2, l1, l2, 24, 32, M, cbuf, dinv, lane);
-    chol_shifted_steps<0, 32>(a1, a2, b1, b2, l1, l2, 32, 40, M, cbuf, dinv, lane);
-    chol_shifted_steps<0, 24>(a1, a2, b1, b2, l1, l2, 40, 48, M, cbuf, dinv, lane);
-    chol_shifted_steps<0, 16>(a1, a2, b1, b2, l1, l2, 48, 56, M, cbuf, dinv, lane);
-    chol_shifted_steps<0, 8>(a1, a2, b1, b2, l1, l2, 56, 64, M, cbuf, dinv, lane);
+    chol_pivot<true>(0, a1[0].x, a2[0].x, b1, b2, l1, l2, M, cbuf, dinv, lane);
+    chol_pair_steps<16, 32>(a1, a2, b1, b2, l1, l2, 0, 8, M, cbuf, dinv, lane);
+    chol_pair_steps<12, 28>(a1, a2, b1, b2, l1, l2, 8, 16, M, cbuf, dinv, lane);
+    chol_pair_steps<8, 24>(a1, a2, b1, b2, l1, l2, 16, 24, M, cbuf, dinv, lane);
+    chol_pair_steps<4, 20>(a1, a2, b1, b2, l1, l2, 24, 32, M, cbuf, dinv, lane);
+    chol_pair_steps<0, 16>(a1, a2, b1, b2, l1, l2, 32, 40, M, cbuf, dinv, lane);
+    chol_pair_steps<0, 12>(a1, a2, b1, b2, l1, l2, 40, 48, M, cbuf, dinv, lane);
+    chol_pair_steps<0, 8>(a1, a2, b1, b2, l1, l2, 48, 56, M, cbuf, dinv, lane);
+    chol_pair_steps<0, 4>(a1, a2, b1, b2, l1, l2, 56, 64, M, cbuf, dinv, lane);
     // every pivot's 1 / L[j][j] is in dinv (the last step began with a warp sync): it is
     // positive and finite exactly when the pivot was
     {
