@@ -177,9 +177,26 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32
                  "r"(src_bytes)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src)
+// L2 policy for data read or written once (the streamed ratings, the scratch slots):
+// evicted first, so that it does not push the other side's gathered 16-bit rows,
+// which every CTA re-reads, out of L2.
+__device__ __forceinline__ uint64_t l2_evict_first()
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void cp_async4_once(uint32_t dst, const void* src, uint64_t pol)
+{
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, 4, %2;" ::"r"(dst),
+                 "l"(src), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st_once(float4* p, float4 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x),
+                 "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol)
+                 : "memory");
 }
 // Arrive on `bar` once every cp.async this thread issued so far has landed.
 __device__ __forceinline__ void cp_async_arrive(uint32_t bar)
@@ -492,6 +509,7 @@ __global__ void __launch_bounds__(kThreads, kGramCtasPerSm) rows_gram_kernel(Row
         } else if (warp == 1) {
             // ======================= prefetch =======================
             uint32_t g = 0;  // stages whose indices were prefetched
+            const uint64_t once = l2_evict_first();
             bool ok = true;
             for (int64_t j0 = 0; j0 < nj && ok; j0 += 32) {
                 // descriptors of the next 32 rows, one row per lane (independent loads)
@@ -534,8 +552,8 @@ __global__ void __launch_bounds__(kThreads, kGramCtasPerSm) rows_gram_kernel(Row
                         const int cnt = (int)min((long long)kStageRatings, p1 - base);
                         const uint32_t dst = sbase + kOffIdxRing + is * 512;
                         for (int e = lane; e < cnt; e += 32) {
-                            cp_async4(dst + 4 * e, a.idx + base + e);
-                            cp_async4(dst + 256 + 4 * e, a.val + base + e);
+                            cp_async4_once(dst + 4 * e, a.idx + base + e, once);
+                            cp_async4_once(dst + 256 + 4 * e, a.val + base + e, once);
                         }
                         cp_async_arrive(bar_idx_full + 8 * is);
                     }
@@ -555,6 +573,7 @@ __global__ void __launch_bounds__(kThreads, kGramCtasPerSm) rows_gram_kernel(Row
         const uint32_t bar_id = 1 + grp;
         float* T = staging + grp * kStagingFloats;
         const float alpha = a.alpha;
+        const uint64_t once = l2_evict_first();
         uint32_t u = 0;  // accumulation chunks drained by this group
         for (int64_t j = grp; j < nj; j += kGroups) {
             const int rs = (int)(j % kRowRing);
@@ -628,7 +647,7 @@ __global__ void __launch_bounds__(kThreads, kGramCtasPerSm) rows_gram_kernel(Row
                         o.y = fmaf(alpha, acc[4 * c + 1] + t.y + T[sw64(4 * c + 1, m)], px.y);
                         o.z = fmaf(alpha, acc[4 * c + 2] + t.z + T[sw64(4 * c + 2, m)], px.z);
                         o.w = fmaf(alpha, acc[4 * c + 3] + t.w + T[sw64(4 * c + 3, m)], px.w);
-                        out[gram_chunk_offset(c) + m - 4 * c] = o;
+                        st_once(out + gram_chunk_offset(c) + m - 4 * c, o, once);
                     }
                 }
                 reinterpret_cast<float*>(out)[4 * kGramChunks + m] =
