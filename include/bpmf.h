@@ -157,6 +157,38 @@ int bpmf_sweep(bpmf_handle h, int32_t n_sweeps, double* rmse_sample, double* rms
 int bpmf_sweep_batch(bpmf_handle* hs, int32_t n, int32_t n_sweeps);
 
 /*
+ * Batched sweeps of many independent chains with the launches shared: each step of
+ * Alg. 1's sweep (hyper-parameters of one side, its rows, the other side's, the
+ * prediction loop) runs for all chains of the batch in one launch per kernel variant
+ * (per K class where kernels are compiled per K), over a table of (chain, blocks) in
+ * which every chain gets the blocks its own launch would have and the heaviest chains
+ * come first -- the work queue in longest-processing-time order of Sec. 4.2's cost
+ * model, c0 + c1 d per item, served by the device's block dispatch.  The chains'
+ * tensor-core launches (K = 64 rows of the long bin) fork over eight streams.  One
+ * sweep is captured as one CUDA graph when `cuda_stream` can be captured.
+ *
+ * bpmf_batch_create: hs is a host array of n >= 1 distinct handles, borrowed (they must
+ * outlive the batch and keep their bins: calling bpmf_set_tuning or bpmf_set_shard on
+ * one of them invalidates the batch; make a new one).  All on one device, with the
+ * same sweep order and no shard restriction, else BPMF_EINVAL.  cuda_stream: the
+ * stream the batch's launches go to (NULL: the legacy default stream, not captured).
+ * The tables live in one device allocation of the batch (cudaMalloc), freed by
+ * bpmf_batch_destroy.
+ *
+ * bpmf_batch_sweep: n_sweeps sweeps of every chain, ordered after the work already
+ * queued on each chain's own stream, and before work queued there later.  Each
+ * chain's result equals bpmf_sweep(hs[k], n_sweeps) alone, bit for bit.  Does not
+ * wait; read RMSEs with bpmf_sweep(h, 0, ...).  bpmf_batch_launch_count: kernels
+ * launched by the batch's sweeps so far.  bpmf_batch_destroy waits for the batch's
+ * stream, then frees it (NULL is a no-op).
+ */
+typedef struct bpmf_batch_ctx* bpmf_batch;
+int bpmf_batch_create(bpmf_handle* hs, int32_t n, void* cuda_stream, bpmf_batch* out);
+int bpmf_batch_sweep(bpmf_batch b, int32_t n_sweeps);
+int bpmf_batch_launch_count(bpmf_batch b, int64_t* launches);
+int bpmf_batch_destroy(bpmf_batch b);
+
+/*
  * Change the tuning thresholds of a live handle (long_min_degree, split_degree and
  * rank_one_degree of bpmf_params, each with its meaning of 0 and of negative values
  * there): the rows of both sides

@@ -89,6 +89,10 @@ def lib():
     L.bpmf_balance_rows.argtypes = [i64, P(i64), i64, P(i32), P(i64), P(i32)]
     L.bpmf_bin_rows.argtypes = [i64, P(i64), i64, P(i32), P(i64)]
     L.bpmf_device_bytes.argtypes = [i64, i64, i32, vp, vp, i64, P(bpmf_params), i32, P(i64)]
+    L.bpmf_batch_create.argtypes = [P(vp), i32, vp, P(vp)]
+    L.bpmf_batch_sweep.argtypes = [vp, i32]
+    L.bpmf_batch_launch_count.argtypes = [vp, P(i64)]
+    L.bpmf_batch_destroy.argtypes = [vp]
     L.bpmf_set_row_timing.argtypes = [vp, i32]
     L.bpmf_row_launch_ms.argtypes = [vp, P(C.c_float), P(C.c_float), P(C.c_float)]
     L.bpmf_row_stats_noalloc.argtypes = [vp, i64, i32, vp, vp, vp, vp]
@@ -203,6 +207,32 @@ def bpmf_sweep_batch(handles, n_sweeps=1):
     arr = (C.c_void_p * len(handles))(*[int(h) if not isinstance(h, C.c_void_p) else h.value
                                          for h in handles])
     _check(lib().bpmf_sweep_batch(arr, len(handles), int(n_sweeps)), "bpmf_sweep_batch")
+
+
+def bpmf_batch_create(handles, stream=None):
+    """A batch over `handles` (borrowed): every step of a sweep runs for all of them in
+    shared launches on `stream` (a cudaStream_t as int).  Returns an opaque handle."""
+    arr = (C.c_void_p * len(handles))(*[int(h) if not isinstance(h, C.c_void_p) else h.value
+                                         for h in handles])
+    b = C.c_void_p()
+    _check(lib().bpmf_batch_create(arr, len(handles), None if stream is None else C.c_void_p(int(stream)),
+                                   C.byref(b)), "bpmf_batch_create")
+    return b.value
+
+
+def bpmf_batch_sweep(b, n_sweeps=1):
+    """n_sweeps sweeps of every chain of the batch.  Does not wait."""
+    _check(lib().bpmf_batch_sweep(b, int(n_sweeps)), "bpmf_batch_sweep")
+
+
+def bpmf_batch_launch_count(b):
+    n = C.c_int64()
+    _check(lib().bpmf_batch_launch_count(b, C.byref(n)), "bpmf_batch_launch_count")
+    return n.value
+
+
+def bpmf_batch_destroy(b):
+    _check(lib().bpmf_batch_destroy(b), "bpmf_batch_destroy")
 
 
 def bpmf_set_tuning(h, long_min_degree=0, split_degree=0, rank_one_degree=0):
@@ -399,6 +429,7 @@ def create_from_problem(prob, flags=0, seed=None, burn_in=None, params=None, str
 
 
 EXPORTED = ["bpmf_default_params", "bpmf_create", "bpmf_sweep", "bpmf_sweep_batch",
+            "bpmf_batch_create", "bpmf_batch_sweep", "bpmf_batch_launch_count", "bpmf_batch_destroy",
             "bpmf_set_tuning", "bpmf_step",
             "bpmf_predict",
             "bpmf_get_state", "bpmf_set_state", "bpmf_get_accum", "bpmf_set_accum",

@@ -495,7 +495,8 @@ int sync_status(bpmf_ctx* h)
 
 // Hyper step of side s on `st`; sweep_offset = 1 draws the next sweep's
 // hyper-parameters (the device sweep counter has not advanced yet).
-int phase_hyper(bpmf_ctx* h, int s, cudaStream_t st, uint32_t sweep_offset)
+// The Normal-Wishart draw's arguments for side s (also the reduction's draw blocks).
+NWArgs nw_args(bpmf_ctx* h, int s, uint32_t sweep_offset)
 {
     DevSide& d = h->side[s];
     NWArgs a;
@@ -520,11 +521,19 @@ int phase_hyper(bpmf_ctx* h, int s, cudaStream_t st, uint32_t sweep_offset)
     a.lam32 = d.lam32;
     a.lammu32 = d.lammu32;
     a.draws = d.nw_draws;
-    // shift + partials + random draws in one launch; a few partials are combined by the
-    // draw kernel itself, more by their own launch
-    const bool fuse = d.red_blocks <= kFuseCombineBlocks;
+    // a few partials are combined by the draw kernel itself, more by their own launch
     a.partials = d.partials;
-    a.nparts = fuse ? d.red_blocks : 0;
+    a.nparts = d.red_blocks <= kFuseCombineBlocks ? d.red_blocks : 0;
+    return a;
+}
+
+int phase_hyper(bpmf_ctx* h, int s, cudaStream_t st, uint32_t sweep_offset)
+{
+    DevSide& d = h->side[s];
+    // shift + partials + random draws in one launch, then the combine when the draw
+    // kernel does not do it, then the draw
+    const NWArgs a = nw_args(h, s, sweep_offset);
+    const bool fuse = a.nparts > 0;
     cudaError_t e = launch_hyper_stats_draws(d.X, d.rows, h->K, h->kp, d.shift64, d.partials,
                                              d.red_blocks, a, st);
     if (e == cudaSuccess && !fuse) e = launch_hyper_combine(d.partials, d.red_blocks, h->kp, d.sums, st);
@@ -533,9 +542,8 @@ int phase_hyper(bpmf_ctx* h, int s, cudaStream_t st, uint32_t sweep_offset)
     return cuda_rc(launch_nw_sample(a, st));
 }
 
-// timed: record events around the CUDA-core and tensor-core launches (bpmf_step only,
-// never inside a captured sweep)
-int phase_rows(bpmf_ctx* h, int s, bool timed = false)
+// The row kernels' arguments for side s, set for the short bin (the CUDA-core kernel).
+RowArgs row_args(bpmf_ctx* h, int s)
 {
     DevSide& d = h->side[s];
     const DevSide& o = h->side[1 - s];
@@ -566,7 +574,6 @@ int phase_rows(bpmf_ctx* h, int s, bool timed = false)
                    1000000LL;
     a.test_stall = (h->p.flags & BPMF_TEST_STALL) ? 1 : 0;
     a.bf16 = (h->p.flags & BPMF_BF16_GRAM) ? 1 : 0;
-    cudaError_t e = cudaSuccess;
     // the short bin (every row when the tensor-core kernel is off) on the CUDA-core
     // kernel, its longest rows as segments
     a.rows = d.bin_rows;
@@ -577,16 +584,14 @@ int phase_rows(bpmf_ctx* h, int s, bool timed = false)
     a.part = d.part;
     a.seg_done = d.seg_done;
     a.nrank_one = d.n_rank_one;
-    timed = timed && h->row_timing;
-    if (timed) {
-        h->timed_parts = (a.nrows > 0 ? 1 : 0) | (d.n_long > 0 ? 2 : 0);
-        e = cudaEventRecord(h->tev[0], h->stream);
-    }
-    if (e == cudaSuccess && a.nrows > 0) {
-        h->launches += rows_warp_launches(a);
-        e = launch_rows_warp(a, h->kp, h->row_sms, h->stream);
-    }
-    if (e == cudaSuccess && timed) e = cudaEventRecord(h->tev[1], h->stream);
+    return a;
+}
+
+// The same arguments turned to the long bin (the tensor-core route) for a Gram launch
+// over row_sms SMs: the balanced plan made for that grid, when there is one.
+void long_bin_args(bpmf_ctx* h, int s, RowArgs& a)
+{
+    const DevSide& d = h->side[s];
     a.nsegs = a.nsplit = a.nrank_one = 0;
     a.rows = d.bin_rows + d.n_short;
     a.nrows = d.n_long;
@@ -598,6 +603,26 @@ int phase_rows(bpmf_ctx* h, int s, bool timed = false)
             a.plan_grid = grid;
         }
     a.gram = h->gram;
+}
+
+// timed: record events around the CUDA-core and tensor-core launches (bpmf_step only,
+// never inside a captured sweep)
+int phase_rows(bpmf_ctx* h, int s, bool timed = false)
+{
+    const DevSide& d = h->side[s];
+    RowArgs a = row_args(h, s);
+    cudaError_t e = cudaSuccess;
+    timed = timed && h->row_timing;
+    if (timed) {
+        h->timed_parts = (a.nrows > 0 ? 1 : 0) | (d.n_long > 0 ? 2 : 0);
+        e = cudaEventRecord(h->tev[0], h->stream);
+    }
+    if (e == cudaSuccess && a.nrows > 0) {
+        h->launches += rows_warp_launches(a);
+        e = launch_rows_warp(a, h->kp, h->row_sms, h->stream);
+    }
+    if (e == cudaSuccess && timed) e = cudaEventRecord(h->tev[1], h->stream);
+    long_bin_args(h, s, a);
     if (e == cudaSuccess && a.nrows > 0) {
         h->launches += 1;
         e = launch_rows_gram(a, h->row_sms, h->stream);
@@ -609,6 +634,28 @@ int phase_rows(bpmf_ctx* h, int s, bool timed = false)
     }
     if (e == cudaSuccess && timed) e = cudaEventRecord(h->tev[3], h->stream);
     return cuda_rc(e);
+}
+
+PredictArgs pred_args(bpmf_ctx* h)
+{
+    PredictArgs p;
+    memset(&p, 0, sizeof(p));
+    p.ti = h->ti;
+    p.tj = h->tj;
+    p.tr = h->tr;
+    p.T = h->T;
+    p.U = h->side[BPMF_USER].X;
+    p.V = h->side[BPMF_MOVIE].X;
+    p.ld = p.kp = h->kp;
+    p.rbar = h->rbar;
+    p.clip = (h->p.flags & BPMF_CLIP) ? 1 : 0;
+    p.lo = h->p.clip_lo;
+    p.hi = h->p.clip_hi;
+    p.burn_in = h->p.burn_in;
+    p.psum = h->psum;
+    p.ctl = h->ctl;
+    p.partials = h->pred_partials;
+    return p;
 }
 
 int phase_predict(bpmf_ctx* h)
@@ -1172,6 +1219,438 @@ int bpmf_sweep_batch(bpmf_handle* hs, int32_t n, int32_t n_sweeps)
     for (int32_t k = 0; k < n; ++k)
         if (overlapped[(size_t)k]) sweep_end(hs[k]);
     return rc;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched sweeps: every step of a sweep runs for all jobs of the batch in one launch
+// (per K class where the kernels are compiled per K), with each job's blocks in a table
+// the CTAs search; the jobs' tensor-core launches go to forked streams.  One sweep is
+// captured as one CUDA graph.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kBatchForks = 8;  // streams the tensor-core launches of the jobs fork to
+
+struct BatchLaunch {
+    int kind;       // 0 rows (CUDA-core), 1 reduce, 2 combine, 3 draw, 4 predict, 5 finish
+    int kp;
+    bool rank_one;
+    const void* table;
+    int n;
+    int64_t blocks;
+};
+
+}  // namespace
+
+struct bpmf_batch_ctx {
+    std::vector<bpmf_ctx*> jobs;
+    cudaStream_t stream = nullptr;
+    cudaStream_t aux = nullptr;  // hyper steps beside the row launches
+    cudaEvent_t ev[4] = {};      // sweep-level fork / join
+    int first = BPMF_MOVIE;
+    int num_sms = 1;
+    void* dev = nullptr;  // all tables, one allocation
+    // hyper[s]: side s's hyper step for the current sweep; hyper_next: the first side's
+    // for the next sweep, drawn before the sweep counter moves (sweep_offset 1)
+    std::vector<BatchLaunch> hyper[2], hyper_next, rows[2];
+    std::vector<bpmf_ctx*> tc[2];  // jobs with a tensor-core bin on the side
+    BatchLaunch predict{}, finish{};
+    cudaStream_t fork[kBatchForks] = {};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[kBatchForks] = {};
+    cudaGraphExec_t graph = nullptr;
+    int graph_state = 0;
+    int64_t graph_launches = 0;
+    int64_t launches = 0;
+};
+
+namespace {
+
+// Blocks of a job's CUDA-core row launch in a batch: its share of about sixteen waves
+// of the launch's resident CTAs, by the cost model c0 + c1 d of its items, at most one
+// block per four items (a warp per item).  Many small blocks of about equal cost keep
+// the launch's tail short (4 waves: 112, 8: 116, 16: 117 M rows/s on 256 jobs).
+int64_t batch_row_blocks(int64_t items, double cost, double total_cost, int64_t waves_blocks)
+{
+    int64_t want = (int64_t)std::llround((double)waves_blocks * cost / std::max(total_cost, 1.0));
+    want = std::max<int64_t>(want, 1);
+    return std::min<int64_t>(want, (items + 3) / 4);
+}
+
+template <class A>
+struct TableBuilder {
+    std::vector<BatchEntry<A>> entries;
+    int64_t blocks = 0;
+    void add(const A& a, int64_t count)
+    {
+        BatchEntry<A> e;
+        e.args = a;
+        e.first = (int32_t)blocks;
+        e.count = (int32_t)count;
+        entries.push_back(e);
+        blocks += count;
+    }
+};
+
+// Stream order between the jobs' streams and the batch stream (outside any capture).
+int batch_order(bpmf_batch_ctx* b, bool jobs_first)
+{
+    for (bpmf_ctx* h : b->jobs) {
+        cudaEvent_t ev = h->ev[0];
+        cudaStream_t from = jobs_first ? h->stream : b->stream;
+        cudaStream_t to = jobs_first ? b->stream : h->stream;
+        if (from == to) continue;
+        if (cudaEventRecord(ev, from) != cudaSuccess || cudaStreamWaitEvent(to, ev, 0) != cudaSuccess)
+            return BPMF_ECUDA;
+    }
+    return BPMF_OK;
+}
+
+int batch_run(bpmf_batch_ctx* b, const std::vector<BatchLaunch>& ls, cudaStream_t st)
+{
+    for (const BatchLaunch& l : ls) {
+        cudaError_t e = cudaSuccess;
+        switch (l.kind) {
+        case 0:
+            e = launch_rows_warp_batch(static_cast<const BatchEntry<RowArgs>*>(l.table), l.n,
+                                       l.blocks, l.kp, l.rank_one, st);
+            break;
+        case 1:
+            e = launch_hyper_reduce_batch(static_cast<const BatchEntry<ReduceArgs>*>(l.table), l.n,
+                                          l.blocks, l.kp, st);
+            break;
+        case 2:
+            e = launch_hyper_combine_batch(static_cast<const BatchEntry<CombineArgs>*>(l.table), l.n,
+                                           l.blocks, st);
+            break;
+        case 3: e = launch_nw_sample_batch(static_cast<const NWArgs*>(l.table), l.n, st); break;
+        case 4:
+            e = launch_predict_batch(static_cast<const BatchEntry<PredictArgs>*>(l.table), l.n,
+                                     l.blocks, st);
+            break;
+        default:
+            e = launch_predict_finish_batch(static_cast<const BatchEntry<PredictArgs>*>(l.table), l.n,
+                                            true, st);
+            break;
+        }
+        if (e != cudaSuccess) return BPMF_ECUDA;
+        b->launches += 1;
+    }
+    return BPMF_OK;
+}
+
+// Side s's rows, forked over the batch's streams and joined back: the CUDA-core
+// launches (one per K class and route, so that one launch's tail overlaps the next)
+// and the jobs' tensor-core launches, heaviest first, round-robin.
+int batch_rows(bpmf_batch_ctx* b, int s)
+{
+    const size_t nl = b->rows[s].size() + b->tc[s].size();
+    const int nf = (int)std::min<size_t>(kBatchForks, nl);
+    if (nf == 0) return BPMF_OK;
+    if (cudaEventRecord(b->ev_fork, b->stream) != cudaSuccess) return BPMF_ECUDA;
+    for (int f = 0; f < nf; ++f)
+        if (cudaStreamWaitEvent(b->fork[f], b->ev_fork, 0) != cudaSuccess) return BPMF_ECUDA;
+    int rc = BPMF_OK;
+    size_t k = 0;
+    for (const BatchLaunch& l : b->rows[s])
+        if (rc == BPMF_OK) rc = batch_run(b, {l}, b->fork[k++ % (size_t)nf]);
+    for (size_t q = 0; q < b->tc[s].size() && rc == BPMF_OK; ++q) {
+        bpmf_ctx* h = b->tc[s][q];
+        cudaStream_t st = b->fork[k++ % (size_t)nf];
+        h->row_sms = h->num_sms;
+        RowArgs a = row_args(h, s);
+        long_bin_args(h, s, a);
+        cudaError_t e = launch_rows_gram(a, h->num_sms, st);
+        if (e == cudaSuccess) e = launch_rows_chol(a, h->num_sms, st);
+        if (e != cudaSuccess) rc = BPMF_ECUDA;
+        b->launches += 2;
+    }
+    for (int f = 0; f < nf && rc == BPMF_OK; ++f)
+        if (cudaEventRecord(b->ev_join[f], b->fork[f]) != cudaSuccess ||
+            cudaStreamWaitEvent(b->stream, b->ev_join[f], 0) != cudaSuccess)
+            rc = BPMF_ECUDA;
+    return rc;
+}
+
+// One sweep whose first-side hyper step is done (Alg. 1's data dependencies, as in
+// bpmf_sweep): the second side's hyper step runs on the aux stream beside the first
+// side's rows; with next, the next sweep's first-side hyper step beside the second
+// side's rows; the prediction, then the sweep counters move.
+int batch_sweep_body(bpmf_batch_ctx* b, bool next)
+{
+    const int f = b->first, sc = 1 - b->first;
+    cudaEvent_t evA = b->ev[0], evR1 = b->ev[1], evH2 = b->ev[2], evH1 = b->ev[3];
+    if (cudaEventRecord(evA, b->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(b->aux, evA, 0) != cudaSuccess)
+        return BPMF_ECUDA;
+    int rc = batch_run(b, b->hyper[sc], b->aux);
+    if (rc == BPMF_OK && cudaEventRecord(evH2, b->aux) != cudaSuccess) rc = BPMF_ECUDA;
+    if (rc == BPMF_OK) rc = batch_rows(b, f);
+    if (rc == BPMF_OK && next) {
+        if (cudaEventRecord(evR1, b->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(b->aux, evR1, 0) != cudaSuccess)
+            rc = BPMF_ECUDA;
+        if (rc == BPMF_OK) rc = batch_run(b, b->hyper_next, b->aux);
+        if (rc == BPMF_OK && cudaEventRecord(evH1, b->aux) != cudaSuccess) rc = BPMF_ECUDA;
+    }
+    if (rc == BPMF_OK && cudaStreamWaitEvent(b->stream, evH2, 0) != cudaSuccess) rc = BPMF_ECUDA;
+    if (rc == BPMF_OK) rc = batch_rows(b, sc);
+    if (rc == BPMF_OK && b->predict.n > 0) rc = batch_run(b, {b->predict}, b->stream);
+    // the counters move once the next sweep's draw (which reads them) is done
+    if (rc == BPMF_OK && next && cudaStreamWaitEvent(b->stream, evH1, 0) != cudaSuccess) rc = BPMF_ECUDA;
+    if (rc == BPMF_OK) rc = batch_run(b, {b->finish}, b->stream);
+    return rc;  // the batch stream has waited for everything the aux stream was given
+}
+
+void batch_free(bpmf_batch_ctx* b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->aux) cudaStreamDestroy(b->aux);
+    for (cudaEvent_t e : b->ev)
+        if (e) cudaEventDestroy(e);
+    for (int f = 0; f < kBatchForks; ++f) {
+        if (b->fork[f]) cudaStreamDestroy(b->fork[f]);
+        if (b->ev_join[f]) cudaEventDestroy(b->ev_join[f]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->dev) cudaFree(b->dev);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bpmf_batch_create(bpmf_handle* hs, int32_t n, void* cuda_stream, bpmf_batch* out)
+{
+    if (!out) return BPMF_EINVAL;
+    *out = nullptr;
+    if (n < 1 || !hs) return BPMF_EINVAL;
+    for (int32_t k = 0; k < n; ++k) {
+        if (!hs[k] || hs[k]->device != hs[0]->device || hs[k]->num_sms != hs[0]->num_sms ||
+            hs[k]->p.order != hs[0]->p.order)
+            return BPMF_EINVAL;
+        for (int32_t q = 0; q < k; ++q)
+            if (hs[q] == hs[k]) return BPMF_EINVAL;
+        for (int s = 0; s < 2; ++s)
+            if (hs[k]->side[s].shard_lo != 0 || hs[k]->side[s].shard_hi != hs[k]->side[s].rows)
+                return BPMF_EINVAL;
+    }
+    bpmf_batch_ctx* b = new (std::nothrow) bpmf_batch_ctx();
+    if (!b) return BPMF_ENOMEM;
+    try {
+        b->jobs.assign(hs, hs + n);
+    } catch (const std::bad_alloc&) {
+        delete b;
+        return BPMF_ENOMEM;
+    }
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->first = hs[0]->p.order == 0 ? BPMF_MOVIE : BPMF_USER;
+    b->num_sms = hs[0]->num_sms;
+    bool ok = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t& e : b->ev)
+        ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    for (int f = 0; f < kBatchForks && ok; ++f)
+        ok = cudaStreamCreateWithFlags(&b->fork[f], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->ev_join[f], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        batch_free(b);
+        return BPMF_ECUDA;
+    }
+    // host tables; each job's share is what its own launch would be, ordered heaviest
+    // first (the work queue in longest-processing-time order of the cost model
+    // c0 + c1 d: the CTAs of the heaviest jobs are dispatched first).  Each table is
+    // staged in `image` at a 256-B aligned offset, kept in its launch until the one
+    // device allocation exists.
+    std::vector<char> image;
+    auto place = [&](const void* p, size_t bytes) -> const void* {
+        const size_t off = image.size();
+        image.resize(off + ((bytes + 255) & ~(size_t)255), 0);
+        memcpy(image.data() + off, p, bytes);
+        return reinterpret_cast<const void*>(off);
+    };
+    const int kps[4] = {16, 32, 48, 64};
+    auto build_hyper = [&](int s, uint32_t offset, std::vector<BatchLaunch>& out) {
+        // the reductions (with the draw blocks) by kp, the combines, the draws
+        for (int kp : kps) {
+            std::vector<std::pair<int64_t, bpmf_ctx*>> order;
+            for (bpmf_ctx* h : b->jobs)
+                if (h->kp == kp) order.push_back({h->side[s].red_blocks + hyper_draw_blocks(h->K), h});
+            if (order.empty()) continue;
+            std::stable_sort(order.begin(), order.end(),
+                             [](const auto& x, const auto& y) { return x.first > y.first; });
+            TableBuilder<ReduceArgs> t;
+            for (auto& o : order) {
+                bpmf_ctx* h = o.second;
+                const DevSide& d = h->side[s];
+                ReduceArgs r;
+                memset(&r, 0, sizeof(r));
+                r.X = d.X;
+                r.rows = d.rows;
+                r.shiftK = h->K;
+                r.shift64 = d.shift64;
+                r.partials = d.partials;
+                r.nred = d.red_blocks;
+                r.draws = nw_args(h, s, offset);
+                t.add(r, o.first);
+            }
+            out.push_back(BatchLaunch{1, kp, false, place(t.entries.data(), t.entries.size() * sizeof(t.entries[0])),
+                                      (int)t.entries.size(), t.blocks});
+        }
+        TableBuilder<CombineArgs> tc;
+        for (bpmf_ctx* h : b->jobs) {
+            const DevSide& d = h->side[s];
+            if (d.red_blocks <= kFuseCombineBlocks) continue;
+            CombineArgs c;
+            c.partials = d.partials;
+            c.nblocks = d.red_blocks;
+            c.E = (int)hyper_partial_doubles(h->kp);
+            c.sums = d.sums;
+            tc.add(c, hyper_combine_blocks(h->kp));
+        }
+        if (!tc.entries.empty())
+            out.push_back(BatchLaunch{2, 0, false, place(tc.entries.data(), tc.entries.size() * sizeof(tc.entries[0])),
+                                      (int)tc.entries.size(), tc.blocks});
+        std::vector<NWArgs> tn;
+        for (bpmf_ctx* h : b->jobs) tn.push_back(nw_args(h, s, offset));
+        out.push_back(BatchLaunch{3, 0, false, place(tn.data(), tn.size() * sizeof(tn[0])), (int)tn.size(),
+                                  (int64_t)tn.size()});
+    };
+    try {
+        for (int s = 0; s < 2; ++s) {
+            build_hyper(s, 0, b->hyper[s]);
+            // the CUDA-core row launches by (kp, route); the tensor-core bins per job
+            for (int kp : kps)
+                for (int r1 = 0; r1 < 2; ++r1) {
+                    std::vector<std::pair<double, bpmf_ctx*>> order;
+                    double total = 0.0;
+                    for (bpmf_ctx* h : b->jobs) {
+                        if (h->kp != kp) continue;
+                        const RowArgs a = row_args(h, s);
+                        const int64_t items = rows_warp_items(a, r1 != 0);
+                        if (items <= 0) continue;
+                        const DevSide& d = h->side[s];
+                        const double ratings = (double)(h->nnz - d.long_ratings);
+                        const double cost = 2.0 * (double)items + (r1 ? 0.0 : ratings / 64.0);
+                        order.push_back({cost, h});
+                        total += cost;
+                    }
+                    if (order.empty()) continue;
+                    std::stable_sort(order.begin(), order.end(),
+                                     [](const auto& x, const auto& y) { return x.first > y.first; });
+                    const int64_t waves = 16LL * b->num_sms * rows_warp_resident_blocks(kp);
+                    TableBuilder<RowArgs> t;
+                    for (auto& o : order) {
+                        const RowArgs a = row_args(o.second, s);
+                        t.add(a, batch_row_blocks(rows_warp_items(a, r1 != 0), o.first, total, waves));
+                    }
+                    b->rows[s].push_back(BatchLaunch{0, kp, r1 != 0,
+                                                     place(t.entries.data(), t.entries.size() * sizeof(t.entries[0])),
+                                                     (int)t.entries.size(), t.blocks});
+                }
+            std::vector<std::pair<int64_t, bpmf_ctx*>> tc;
+            for (bpmf_ctx* h : b->jobs)
+                if (h->tc && h->side[s].n_long > 0) tc.push_back({h->side[s].long_ratings, h});
+            std::stable_sort(tc.begin(), tc.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+            for (auto& o : tc) b->tc[s].push_back(o.second);
+        }
+        build_hyper(b->first, 1, b->hyper_next);
+        TableBuilder<PredictArgs> tp, tf;
+        for (bpmf_ctx* h : b->jobs) {
+            const PredictArgs p = pred_args(h);
+            if (h->T > 0) tp.add(p, h->pred_blocks);
+            BatchEntry<PredictArgs> e;
+            e.args = p;
+            e.first = 0;
+            e.count = h->T > 0 ? h->pred_blocks : 0;
+            tf.entries.push_back(e);
+        }
+        b->predict = BatchLaunch{4, 0, false, nullptr, (int)tp.entries.size(), tp.blocks};
+        if (!tp.entries.empty())
+            b->predict.table = place(tp.entries.data(), tp.entries.size() * sizeof(tp.entries[0]));
+        b->finish = BatchLaunch{5, 0, false, place(tf.entries.data(), tf.entries.size() * sizeof(tf.entries[0])),
+                                (int)tf.entries.size(), 0};
+    } catch (const std::bad_alloc&) {
+        batch_free(b);
+        return BPMF_ENOMEM;
+    }
+    if (cudaMalloc(&b->dev, image.size()) != cudaSuccess ||
+        cudaMemcpy(b->dev, image.data(), image.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        batch_free(b);
+        return BPMF_ENOMEM;
+    }
+    // table offsets into device addresses
+    auto fix = [&](BatchLaunch& l) {
+        if (l.n > 0) l.table = static_cast<char*>(b->dev) + reinterpret_cast<size_t>(l.table);
+    };
+    for (int s = 0; s < 2; ++s) {
+        for (BatchLaunch& l : b->hyper[s]) fix(l);
+        for (BatchLaunch& l : b->rows[s]) fix(l);
+    }
+    for (BatchLaunch& l : b->hyper_next) fix(l);
+    fix(b->predict);
+    fix(b->finish);
+    *out = b;
+    return BPMF_OK;
+}
+
+int bpmf_batch_sweep(bpmf_batch b, int32_t n_sweeps)
+{
+    if (!b || n_sweeps < 0) return BPMF_EINVAL;
+    if (n_sweeps == 0) return BPMF_OK;
+    const NvtxRange range("bpmf_batch_sweep");
+    int rc = batch_order(b, true);
+    // the first side's hyper step of the first sweep; the sweeps but the last draw the
+    // next one's beside their own work (one captured graph, made on first use when the
+    // batch stream can be captured); the last leaves it undrawn, as bpmf_sweep does
+    if (rc == BPMF_OK) rc = batch_run(b, b->hyper[b->first], b->stream);
+    if (rc == BPMF_OK && n_sweeps > 1 && b->graph_state == 0) {
+        b->graph_state = -1;
+        if (b->stream && cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const int64_t l0 = b->launches;
+            const int rcb = batch_sweep_body(b, true);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+            b->graph_launches = b->launches - l0;
+            b->launches = l0;
+            if (rcb == BPMF_OK && e == cudaSuccess && g &&
+                cudaGraphInstantiate(&b->graph, g, 0) == cudaSuccess)
+                b->graph_state = 1;
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();
+    }
+    for (int32_t it = 0; it < n_sweeps && rc == BPMF_OK; ++it) {
+        const bool last = it + 1 == n_sweeps;
+        if (!last && b->graph_state > 0) {
+            rc = cuda_rc(cudaGraphLaunch(b->graph, b->stream));
+            b->launches += b->graph_launches;
+        } else {
+            rc = batch_sweep_body(b, !last);
+        }
+    }
+    if (rc == BPMF_OK) rc = batch_order(b, false);
+    return rc;
+}
+
+int bpmf_batch_launch_count(bpmf_batch b, int64_t* launches)
+{
+    if (!b || !launches) return BPMF_EINVAL;
+    *launches = b->launches;
+    return BPMF_OK;
+}
+
+int bpmf_batch_destroy(bpmf_batch b)
+{
+    if (!b) return BPMF_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    return BPMF_OK;
 }
 
 int bpmf_predict(bpmf_handle h, int64_t n, const int32_t* i, const int32_t* j, float* out,

@@ -152,6 +152,82 @@ int rows_warp_launches(const RowArgs& a);
 // Floats of one segment's partial in `part` (Gram rows owned by a lane, and the
 // right-hand side, lane-interleaved).
 int warp_partial_floats(int kp);
+// ---- batched launches: one launch runs the same step for many jobs --------------
+// A job's share of a batched launch: its arguments and the blocks [first, first + count)
+// of the launch's grid, which run the job's work exactly as a launch of `count` blocks of
+// its own would (a job's result does not depend on the other jobs in the launch).
+// Tables are ordered by `first`.
+template <class A>
+struct BatchEntry {
+    A args;
+    int32_t first;
+    int32_t count;
+};
+// The entry whose blocks hold block b.
+template <class A>
+__device__ __forceinline__ int batch_find(const BatchEntry<A>* t, int n, int b)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t[mid].first <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+// Work items of a row launch (segments and rows of the Gram route, or rank-one rows).
+int64_t rows_warp_items(const RowArgs& a, bool rank_one);
+// CTAs of the CUDA-core row kernel one SM holds at once for this kp.
+int rows_warp_resident_blocks(int kp);
+cudaError_t launch_rows_warp_batch(const BatchEntry<RowArgs>* t, int n, int64_t blocks, int kp,
+                                   bool rank_one, cudaStream_t s);
+// The hyper step's reduction for many jobs of one kp (blocks: nred + draw blocks each).
+struct ReduceArgs {
+    const float* X;
+    int64_t rows;
+    int shiftK;
+    double* shift64;
+    double* partials;
+    int nred;
+    NWArgs draws;
+};
+cudaError_t launch_hyper_reduce_batch(const BatchEntry<ReduceArgs>* t, int n, int64_t blocks,
+                                      int kp, cudaStream_t s);
+int hyper_draw_blocks(int K);
+// The fixed-order combine for many jobs (E = kp + kp^2 doubles each, 128 per block).
+struct CombineArgs {
+    const double* partials;
+    int nblocks, E;
+    double* sums;
+};
+int hyper_combine_blocks(int kp);
+cudaError_t launch_hyper_combine_batch(const BatchEntry<CombineArgs>* t, int n, int64_t blocks,
+                                       cudaStream_t s);
+// The Normal-Wishart draw for many jobs: one CTA each.
+cudaError_t launch_nw_sample_batch(const NWArgs* t, int n, cudaStream_t s);
+// Test-set prediction for many jobs: the blocks of each job (its own prediction block
+// count), then one thread per job for its RMSEs (and, with advance, its sweep counter).
+struct PredictArgs {
+    const int32_t* ti;
+    const int32_t* tj;
+    const float* tr;
+    int64_t T;
+    const float* U;
+    const float* V;
+    int ld, kp;
+    double rbar;
+    int clip;
+    double lo, hi;
+    int burn_in;
+    double* psum;
+    Control* ctl;
+    double* partials;
+};
+cudaError_t launch_predict_batch(const BatchEntry<PredictArgs>* t, int n, int64_t blocks,
+                                 cudaStream_t s);
+cudaError_t launch_predict_finish_batch(const BatchEntry<PredictArgs>* t, int n, bool advance,
+                                        cudaStream_t s);
+
 // Row updates with the Gram on tensor cores (kp == 64, rows of the long bin).
 // Scratch device memory for one call (allocated and returned inside it).
 struct TempAlloc {

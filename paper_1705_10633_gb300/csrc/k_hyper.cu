@@ -90,16 +90,16 @@ int hyper_reduce_blocks(int64_t rows, int num_sms)
     return (int)want;
 }
 
+// Block `bid` of one side's reduction launch (nred reduction blocks, then draw blocks).
 template <int KT>
-__global__ void __launch_bounds__(kRedThreads) hyper_reduce_kernel(const float* __restrict__ X,
-                                                                   int64_t rows, int shiftK,
-                                                                   double* __restrict__ shift64,
-                                                                   double* __restrict__ partials,
-                                                                   int nred, NWArgs draws)
+__device__ __forceinline__ void hyper_reduce_body(const float* __restrict__ X, int64_t rows,
+                                                  int shiftK, double* __restrict__ shift64,
+                                                  double* __restrict__ partials, int nred,
+                                                  const NWArgs& draws, int bid)
 {
     // blocks past the reduction's draw the Normal-Wishart step's random numbers
-    if ((int)blockIdx.x >= nred) {
-        nw_draws_thread(draws, ((int)blockIdx.x - nred) * kRedThreads + (int)threadIdx.x);
+    if (bid >= nred) {
+        nw_draws_thread(draws, (bid - nred) * kRedThreads + (int)threadIdx.x);
         return;
     }
     // The scatter is a 16 x 16 grid of TT x TT tiles; threads 0..135 own the tiles on
@@ -137,13 +137,13 @@ __global__ void __launch_bounds__(kRedThreads) hyper_reduce_kernel(const float* 
             const double tot = (part[0][t] + part[1][t]) + (part[2][t] + part[3][t]);
             const double v = (t < shiftK && n > 0) ? tot / (double)n : 0.0;
             sh[t] = (float)v;
-            if (blockIdx.x == 0) shift64[t] = v;
+            if (bid == 0) shift64[t] = v;
         }
     } else if (t < KT) {
         sh[t] = (float)shift64[t];
     }
-    const int64_t r0 = rows * blockIdx.x / nred;
-    const int64_t r1 = rows * (blockIdx.x + 1) / nred;
+    const int64_t r0 = rows * bid / nred;
+    const int64_t r1 = rows * (bid + 1) / nred;
     // a chunk's rows in registers (rows past the slab's end zero)
     float4 pf[NPF];
     auto load_chunk = [&](int64_t base) {
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kRedThreads) hyper_reduce_kernel(const float* 
         }
         __syncthreads();
     }
-    double* out = partials + (size_t)blockIdx.x * hyper_partial_doubles(KT);
+    double* out = partials + (size_t)bid * hyper_partial_doubles(KT);
     if (t < KT) out[t] = s64;
     if (tile_on) {
         // entry (p, q) and its mirror (q, p): fmaf(x_p, x_q, .) equals fmaf(x_q, x_p, .),
@@ -226,6 +226,43 @@ __global__ void __launch_bounds__(kRedThreads) hyper_reduce_kernel(const float* 
             }
     }
 }
+
+template <int KT>
+__global__ void __launch_bounds__(kRedThreads) hyper_reduce_kernel(const float* __restrict__ X,
+                                                                   int64_t rows, int shiftK,
+                                                                   double* __restrict__ shift64,
+                                                                   double* __restrict__ partials,
+                                                                   int nred, NWArgs draws)
+{
+    hyper_reduce_body<KT>(X, rows, shiftK, shift64, partials, nred, draws, (int)blockIdx.x);
+}
+
+template <int KT>
+__global__ void __launch_bounds__(kRedThreads)
+    hyper_reduce_batch_kernel(const BatchEntry<ReduceArgs>* __restrict__ t, int n)
+{
+    const int j = batch_find(t, n, (int)blockIdx.x);
+    const ReduceArgs r = t[j].args;
+    hyper_reduce_body<KT>(r.X, r.rows, r.shiftK, r.shift64, r.partials, r.nred, r.draws,
+                          (int)blockIdx.x - t[j].first);
+}
+
+cudaError_t launch_hyper_reduce_batch(const BatchEntry<ReduceArgs>* t, int n, int64_t blocks,
+                                      int kp, cudaStream_t s)
+{
+    if (n <= 0 || blocks <= 0) return cudaSuccess;
+    const unsigned g = (unsigned)blocks;
+    switch (kp) {
+    case 16: hyper_reduce_batch_kernel<16><<<g, kRedThreads, 0, s>>>(t, n); break;
+    case 32: hyper_reduce_batch_kernel<32><<<g, kRedThreads, 0, s>>>(t, n); break;
+    case 48: hyper_reduce_batch_kernel<48><<<g, kRedThreads, 0, s>>>(t, n); break;
+    case 64: hyper_reduce_batch_kernel<64><<<g, kRedThreads, 0, s>>>(t, n); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int hyper_draw_blocks(int K) { return (nw_draws_threads(K) + kRedThreads - 1) / kRedThreads; }
 
 static cudaError_t reduce_launch(const float* X, int64_t rows, int kp, int shiftK, double* shift64,
                                  double* partials, int nblocks, int ndraw, const NWArgs& draws,
@@ -253,14 +290,13 @@ cudaError_t launch_hyper_reduce(const float* X, int64_t rows, int kp, const doub
 cudaError_t launch_hyper_stats_draws(const float* X, int64_t rows, int K, int kp, double* shift64,
                                      double* partials, int nblocks, const NWArgs& a, cudaStream_t s)
 {
-    const int ndraw = (nw_draws_threads(K) + kRedThreads - 1) / kRedThreads;
-    return reduce_launch(X, rows, kp, K, shift64, partials, nblocks, ndraw, a, s);
+    return reduce_launch(X, rows, kp, K, shift64, partials, nblocks, hyper_draw_blocks(K), a, s);
 }
 
-__global__ void hyper_combine_kernel(const double* __restrict__ partials, int nblocks, int E,
-                                     double* __restrict__ sums)
+__device__ __forceinline__ void hyper_combine_body(const double* __restrict__ partials,
+                                                   int nblocks, int E, double* __restrict__ sums,
+                                                   int e)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     // four interleaved accumulators (more loads in flight), added in a fixed order
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -275,11 +311,35 @@ __global__ void hyper_combine_kernel(const double* __restrict__ partials, int nb
     sums[e] = (a0 + a1) + (a2 + a3);
 }
 
+__global__ void hyper_combine_kernel(const double* __restrict__ partials, int nblocks, int E,
+                                     double* __restrict__ sums)
+{
+    hyper_combine_body(partials, nblocks, E, sums, (int)(blockIdx.x * blockDim.x + threadIdx.x));
+}
+
+__global__ void hyper_combine_batch_kernel(const BatchEntry<CombineArgs>* __restrict__ t, int n)
+{
+    const int j = batch_find(t, n, (int)blockIdx.x);
+    const CombineArgs c = t[j].args;
+    hyper_combine_body(c.partials, c.nblocks, c.E, c.sums,
+                       ((int)blockIdx.x - t[j].first) * (int)blockDim.x + (int)threadIdx.x);
+}
+
+int hyper_combine_blocks(int kp) { return ((int)hyper_partial_doubles(kp) + 127) / 128; }
+
 cudaError_t launch_hyper_combine(const double* partials, int nblocks, int kp, double* sums,
                                  cudaStream_t s)
 {
     const int E = (int)hyper_partial_doubles(kp);
-    hyper_combine_kernel<<<(E + 127) / 128, 128, 0, s>>>(partials, nblocks, E, sums);
+    hyper_combine_kernel<<<hyper_combine_blocks(kp), 128, 0, s>>>(partials, nblocks, E, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hyper_combine_batch(const BatchEntry<CombineArgs>* t, int n, int64_t blocks,
+                                       cudaStream_t s)
+{
+    if (n <= 0 || blocks <= 0) return cudaSuccess;
+    hyper_combine_batch_kernel<<<(unsigned)blocks, 128, 0, s>>>(t, n);
     return cudaGetLastError();
 }
 
@@ -373,7 +433,7 @@ __device__ double nw_sum(const NWArgs& a, int e)
     return (a0 + a1) + (a2 + a3);
 }
 
-__global__ void __launch_bounds__(kNWThreads) nw_sample_kernel(NWArgs a)
+__device__ __forceinline__ void nw_sample_body(const NWArgs& a)
 {
     extern __shared__ double nw_sm[];
     const int K = a.K, KK = K * K, t = threadIdx.x;
@@ -524,18 +584,39 @@ __global__ void __launch_bounds__(kNWThreads) nw_sample_kernel(NWArgs a)
     }
 }
 
+__global__ void __launch_bounds__(kNWThreads) nw_sample_kernel(NWArgs a) { nw_sample_body(a); }
+
+// One CTA per job.
+__global__ void __launch_bounds__(kNWThreads) nw_sample_batch_kernel(const NWArgs* __restrict__ t)
+{
+    const NWArgs a = t[blockIdx.x];
+    nw_sample_body(a);
+}
+
+static size_t nw_smem(int K) { return sizeof(double) * (3 * (size_t)K * K + 5 * (size_t)K); }
+
 cudaError_t launch_nw_sample(const NWArgs& a, cudaStream_t s)
 {
-    const size_t smem = sizeof(double) * (3 * (size_t)a.K * a.K + 5 * (size_t)a.K);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(nw_sample_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(sizeof(double) * (3 * 64 * 64 + 5 * 64)));
+                                             (int)nw_smem(64));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    nw_sample_kernel<<<1, kNWThreads, smem, s>>>(a);
+    nw_sample_kernel<<<1, kNWThreads, nw_smem(a.K), s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nw_sample_batch(const NWArgs* t, int n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(nw_sample_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)nw_smem(64));
+    if (e != cudaSuccess) return e;
+    nw_sample_batch_kernel<<<(unsigned)n, kNWThreads, nw_smem(64), s>>>(t);
     return cudaGetLastError();
 }
 

@@ -158,18 +158,18 @@ __device__ __forceinline__ double block_sum(double v, double* red)
     return s;
 }
 
-__global__ void __launch_bounds__(kPredThreads) predict_kernel(
+// Block `bid` of `nblocks` of one job's prediction launch.
+__device__ __forceinline__ void predict_body(
     const int32_t* __restrict__ ti, const int32_t* __restrict__ tj, const float* __restrict__ tr,
     int64_t T, const float* __restrict__ U, const float* __restrict__ V, int ld, int kp,
     double rbar, int clip, double lo, double hi, int burn_in, double* __restrict__ psum,
-    const Control* __restrict__ ctl, double* __restrict__ partials)
+    const Control* __restrict__ ctl, double* __restrict__ partials, int64_t bid, int64_t nblocks)
 {
     __shared__ double red[kPredThreads / 32];
     const int acc = (long long)ctl->sweep >= (long long)burn_in ? 1 : 0;
     const long long n_new = ctl->n_avg + acc;
     double se = 0.0, sa = 0.0;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < T;
-         t += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t t = bid * blockDim.x + threadIdx.x; t < T; t += nblocks * blockDim.x) {
         const int i = ti[t], j = tj[t];
         double p = rbar + (double)dot_row(U + (int64_t)i * ld, V + (int64_t)j * ld, kp);
         if (clip) p = fmin(fmax(p, lo), hi);
@@ -188,9 +188,29 @@ __global__ void __launch_bounds__(kPredThreads) predict_kernel(
     const double bse = block_sum(se, red);
     const double bsa = block_sum(sa, red);
     if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = bse;
-        partials[2 * blockIdx.x + 1] = bsa;
+        partials[2 * bid] = bse;
+        partials[2 * bid + 1] = bsa;
     }
+}
+
+__global__ void __launch_bounds__(kPredThreads) predict_kernel(
+    const int32_t* __restrict__ ti, const int32_t* __restrict__ tj, const float* __restrict__ tr,
+    int64_t T, const float* __restrict__ U, const float* __restrict__ V, int ld, int kp,
+    double rbar, int clip, double lo, double hi, int burn_in, double* __restrict__ psum,
+    const Control* __restrict__ ctl, double* __restrict__ partials)
+{
+    predict_body(ti, tj, tr, T, U, V, ld, kp, rbar, clip, lo, hi, burn_in, psum, ctl, partials,
+                 blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kPredThreads)
+    predict_batch_kernel(const BatchEntry<PredictArgs>* __restrict__ tab, int n)
+{
+    const int j = batch_find(tab, n, (int)blockIdx.x);
+    const PredictArgs p = tab[j].args;
+    predict_body(p.ti, p.tj, p.tr, p.T, p.U, p.V, p.ld, p.kp, p.rbar, p.clip, p.lo, p.hi,
+                 p.burn_in, p.psum, p.ctl, p.partials, (int64_t)blockIdx.x - tab[j].first,
+                 tab[j].count);
 }
 
 cudaError_t launch_predict(const int32_t* ti, const int32_t* tj, const float* tr, int64_t T,
@@ -203,10 +223,9 @@ cudaError_t launch_predict(const int32_t* ti, const int32_t* tj, const float* tr
     return cudaGetLastError();
 }
 
-__global__ void predict_finish_kernel(const double* partials, int nblocks, int64_t T, int burn_in,
-                                      Control* ctl)
+__device__ __forceinline__ void predict_finish_body(const double* partials, int nblocks,
+                                                    int64_t T, int burn_in, Control* ctl)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int acc = (long long)ctl->sweep >= (long long)burn_in ? 1 : 0;
     const long long n_new = ctl->n_avg + acc;
     double se = 0.0, sa = 0.0;
@@ -222,6 +241,41 @@ __global__ void predict_finish_kernel(const double* partials, int nblocks, int64
         ctl->rmse_sample = (double)NAN;
         ctl->rmse_avg = (double)NAN;
     }
+}
+
+__global__ void predict_finish_kernel(const double* partials, int nblocks, int64_t T, int burn_in,
+                                      Control* ctl)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    predict_finish_body(partials, nblocks, T, burn_in, ctl);
+}
+
+// One thread per job: the job's RMSEs from its prediction partials (its `count` blocks;
+// none without test points), then, with advance, its sweep counter moved on.
+__global__ void predict_finish_batch_kernel(const BatchEntry<PredictArgs>* __restrict__ tab, int n,
+                                            int advance)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const PredictArgs p = tab[j].args;
+    predict_finish_body(p.partials, p.T > 0 ? tab[j].count : 0, p.T, p.burn_in, p.ctl);
+    if (advance) p.ctl->sweep += 1ull;
+}
+
+cudaError_t launch_predict_batch(const BatchEntry<PredictArgs>* t, int n, int64_t blocks,
+                                 cudaStream_t s)
+{
+    if (n <= 0 || blocks <= 0) return cudaSuccess;
+    predict_batch_kernel<<<(unsigned)blocks, kPredThreads, 0, s>>>(t, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predict_finish_batch(const BatchEntry<PredictArgs>* t, int n, bool advance,
+                                        cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    predict_finish_batch_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(t, n, advance ? 1 : 0);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_predict_finish(const double* partials, int nblocks, int64_t T, int burn_in,

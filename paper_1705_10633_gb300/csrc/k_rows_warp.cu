@@ -180,8 +180,10 @@ __device__ __forceinline__ void add_partial(const float* pp, int lane, float (&a
 // kR1 = false: the segments of the split rows, then rows nsplit .. nrows - nrank_one - 1
 // of the bin on the Gram route; kR1 = true: the last nrank_one rows (the shortest) on
 // the rank-one route.  Two instantiations keep each route's register budget its own.
+// The kernel's work for one job: this CTA is block `bid` of the `nblocks` blocks the
+// job's items are dealt over (items q = bid * 4 + warp, step 4 nblocks).
 template <int KT, bool kR1>
-__global__ void __launch_bounds__(kWarpsPerCta * 32) rows_warp_kernel(RowArgs a)
+__device__ __forceinline__ void rows_warp_body(const RowArgs& a, int64_t bid, int64_t nblocks)
 {
     using W = WarpLayout<KT>;
     extern __shared__ float4 dyn_smem4[];
@@ -200,11 +202,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) rows_warp_kernel(RowArgs a)
     const int i2 = 63 - lane;
     const bool v1 = i1 < KT;
     const bool v2 = W::TWO && i2 < KT;
-    const int64_t nwarps = (int64_t)gridDim.x * kWarpsPerCta;
+    const int64_t nwarps = nblocks * kWarpsPerCta;
     bool bad = false;
 
     const int64_t nitems = kR1 ? a.nrank_one : a.nsegs + a.nrows - a.nsplit - a.nrank_one;
-    for (int64_t q = (int64_t)blockIdx.x * kWarpsPerCta + wib; q < nitems; q += nwarps) {
+    for (int64_t q = bid * kWarpsPerCta + wib; q < nitems; q += nwarps) {
         // Gram rows i1, i2 accumulate in the registers the Cholesky works on
         float a1[RowRegs<KT>::NR1];
         float a2[RowRegs<KT>::NA2];
@@ -315,19 +317,64 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32) rows_warp_kernel(RowArgs a)
 }
 
 template <int KT, bool kR1>
+__global__ void __launch_bounds__(kWarpsPerCta * 32) rows_warp_kernel(RowArgs a)
+{
+    rows_warp_body<KT, kR1>(a, blockIdx.x, gridDim.x);
+}
+
+// Many jobs in one launch: each CTA finds its job's entry and runs the job's work as
+// block bid of the job's count (the same per-row arithmetic as a launch of its own).
+// The job's arguments are staged in shared memory: the body reads them where it needs
+// them, as a launch of its own reads its parameters, instead of holding a copy of the
+// whole struct in registers (which cost the K = 16 kernel half its occupancy and the
+// K = 64 one spills).
+template <int KT, bool kR1>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+    rows_warp_batch_kernel(const BatchEntry<RowArgs>* __restrict__ t, int n)
+{
+    __shared__ __align__(16) unsigned char args_raw[sizeof(RowArgs)];
+    __shared__ int64_t span[2];
+    if (threadIdx.x == 0) {
+        const int j = batch_find(t, n, (int)blockIdx.x);
+        span[0] = (int64_t)blockIdx.x - t[j].first;
+        span[1] = t[j].count;
+        // the whole struct, 4 bytes at a time (RowArgs is 8-byte aligned)
+        const unsigned int* src = reinterpret_cast<const unsigned int*>(&t[j].args);
+        unsigned int* dst = reinterpret_cast<unsigned int*>(args_raw);
+        for (int w = 0; w < (int)(sizeof(RowArgs) / 4); ++w) dst[w] = __ldg(src + w);
+    }
+    __syncthreads();
+    rows_warp_body<KT, kR1>(*reinterpret_cast<const RowArgs*>(args_raw), span[0], span[1]);
+}
+
+template <int KT, bool kR1>
+static cudaError_t warp_kernel_attrs(size_t smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(rows_warp_kernel<KT, kR1>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(rows_warp_kernel<KT, kR1>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(rows_warp_batch_kernel<KT, kR1>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(rows_warp_batch_kernel<KT, kR1>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
+template <int KT, bool kR1>
 static cudaError_t launch_route(const RowArgs& a, int num_sms, cudaStream_t s)
 {
     using W = WarpLayout<KT>;
     const int64_t nitems = kR1 ? a.nrank_one : a.nsegs + a.nrows - a.nsplit - a.nrank_one;
     if (nitems <= 0) return cudaSuccess;
     const size_t smem = sizeof(float) * (size_t)W::PER_WARP_ALIGNED * kWarpsPerCta;
-    cudaError_t e = cudaFuncSetAttribute(rows_warp_kernel<KT, kR1>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     // all of the unified L1 / shared memory as shared, so residency is set by registers
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(rows_warp_kernel<KT, kR1>,
-                                 cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared);
+    cudaError_t e = warp_kernel_attrs<KT, kR1>(smem);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows_warp_kernel<KT, kR1>,
@@ -375,6 +422,63 @@ cudaError_t launch_rows_warp(const RowArgs& a, int kp, int num_sms, cudaStream_t
 int rows_warp_launches(const RowArgs& a)
 {
     return (a.nsegs + a.nrows - a.nsplit - a.nrank_one > 0 ? 1 : 0) + (a.nrank_one > 0 ? 1 : 0);
+}
+
+int64_t rows_warp_items(const RowArgs& a, bool rank_one)
+{
+    return rank_one ? a.nrank_one : a.nsegs + a.nrows - a.nsplit - a.nrank_one;
+}
+
+template <int KT, bool kR1>
+static cudaError_t launch_batch_kt(const BatchEntry<RowArgs>* t, int n, int64_t blocks,
+                                   cudaStream_t s)
+{
+    using W = WarpLayout<KT>;
+    const size_t smem = sizeof(float) * (size_t)W::PER_WARP_ALIGNED * kWarpsPerCta;
+    cudaError_t e = warp_kernel_attrs<KT, kR1>(smem);
+    if (e != cudaSuccess) return e;
+    rows_warp_batch_kernel<KT, kR1><<<(unsigned)blocks, kWarpsPerCta * 32, smem, s>>>(t, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_warp_batch(const BatchEntry<RowArgs>* t, int n, int64_t blocks, int kp,
+                                   bool rank_one, cudaStream_t s)
+{
+    if (n <= 0 || blocks <= 0) return cudaSuccess;
+    switch (kp * 2 + (rank_one ? 1 : 0)) {
+    case 32: return launch_batch_kt<16, false>(t, n, blocks, s);
+    case 33: return launch_batch_kt<16, true>(t, n, blocks, s);
+    case 64: return launch_batch_kt<32, false>(t, n, blocks, s);
+    case 65: return launch_batch_kt<32, true>(t, n, blocks, s);
+    case 96: return launch_batch_kt<48, false>(t, n, blocks, s);
+    case 97: return launch_batch_kt<48, true>(t, n, blocks, s);
+    case 128: return launch_batch_kt<64, false>(t, n, blocks, s);
+    case 129: return launch_batch_kt<64, true>(t, n, blocks, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int rows_warp_resident_blocks(int kp)
+{
+    int per_sm = 1;
+    auto occ = [&](auto kernel, size_t smem) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarpsPerCta * 32, smem) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+    };
+    switch (kp) {
+    case 16: warp_kernel_attrs<16, false>(sizeof(float) * WarpLayout<16>::PER_WARP_ALIGNED * kWarpsPerCta);
+             occ(rows_warp_batch_kernel<16, false>, sizeof(float) * WarpLayout<16>::PER_WARP_ALIGNED * kWarpsPerCta); break;
+    case 32: warp_kernel_attrs<32, false>(sizeof(float) * WarpLayout<32>::PER_WARP_ALIGNED * kWarpsPerCta);
+             occ(rows_warp_batch_kernel<32, false>, sizeof(float) * WarpLayout<32>::PER_WARP_ALIGNED * kWarpsPerCta); break;
+    case 48: warp_kernel_attrs<48, false>(sizeof(float) * WarpLayout<48>::PER_WARP_ALIGNED * kWarpsPerCta);
+             occ(rows_warp_batch_kernel<48, false>, sizeof(float) * WarpLayout<48>::PER_WARP_ALIGNED * kWarpsPerCta); break;
+    default: warp_kernel_attrs<64, false>(sizeof(float) * WarpLayout<64>::PER_WARP_ALIGNED * kWarpsPerCta);
+             occ(rows_warp_batch_kernel<64, false>, sizeof(float) * WarpLayout<64>::PER_WARP_ALIGNED * kWarpsPerCta); break;
+    }
+    return per_sm < 1 ? 1 : per_sm;
 }
 
 }  // namespace bpmf

@@ -175,3 +175,16 @@ def test_device_bytes_is_host_only_and_follows_the_buffers(bp):
     with pytest.raises(bp.BpmfError) as ei:
         bp.bpmf_device_bytes(prob.M, prob.N, 64, prob.csr_ptr, col, 0, num_sms=152)
     assert ei.value.code == bp.BPMF_EINVAL
+
+
+def test_batch_object_rejects_bad_arguments_on_the_host(bp):
+    lib = bp.lib()
+    out = C.c_void_p()
+    arr = (C.c_void_p * 1)(None)
+    assert lib.bpmf_batch_create(arr, 1, None, C.byref(out)) == bp.BPMF_EINVAL  # NULL handle
+    assert lib.bpmf_batch_create(arr, 0, None, C.byref(out)) == bp.BPMF_EINVAL  # no chains
+    assert lib.bpmf_batch_create(arr, 1, None, None) == bp.BPMF_EINVAL
+    assert lib.bpmf_batch_sweep(None, 1) == bp.BPMF_EINVAL
+    n = C.c_int64()
+    assert lib.bpmf_batch_launch_count(None, C.byref(n)) == bp.BPMF_EINVAL
+    assert lib.bpmf_batch_destroy(None) == bp.BPMF_OK
