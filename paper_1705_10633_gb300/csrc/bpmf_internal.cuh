@@ -252,9 +252,11 @@ cudaError_t check_csc_device(const int64_t* built_ptr, const int32_t* built_row,
                              int64_t N, int64_t nnz, double rbar, const TempAlloc& tmp, bool* same,
                              cudaStream_t s);
 
-// One slot of the tensor-core route's scratch (K = 64): the lower triangle of
-// Lambda_i in float4 chunks, chunk column c (columns 4c .. 4c + 3) holding rows
-// 4c .. 63 consecutively from float4 gram_chunk_offset(c), then b_i (64 floats).
+// One slot of the tensor-core route's scratch (K = 64): the lower triangle of the
+// row's Gram sum_c y_c y_c^T in float4 chunks, chunk column c (columns 4c .. 4c + 3)
+// holding rows 4c .. 63 consecutively from float4 gram_chunk_offset(c), then
+// sum_c r_c y_c (64 floats); Lambda_i = Lambda_X + alpha Gram and b_i =
+// Lambda_X mu_X + alpha sum_c r_c y_c are formed from it by the factorisation kernel.
 constexpr int kGramChunks = 544;
 constexpr int kGramSlotFloats = 4 * kGramChunks + 64;
 __host__ __device__ constexpr int gram_chunk_offset(int c) { return c * (66 - 2 * c); }

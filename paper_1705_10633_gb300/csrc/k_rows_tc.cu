@@ -13,9 +13,10 @@
 // 128B-swizzled MN-major atoms (l rows, h rows, ratings in the first two columns
 // of an otherwise zero atom); A starts at the l atom, B at the h atom.
 //
-// This kernel only forms Lambda_i = Lambda_X + alpha Gram and b_i = Lambda_X mu_X +
-// alpha (H + L)^T r and writes them to the row's slot of the scratch (layout in
-// bpmf_internal.cuh); k_rows_chol.cu factors them.  Keeping the factorisation out
+// This kernel only forms the Gram (H + L)^T (H + L) and (H + L)^T r of each row and
+// writes them to the row's slot of the scratch (layout in bpmf_internal.cuh);
+// k_rows_chol.cu forms Lambda_i = Lambda_X + alpha Gram and b_i = Lambda_X mu_X +
+// alpha (H + L)^T r as it loads the slot, and factors them.  Keeping the factorisation out
 // of this kernel leaves the SM's issue slots and shared memory to the gather and
 // the tensor core, and the factorisation kernel runs with every warp of the SM.
 //
@@ -33,7 +34,9 @@
 //   warps 4-7     drain (TMEM lane quarters 0-3): TMEM -> registers, summed over the
 //                 row's accumulation chunks; at the row's end the L^T H rows go
 //                 through a shared staging buffer so the H^T H rows can add L^T H and
-//                 its transpose, add Lambda_X and store the packed lower triangle
+//                 its transpose and store the packed lower triangle of the Gram (the
+//                 factorisation kernel scales it by alpha and adds Lambda_X as it loads
+//                 it)
 // Stages of 64 ratings flow producer -> MMA through mbarriers; accumulators MMA ->
 // drain.  A long row is accumulated in chunks of 16 stages, each in a fresh
 // accumulator that the drain adds into its registers: the tensor core's accumulation
@@ -73,8 +76,7 @@ constexpr uint32_t kStagingFloats = 64 * 64 + 64;  // L^T H rows (sw64 layout) a
 
 constexpr uint32_t kOffStages = 0;
 constexpr uint32_t kOffStaging = kOffStages + kNStage * kStageBytes;
-constexpr uint32_t kOffPrior = kOffStaging + kGroups * kStagingFloats * 4;  // packed Lambda_X, Lambda_X mu_X
-constexpr uint32_t kOffRowRing = kOffPrior + kGramSlotFloats * 4;            // kRowRing x 32 B
+constexpr uint32_t kOffRowRing = kOffStaging + kGroups * kStagingFloats * 4;  // kRowRing x 32 B
 constexpr uint32_t kOffIdxRing = kOffRowRing + kRowRing * 32;                // kIdxRing x (64 idx + 64 val)
 constexpr uint32_t kOffBars = kOffIdxRing + kIdxRing * 512;
 constexpr int kNumBars = 2 * kNStage + 2 * kNumAcc + 2 * kRowRing + 2 * kIdxRing + 1;
@@ -278,8 +280,6 @@ __global__ void __launch_bounds__(kThreads, kGramCtasPerSm) rows_gram_kernel(Row
                                              ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(sm);
     float* staging = reinterpret_cast<float*>(sm + kOffStaging);
-    float4* prior4 = reinterpret_cast<float4*>(sm + kOffPrior);
-    float* prior_mu = reinterpret_cast<float*>(sm + kOffPrior) + 4 * kGramChunks;
     long long* row_ring = reinterpret_cast<long long*>(sm + kOffRowRing);  // [row, p0, p1, slot]
     const int* idx_ring = reinterpret_cast<const int*>(sm + kOffIdxRing);
     const float* val_ring = reinterpret_cast<const float*>(sm + kOffIdxRing + 256);
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, kGramCtasPerSm) rows_gram_kernel(Row
     const WaitCtx wc{abort_flag, a.timeout_ns, a.ctl};
 
     // ---- set-up: zero the ratings atoms (and the l atoms, which the BF16 Gram leaves
-    // unused), the prior precision packed like a scratch slot, barriers, TMEM
+    // unused), barriers, TMEM
     for (uint32_t e = tid; e < kNStage * kTileBytes / 16; e += kThreads) {
         const uint32_t s = e / (kTileBytes / 16), o = e % (kTileBytes / 16);
         *reinterpret_cast<uint4*>(sm + kOffStages + s * kStageBytes + 2 * kTileBytes + 16 * o) =
@@ -316,15 +316,6 @@ __global__ void __launch_bounds__(kThreads, kGramCtasPerSm) rows_gram_kernel(Row
         if (kBf16)
             *reinterpret_cast<uint4*>(sm + kOffStages + s * kStageBytes + 16 * o) =
                 make_uint4(0u, 0u, 0u, 0u);
-    }
-    {
-        // Lambda_X comes chunk-transposed (float4 (i, 4c..4c+3) at c * 64 + i)
-        const float4* lam_ct = reinterpret_cast<const float4*>(a.lam_ct);
-        for (int e = tid; e < 1024; e += kThreads) {
-            const int i = e & 63, c = e >> 6;
-            if (4 * c <= i) prior4[gram_chunk_offset(c) + i - 4 * c] = __ldg(lam_ct + c * 64 + i);
-        }
-        for (int e = tid; e < 64; e += kThreads) prior_mu[e] = __ldg(a.lammu + e);
     }
     if (tid == 0) {
         for (int s = 0; s < kNStage; ++s) {
@@ -641,17 +632,15 @@ __global__ void __launch_bounds__(kThreads, kGramCtasPerSm) rows_gram_kernel(Row
                 for (int c = 0; c < 16; ++c) {
                     if (4 * c <= m) {
                         const float4 t = ld_chunk(T, m, c);
-                        const float4 px = prior4[gram_chunk_offset(c) + m - 4 * c];
                         float4 o;
-                        o.x = fmaf(alpha, acc[4 * c + 0] + t.x + T[sw64(4 * c + 0, m)], px.x);
-                        o.y = fmaf(alpha, acc[4 * c + 1] + t.y + T[sw64(4 * c + 1, m)], px.y);
-                        o.z = fmaf(alpha, acc[4 * c + 2] + t.z + T[sw64(4 * c + 2, m)], px.z);
-                        o.w = fmaf(alpha, acc[4 * c + 3] + t.w + T[sw64(4 * c + 3, m)], px.w);
+                        o.x = acc[4 * c + 0] + t.x + T[sw64(4 * c + 0, m)];
+                        o.y = acc[4 * c + 1] + t.y + T[sw64(4 * c + 1, m)];
+                        o.z = acc[4 * c + 2] + t.z + T[sw64(4 * c + 2, m)];
+                        o.w = acc[4 * c + 3] + t.w + T[sw64(4 * c + 3, m)];
                         st_once(out + gram_chunk_offset(c) + m - 4 * c, o, once);
                     }
                 }
-                reinterpret_cast<float*>(out)[4 * kGramChunks + m] =
-                    fmaf(alpha, rsum + T[4096 + m], prior_mu[m]);
+                reinterpret_cast<float*>(out)[4 * kGramChunks + m] = rsum + T[4096 + m];
             }
             named_bar(bar_id, 128);  // the staging buffer is reused by the group's next row
             if (q == 0 && lane == 0) mbar_arrive(bar_row_empty + 8 * rs);
