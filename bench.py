@@ -168,12 +168,14 @@ def gathered_bytes(nnz, K, bf16=False):
 # DRAM bytes (read + write) per launch, per workload, phase and kernel, from one ncu
 # capture of the current kernels (two metrics, one pass, full size): the commit that
 # changes a kernel sets its entry to None until it is captured again.  480k x 18k,
-# K = 64: the user factorisation launch reads the 352,197 precision slots the user Gram
-# launch wrote (3.16 GB) and writes the new rows (0.18 GB).
-TRAFFIC = {"config3_480kx18k_K64": {"rows_movie/rows_gram_kernel": None,
+# K = 64: the movie Gram launch reads 1.11 GB (the column view's index and value stream,
+# 0.79 GB, and user rows that miss L2) and writes 32.9 MB; the user Gram launch reads
+# 0.86 GB and writes its 352,197 Gram slots (3.09 GB), which the user factorisation
+# launch reads back (3.16 GB) before writing the new rows (0.18 GB).
+TRAFFIC = {"config3_480kx18k_K64": {"rows_movie/rows_gram_kernel": 1.147e9,
                                     "rows_movie/rows_chol_kernel": 93.1e6,
-                                    "rows_user/rows_gram_kernel": None,
-                                    "rows_user/rows_chol_kernel": 3.333e9}}
+                                    "rows_user/rows_gram_kernel": 3.953e9,
+                                    "rows_user/rows_chol_kernel": 3.332e9}}
 
 
 def l2_note(nnz):
