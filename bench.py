@@ -203,22 +203,58 @@ def load_peaks():
 # ----------------------------------------------------------------------------
 # CPU oracle timing (baseline and reference arm)
 # ----------------------------------------------------------------------------
+def stratified_relabel(prob, stride):
+    """The same ratings with users and movies renumbered so that every contiguous block of
+    1/stride of a side holds the same mix of degrees: each side's rows in degree order
+    are dealt round-robin to the blocks (block b gets ranks b, b + stride, ...) and each
+    block's rows are numbered consecutively.  Degrees, and so the oracle's work per row,
+    are unchanged; only which rows share a block changes (a heavy-tailed side, such as
+    Zipf-popular movies, otherwise gives blocks of very different cost)."""
+    def new_ids(deg):
+        n = len(deg)
+        ranked = np.argsort(-np.asarray(deg), kind="stable")
+        order = np.concatenate([ranked[b::stride] for b in range(stride)])
+        ids = np.empty(n, dtype=np.int64)
+        ids[order] = np.arange(n)
+        return order, ids
+    deg_u = np.diff(prob.csr_ptr)
+    deg_v = np.bincount(prob.csr_col, minlength=prob.N)
+    order_u, _ = new_ids(deg_u)
+    _, ids_v = new_ids(deg_v)
+    rows = np.repeat(np.arange(prob.M, dtype=np.int64), deg_u)
+    new_u = np.empty(prob.M, dtype=np.int64)
+    new_u[order_u] = np.arange(prob.M)
+    r = new_u[rows]
+    c = ids_v[prob.csr_col]
+    key = np.lexsort((c, r))  # rows in their new order, columns ascending in each
+    ptr = np.zeros(prob.M + 1, dtype=np.int64)
+    np.cumsum(np.bincount(r, minlength=prob.M), out=ptr[1:])
+    import workloads
+    return workloads.Problem(name=prob.name, M=prob.M, N=prob.N, K=prob.K, csr_ptr=ptr,
+                             csr_col=c[key].astype(np.int32), csr_val=prob.csr_val[key],
+                             test_i=new_u[prob.test_i].astype(np.int32),
+                             test_j=ids_v[prob.test_j].astype(np.int32), test_r=prob.test_r,
+                             alpha=prob.alpha, seed=prob.seed, burn_in=prob.burn_in,
+                             sweeps=prob.sweeps, noise_sd=prob.noise_sd)
+
+
 class OracleSampler:
     """Bounded steps of the FP64 oracle on the bench's own workload, on the host cores.
 
-    Step q takes block q mod `stride` of each side: rows [b n / stride, (b + 1) n /
-    stride).  Row indices carry no order by degree, so a block is a random sample of
-    the side and the oracle's threads split it into contiguous ranges as they split a
-    whole side; `stride` consecutive steps cover one full sweep's rows once.  A step
-    runs the row statistics of its rows and their row updates (the oracle's whole
-    per-row work of a sweep) and is timed end to end: rows/s = rows updated / seconds,
-    measured, not extrapolated."""
+    The workload's rows are first renumbered so that every block of 1/stride of a side
+    holds the same mix of degrees (stratified_relabel).  Step q takes block q mod `stride`
+    of each side: rows [b n / stride, (b + 1) n / stride), which the oracle's threads
+    split into contiguous ranges as they split a whole side; `stride` consecutive steps
+    cover one full sweep's rows once.  A step runs the row statistics of its rows and
+    their row updates (the oracle's whole per-row work of a sweep) and is timed end to
+    end: rows/s = rows updated / seconds, measured, not extrapolated."""
 
     def __init__(self, prob, frac, nthreads=None):
         import oracle
         self.cores = nthreads or os.cpu_count() or 1
-        self.orc = oracle.Oracle(prob, nthreads=self.cores)
         self.stride = max(1, int(round(1.0 / frac)))
+        prob = stratified_relabel(prob, self.stride)
+        self.orc = oracle.Oracle(prob, nthreads=self.cores)
         self.sides = [(oracle.MOVIE, prob.N), (oracle.USER, prob.M)]
 
     def step(self, q):
@@ -236,10 +272,11 @@ class OracleSampler:
         return rows_done, secs
 
     def describe(self, steps):
-        return ("%d step(s), each 1/%d of both sides (a contiguous block of %d movies and %d "
-                "users; row statistics and row updates), timed, not extrapolated; %d steps "
-                "cover one sweep" % (steps, self.stride, self.sides[0][1] // self.stride,
-                                     self.sides[1][1] // self.stride, self.stride))
+        return ("%d step(s), each 1/%d of both sides (a block of %d movies and %d users with "
+                "the sides' mix of degrees; row statistics and row updates), timed, not "
+                "extrapolated; %d steps cover one sweep" % (
+                    steps, self.stride, self.sides[0][1] // self.stride,
+                    self.sides[1][1] // self.stride, self.stride))
 
 
 # ----------------------------------------------------------------------------

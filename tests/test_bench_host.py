@@ -83,3 +83,30 @@ def test_l2_note_states_how_inputs_stand_to_l2():
     # the ratings are held twice (row and column views), 8 B per rating each
     assert bench.l2_note(98_959_257).startswith("inputs larger than L2 (ratings CSR+CSC 1.58 GB)")
     assert bench.l2_note(20_000).startswith("inputs fit in L2")
+
+
+def test_stratified_relabel_keeps_the_ratings_and_levels_the_blocks():
+    """The oracle sampler's renumbering: the same (user, movie, rating) triples under a
+    permutation of each side, columns ascending in every row, and blocks of 1/stride of
+    a side with nearly equal rating counts (Zipf-like columns otherwise vary widely)."""
+    import numpy as np
+    import bench
+    import workloads
+    p = workloads.random_small(3000, 800, 16, 60000, seed=3, n_test=100, long_rows=5, long_deg=500)
+    q = bench.stratified_relabel(p, 10)
+    deg_u, deg_v = np.diff(p.csr_ptr), np.bincount(p.csr_col, minlength=p.N)
+    rows_p = np.repeat(np.arange(p.M), deg_u)
+    rows_q = np.repeat(np.arange(q.M), np.diff(q.csr_ptr))
+    # recover the permutations from the degrees' new positions and compare triples
+    trip_p = sorted(zip(deg_u[rows_p], deg_v[p.csr_col], p.csr_val.tolist()))
+    dq_u, dq_v = np.diff(q.csr_ptr), np.bincount(q.csr_col, minlength=q.N)
+    trip_q = sorted(zip(dq_u[rows_q], dq_v[q.csr_col], q.csr_val.tolist()))
+    assert trip_p == trip_q and q.nnz == p.nnz
+    for i in range(q.M):
+        assert np.all(np.diff(q.csr_col[q.csr_ptr[i]:q.csr_ptr[i + 1]]) > 0)
+    # round-robin by degree rank: blocks differ by at most one row's ratings
+    blocks = [dq_v[b * 80:(b + 1) * 80].sum() for b in range(10)]
+    assert max(blocks) - min(blocks) <= dq_v.max()
+    ublocks = [dq_u[b * 300:(b + 1) * 300].sum() for b in range(10)]
+    assert max(ublocks) - min(ublocks) <= dq_u.max()
+    assert np.all((q.test_i >= 0) & (q.test_i < q.M)) and np.all((q.test_j >= 0) & (q.test_j < q.N))
