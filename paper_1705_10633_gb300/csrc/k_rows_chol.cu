@@ -21,9 +21,9 @@ namespace bpmf {
 namespace {
 
 constexpr int kCholWarps = 8;
-// per warp: L^T (64 x kLtLd), the column buffers (2 x 64), 1 / diag (64), noise (64);
-// per CTA: Lambda_X packed like a slot and Lambda_X mu_X
-constexpr int kCholWarpFloats = 64 * kLtLd + 128 + 64 + 64;
+// per warp: L^T (64 x kLtLd), 1 / diag (64), noise (64); per CTA: Lambda_X packed like
+// a slot and Lambda_X mu_X
+constexpr int kCholWarpFloats = 64 * kLtLd + 64 + 64;
 constexpr size_t kCholSmemBytes = ((size_t)kCholWarps * kCholWarpFloats + kGramSlotFloats) * 4;
 static_assert(kCholSmemBytes <= 232448, "shared memory");
 
@@ -48,8 +48,7 @@ __global__ void __launch_bounds__(kCholWarps * 32, 1) rows_chol_kernel(RowArgs a
         __syncthreads();
     }
     float* M = chol_smem + warp * kCholWarpFloats;
-    float* cbuf = M + 64 * kLtLd;
-    float* dinv = cbuf + 128;
+    float* dinv = M + 64 * kLtLd;
     float* zb = dinv + 64;
     const uint32_t sweep = (uint32_t)a.ctl->sweep;
     // a Gram launch that gave up on a wait left its slots unfinished: nothing to factor
@@ -88,7 +87,7 @@ __global__ void __launch_bounds__(kCholWarps * 32, 1) rows_chol_kernel(RowArgs a
         const float b2 = fmaf(alpha, __ldg(bsrc + 32 + lane), prior_mu[32 + lane]);
         __syncwarp();  // every lane's back solve of the previous row is done with M
         float x1, x2, m1, m2;
-        factor_solve_sample_rl64(a1, a2, b1, b2, M, cbuf, dinv, zb, lane, a.K, a.seed,
+        factor_solve_sample_rl64(a1, a2, b1, b2, M, dinv, zb, lane, a.K, a.seed,
                                  (uint32_t)row, sweep, a.c3, a.means != nullptr, x1, x2, m1, m2,
                                  bad);
         store_row_panels(a, row, lane, x1, x2, m1, m2);

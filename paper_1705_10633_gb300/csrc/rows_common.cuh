@@ -319,9 +319,10 @@ __device__ __forceinline__ float4 ld_chunk(const float* M, int i, int c)
 }
 
 
-// The K = 64 factor's transpose L^T in a warp's buffer: element (j, r) at j * kLtLd + r.
-// The padded row (68 floats) keeps the back solve's float4 loads of 32 different rows
-// at the minimum of four wavefronts, and a pivot's row store is one index add.
+// The K = 64 factor's transpose L^T in a warp's buffer: row j holds column j of L,
+// L[r][j] at j * kLtLd + r - (j & ~1) (chol_pivot).  The padded row (68 floats) keeps
+// the row stores conflict-free and spreads the back solve's loads of 32 different rows
+// over the banks.
 constexpr int kLtLd = 68;
 
 // Pivot work of column j of a right-looking Cholesky with the forward solve fused,
@@ -329,17 +330,16 @@ constexpr int kLtLd = 68;
 // entries A[r1][j] / A[r2][j] after the updates of columns 0 .. j-1.  Gives the
 // lane's L[r][j] in l1 / l2 (zero on and above the diagonal), applies y_j to the
 // right-hand side (b_j becomes y_j = b_j / L[j][j], rows below lose L[r][j] y_j),
-// writes 1 / L[j][j] to dinv, column j of L transposed into row j of M (a
-// conflict-free row store) and into the column buffer of j's parity, L[r][j] at
-// position r - (j & ~1): in a step over the columns k, k + 1 (k even) both columns'
-// entries of row k + 2 + t then sit at position t + 2, in aligned pairs.  Branch-free
-// apart from the predicated stores.  HAS1 = false once the rows r1 are finished.
+// writes 1 / L[j][j] to dinv and column j of L transposed into row j of M, L[r][j]
+// at position r - (j & ~1) (a conflict-free row store): in a step over the columns
+// k, k + 1 (k even) both columns' entries of row k + 2 + t then sit at position t + 2,
+// in aligned pairs, and the row is both the columns' broadcast source and the back
+// solve's copy of L.  Branch-free apart from the predicated stores.  HAS1 = false once the rows r1 are finished.
 // A pivot that is not positive and finite is not caught here: 1 / L[j][j] then comes
 // out non-positive, infinite or NaN, which the caller checks once per row.
 template <bool HAS1>
 __device__ __forceinline__ void chol_pivot(int j, float p1, float p2, float& b1, float& b2,
-                                           float& l1, float& l2, float* M, float* cbuf,
-                                           float* dinv, int lane)
+                                           float& l1, float& l2, float* M, float* dinv, int lane)
 {
     const int r1 = lane, r2 = 32 + lane;
     const int owner = j & 31;
@@ -348,29 +348,22 @@ __device__ __forceinline__ void chol_pivot(int j, float p1, float p2, float& b1,
     const float rinv = rsqrtf(piv);
     const float yk = bk * rinv;
     if (lane == 0) dinv[j] = rinv;
-    float* cb = cbuf + (j & 1) * 64 - (j & ~1);
-    float* mrow = M + j * kLtLd;
+    float* cb = M + j * kLtLd - (j & ~1);
     l1 = 0.f;
     if (HAS1) {
         const bool below = r1 > j;
         l1 = below ? p1 * rinv : 0.f;
         b1 = below ? fmaf(-l1, yk, b1) : (r1 == j ? yk : b1);
-        if (below) {
-            mrow[r1] = l1;
-            cb[r1] = l1;
-        }
+        if (below) cb[r1] = l1;
     }
     const bool below2 = r2 > j;
     l2 = below2 ? p2 * rinv : 0.f;
     b2 = below2 ? fmaf(-l2, yk, b2) : (r2 == j ? yk : b2);
-    if (below2) {
-        mrow[r2] = l2;
-        cb[r2] = l2;
-    }
+    if (below2) cb[r2] = l2;
 }
 
 // Column pairs (k, k + 1), k = k0, k0 + 2, .. < k1, all even (the pivot work of
-// column k0 already done: l1 / l2 hold the lane's L[r][k0] and the even buffer its
+// column k0 already done: l1 / l2 hold the lane's L[r][k0] and row k0 of M its
 // column).  The rows are kept in registers as pairs, "shifted": at pair k,
 // (a[s].x, a[s].y) = (A[r][k + 2s], A[r][k + 2s + 1]).  A pair updates column k + 1
 // by column k and does its pivot work, then the rest of each row twice,
@@ -385,20 +378,20 @@ __device__ __forceinline__ void chol_pivot(int j, float p1, float p2, float& b1,
 template <int P1, int P2>
 __device__ __forceinline__ void chol_pair_steps(float2 (&a1)[16], float2 (&a2)[32], float& b1,
                                                 float& b2, float& l1, float& l2, int k0, int k1,
-                                                float* M, float* cbuf, float* dinv, int lane)
+                                                float* M, float* dinv, int lane)
 {
     static_assert(P1 % 2 == 0 && P2 % 2 == 0 && P2 > 0, "step shape");
 #pragma unroll 1
     for (int k = k0; k < k1; k += 2) {
-        __syncwarp();  // column k is in the even buffer
-        const float4* ce = reinterpret_cast<const float4*>(cbuf);
-        const float4* co = reinterpret_cast<const float4*>(cbuf + 64);
+        __syncwarp();  // column k is in row k of M
+        const float4* ce = reinterpret_cast<const float4*>(M + k * kLtLd);
+        const float4* co = reinterpret_cast<const float4*>(M + (k + 1) * kLtLd);
         const float4 e0 = ce[0];  // e0.y = L[k + 1][k]
         float m1 = 0.f, m2 = 0.f;
         {
             const float n1 = P1 > 0 ? fmaf(-l1, e0.y, a1[0].y) : 0.f;
             const float n2 = fmaf(-l2, e0.y, a2[0].y);
-            chol_pivot<(P1 > 0)>(k + 1, n1, n2, b1, b2, m1, m2, M, cbuf, dinv, lane);
+            chol_pivot<(P1 > 0)>(k + 1, n1, n2, b1, b2, m1, m2, M, dinv, lane);
         }
         const float2 nl1 = make_float2(-l1, -l1), nl2 = make_float2(-l2, -l2);
 #pragma unroll
@@ -409,7 +402,7 @@ __device__ __forceinline__ void chol_pair_steps(float2 (&a1)[16], float2 (&a2)[3
             a2[s] = __ffma2_rn(nl2, c, a2[s + 1]);
             if (s + 1 < P1) a1[s] = __ffma2_rn(nl1, c, a1[s + 1]);
         }
-        __syncwarp();  // column k + 1 is in the odd buffer
+        __syncwarp();  // column k + 1 is in row k + 1 of M
         const float2 ml1 = make_float2(-m1, -m1), ml2 = make_float2(-m2, -m2);
         float q1 = 0.f, q2 = 0.f;
 #pragma unroll
@@ -420,7 +413,7 @@ __device__ __forceinline__ void chol_pair_steps(float2 (&a1)[16], float2 (&a2)[3
             a2[s] = __ffma2_rn(ml2, c, a2[s]);
             if (s + 1 < P1) a1[s] = __ffma2_rn(ml1, c, a1[s]);
             if (s == 0 && k + 2 < 64)
-                chol_pivot<(P1 > 0)>(k + 2, a1[0].x, a2[0].x, b1, b2, q1, q2, M, cbuf, dinv, lane);
+                chol_pivot<(P1 > 0)>(k + 2, a1[0].x, a2[0].x, b1, b2, q1, q2, M, dinv, lane);
         }
         l1 = q1;
         l2 = q2;
@@ -431,13 +424,14 @@ __device__ __forceinline__ void chol_pair_steps(float2 (&a1)[16], float2 (&a2)[3
 // and r2 = 32 + l (a2: columns 0..63) of Lambda_i in registers, as pairs of columns
 // -- entries above the diagonal are never used -- and its entries b1 = b_i[r1],
 // b2 = b_i[r2].  M is the warp's 64 x kLtLd buffer; it receives the strictly lower
-// part of L, transposed, for the back solve (its previous contents are ignored).
+// part of L, transposed and shifted (chol_pivot), for the column steps and the back
+// solve (its previous contents are ignored).
 // bad is set when a pivot was not positive and finite (Lambda_i not positive
 // definite in FP32).  The factorisation runs in eight spans of 8 columns so the
 // register rows shrink as they finish, then x = L^{-T}(y + z).
 __device__ __forceinline__ void factor_solve_sample_rl64(float2 (&a1)[16], float2 (&a2)[32], float b1,
-                                                         float b2, float* M, float* cbuf,
-                                                         float* dinv, float* zb, int lane, int K,
+                                                         float b2, float* M, float* dinv,
+                                                         float* zb, int lane, int K,
                                                          uint64_t seed, uint32_t row,
                                                          uint32_t sweep, uint32_t c3,
                                                          bool want_means, float& x1, float& x2,
@@ -445,15 +439,15 @@ __device__ __forceinline__ void factor_solve_sample_rl64(float2 (&a1)[16], float
 {
     const int r1 = lane, r2 = 32 + lane;
     float l1, l2;
-    chol_pivot<true>(0, a1[0].x, a2[0].x, b1, b2, l1, l2, M, cbuf, dinv, lane);
-    chol_pair_steps<16, 32>(a1, a2, b1, b2, l1, l2, 0, 8, M, cbuf, dinv, lane);
-    chol_pair_steps<12, 28>(a1, a2, b1, b2, l1, l2, 8, 16, M, cbuf, dinv, lane);
-    chol_pair_steps<8, 24>(a1, a2, b1, b2, l1, l2, 16, 24, M, cbuf, dinv, lane);
-    chol_pair_steps<4, 20>(a1, a2, b1, b2, l1, l2, 24, 32, M, cbuf, dinv, lane);
-    chol_pair_steps<0, 16>(a1, a2, b1, b2, l1, l2, 32, 40, M, cbuf, dinv, lane);
-    chol_pair_steps<0, 12>(a1, a2, b1, b2, l1, l2, 40, 48, M, cbuf, dinv, lane);
-    chol_pair_steps<0, 8>(a1, a2, b1, b2, l1, l2, 48, 56, M, cbuf, dinv, lane);
-    chol_pair_steps<0, 4>(a1, a2, b1, b2, l1, l2, 56, 64, M, cbuf, dinv, lane);
+    chol_pivot<true>(0, a1[0].x, a2[0].x, b1, b2, l1, l2, M, dinv, lane);
+    chol_pair_steps<16, 32>(a1, a2, b1, b2, l1, l2, 0, 8, M, dinv, lane);
+    chol_pair_steps<12, 28>(a1, a2, b1, b2, l1, l2, 8, 16, M, dinv, lane);
+    chol_pair_steps<8, 24>(a1, a2, b1, b2, l1, l2, 16, 24, M, dinv, lane);
+    chol_pair_steps<4, 20>(a1, a2, b1, b2, l1, l2, 24, 32, M, dinv, lane);
+    chol_pair_steps<0, 16>(a1, a2, b1, b2, l1, l2, 32, 40, M, dinv, lane);
+    chol_pair_steps<0, 12>(a1, a2, b1, b2, l1, l2, 40, 48, M, dinv, lane);
+    chol_pair_steps<0, 8>(a1, a2, b1, b2, l1, l2, 48, 56, M, dinv, lane);
+    chol_pair_steps<0, 4>(a1, a2, b1, b2, l1, l2, 56, 64, M, dinv, lane);
     // every pivot's 1 / L[j][j] is in dinv (the last step began with a warp sync): it is
     // positive and finite exactly when the pivot was
     {
@@ -474,13 +468,17 @@ __device__ __forceinline__ void factor_solve_sample_rl64(float2 (&a1)[16], float
     float t2 = b2 + zb[r2];
     float n1 = b1, n2 = b2;
     // ---- back substitution x = L^{-T} t: step i broadcasts x_i and every lane
-    // updates its rows r < i with L[i][r], which sits in row r of M (L^T); one
-    // float4 of that row serves four steps.  Selects, not branches: the update of
-    // a row on or below i is computed and dropped.
+    // updates its rows r < i with L[i][r], which sits in row r of M at position
+    // i - (r & ~1); four of them (two aligned pairs) serve four steps.  Selects, not
+    // branches: the update of a row on or below i is computed and dropped.
 #pragma unroll 1
     for (int g = 15; g >= 0; --g) {
-        const float4 A1 = *reinterpret_cast<const float4*>(M + r1 * kLtLd + 4 * g);
-        const float4 A2 = *reinterpret_cast<const float4*>(M + r2 * kLtLd + 4 * g);
+        const float* q1 = M + r1 * kLtLd + 4 * g - (r1 & ~1);
+        const float* q2 = M + r2 * kLtLd + 4 * g - (r2 & ~1);
+        const float2 x1 = *reinterpret_cast<const float2*>(q1), y1 = *reinterpret_cast<const float2*>(q1 + 2);
+        const float2 x2 = *reinterpret_cast<const float2*>(q2), y2 = *reinterpret_cast<const float2*>(q2 + 2);
+        const float4 A1 = make_float4(x1.x, x1.y, y1.x, y1.y);
+        const float4 A2 = make_float4(x2.x, x2.y, y2.x, y2.y);
         const float4 D = *reinterpret_cast<const float4*>(dinv + 4 * g);
         const float l1v[4] = {A1.x, A1.y, A1.z, A1.w};
         const float l2v[4] = {A2.x, A2.y, A2.z, A2.w};
