@@ -22,7 +22,7 @@ using namespace bpmf;
 
 namespace {
 
-constexpr int kDefaultLongMinDegree = 48;
+constexpr int kDefaultLongMinDegree = 16;
 constexpr int kDefaultSplitDegree = 1024;
 constexpr int kDefaultRankOneDegree = 1;
 constexpr int kDefaultWaitTimeoutMs = 2000;

@@ -152,11 +152,11 @@ def test_device_bytes_is_host_only_and_follows_the_buffers(bp):
                                     params=bp.bpmf_default_params(**kw), num_sms=152)
 
     base = nbytes()
-    # rows with at least 48 ratings take the tensor-core route at K = 64: one 8,960-B
+    # rows with at least 16 ratings take the tensor-core route at K = 64: one 8,960-B
     # scratch slot per row of the larger long bin
     deg_u = np.diff(prob.csr_ptr)
     deg_v = np.bincount(prob.csr_col, minlength=prob.N)
-    n_long = max(int((deg_u >= 48).sum()), int((deg_v >= 48).sum()))
+    n_long = max(int((deg_u >= 16).sum()), int((deg_v >= 16).sum()))
     assert n_long > 0
     cuda_core = nbytes(flags=bp.BPMF_CUDA_CORE_GRAM)
     assert base - cuda_core >= n_long * 8960 + 2 * 2 * (prob.M + prob.N) * 64

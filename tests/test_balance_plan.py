@@ -1,6 +1,6 @@
 """Host logic of the degree bins and of the balanced row plan (no GPU).
 
-bpmf_create deals each side's tensor-core rows (48 ratings or more when K pads to 64) to
+bpmf_create deals each side's tensor-core rows (16 ratings or more by default when K pads to 64) to
 the CTAs of the persistent kernel.  Round-robin in longest-first order is kept unless it
 would leave the busiest CTA more than 5% above the mean; then every row, longest first,
 goes to the CTA with the least work so far (list scheduling over Sec. 4.2's item cost: a

@@ -168,10 +168,11 @@ def test_sweep_entry_point_matches_phases(bp, K, order):
     prob = workloads.random_small(150, 70, K, 1500 if K == 8 else 6000, seed=9, n_test=60)
     # a stream of its own: the sweeps after the first replay a captured CUDA graph
     sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
-    a = bp.create_from_problem(prob, order=order, stream=sa.cuda_stream)
-    b = bp.create_from_problem(prob, order=order, stream=sb.cuda_stream)
+    # a tensor-core threshold that leaves users on both kernels at K = 64
+    a = bp.create_from_problem(prob, order=order, stream=sa.cuda_stream, long_min_degree=48)
+    b = bp.create_from_problem(prob, order=order, stream=sb.cuda_stream, long_min_degree=48)
     try:
-        if K == 64:  # movies on the tensor-core kernel, users on the CUDA-core one
+        if K == 64:  # movies on the tensor-core kernel, users on both
             assert bp.bpmf_info(a, 1)["n_long"] > 0 and bp.bpmf_info(a, 0)["n_short"] > 0
         ra = bp.bpmf_sweep(a, 3)
         seq = (bp.BPMF_PHASE_HYPER_MOVIE, bp.BPMF_PHASE_ROWS_MOVIE, bp.BPMF_PHASE_HYPER_USER,

@@ -45,7 +45,7 @@ def _rank(rank, world, port, K, sweeps, q):
         import paper_1705_10633_gb300 as bp
         from paper_1705_10633_gb300.shard import HandleBackend, ShardedChain
         prob = _problem(K)
-        kw = {"split_degree": 64} if K != 64 else {}
+        kw = {"split_degree": 64} if K != 64 else {"long_min_degree": 48}
         h = bp.create_from_problem(prob, stream=bp.torch_stream(), **kw)
         try:
             b = HandleBackend(bp, h, prob.M, prob.N, prob.K, prob.degrees(), prob.col_degrees(),
@@ -81,7 +81,7 @@ def test_two_sharded_ranks_equal_one_handle(K):
         assert p.exitcode == 0
     torch.cuda.set_device(0)
     prob = _problem(K)
-    kw = {"split_degree": 64} if K != 64 else {}
+    kw = {"split_degree": 64} if K != 64 else {"long_min_degree": 48}
     h = bp.create_from_problem(prob, stream=bp.torch_stream(), **kw)
     try:
         rmse = bp.bpmf_sweep(h, sweeps)
