@@ -207,13 +207,17 @@ def stratified_relabel(prob, stride):
     """The same ratings with users and movies renumbered so that every contiguous block of
     1/stride of a side holds the same mix of degrees: each side's rows in degree order
     are dealt round-robin to the blocks (block b gets ranks b, b + stride, ...) and each
-    block's rows are numbered consecutively.  Degrees, and so the oracle's work per row,
+    block's rows are numbered consecutively, in a seeded random order.  Degrees, and so the oracle's work per row,
     are unchanged; only which rows share a block changes (a heavy-tailed side, such as
     Zipf-popular movies, otherwise gives blocks of very different cost)."""
+    rng = np.random.default_rng(12345)
+
     def new_ids(deg):
         n = len(deg)
         ranked = np.argsort(-np.asarray(deg), kind="stable")
-        order = np.concatenate([ranked[b::stride] for b in range(stride)])
+        # each block shuffled: the oracle's threads split a block into contiguous ranges,
+        # which must not be ordered by degree either
+        order = np.concatenate([rng.permutation(ranked[b::stride]) for b in range(stride)])
         ids = np.empty(n, dtype=np.int64)
         ids[order] = np.arange(n)
         return order, ids

@@ -87,7 +87,8 @@ typedef struct {
     uint32_t flags;     /* BPMF_* flags                                                  */
     double clip_lo, clip_hi;
     int32_t long_min_degree; /* rows with at least this many ratings use the tensor-core
-                                kernel (K in 49..64); <= 0 = library default (16)      */
+                                kernel (K in 49..64); <= 0 = library default (16;
+                                48 with BPMF_BF16_GRAM)                               */
     int32_t wait_timeout_ms; /* limit of every device-side wait, <= 0 = 2000 ms         */
     int32_t split_degree; /* rows on the CUDA-core kernel with at least this many ratings
                              are split into runs of split_degree / 2 ratings done by

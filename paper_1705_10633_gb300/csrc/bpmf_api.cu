@@ -22,7 +22,17 @@ using namespace bpmf;
 
 namespace {
 
+// Default threshold of the tensor-core route.  With the BF16 Gram (8-bit mantissas) the
+// rows keep to 48 ratings and more: a row of few ratings has a precision dominated by a
+// handful of rank-one terms, and its conditional mean then carries the inputs' 2^-9
+// error at up to 1.7% (a 16-rating movie of the 480k x 18k workload); the FP32-class
+// Gram has no such limit.
 constexpr int kDefaultLongMinDegree = 16;
+constexpr int kDefaultLongMinDegreeBf16 = 48;
+int64_t default_long_min(uint32_t flags)
+{
+    return (flags & BPMF_BF16_GRAM) ? kDefaultLongMinDegreeBf16 : kDefaultLongMinDegree;
+}
 constexpr int kDefaultSplitDegree = 1024;
 constexpr int kDefaultRankOneDegree = 1;
 constexpr int kDefaultWaitTimeoutMs = 2000;
@@ -873,7 +883,7 @@ int bpmf_create(bpmf_handle* out, int64_t M, int64_t N, int32_t K, const int64_t
         csc_row = ri.data();
         csc_val = cv.data();
     }
-    const int64_t long_min = prm.long_min_degree > 0 ? prm.long_min_degree : kDefaultLongMinDegree;
+    const int64_t long_min = prm.long_min_degree > 0 ? prm.long_min_degree : default_long_min(prm.flags);
     h->long_min = long_min;
     h->split_degree = prm.split_degree > 0 ? prm.split_degree : kDefaultSplitDegree;
     h->rank_one_max = rank_one_from(prm.rank_one_degree);
@@ -1026,7 +1036,7 @@ int bpmf_set_tuning(bpmf_handle h, int32_t long_min_degree, int32_t split_degree
 {
     if (!h) return BPMF_EINVAL;
     h->rank_one_max = rank_one_from(rank_one_degree);
-    h->long_min = long_min_degree > 0 ? long_min_degree : kDefaultLongMinDegree;
+    h->long_min = long_min_degree > 0 ? long_min_degree : default_long_min(h->p.flags);
     h->split_degree = split_degree > 0 ? split_degree : kDefaultSplitDegree;
     std::vector<int32_t> order;
     for (int s = 0; s < 2; ++s) {
@@ -1944,7 +1954,7 @@ int bpmf_device_bytes(int64_t M, int64_t N, int32_t K, const int64_t* csr_ptr,
     };
     const int kp = (K + 15) / 16 * 16;
     const bool tc = kp == 64 && !(prm.flags & BPMF_CUDA_CORE_GRAM);
-    const int64_t long_min = prm.long_min_degree > 0 ? prm.long_min_degree : kDefaultLongMinDegree;
+    const int64_t long_min = prm.long_min_degree > 0 ? prm.long_min_degree : default_long_min(prm.flags);
     const int64_t split = prm.split_degree > 0 ? prm.split_degree : kDefaultSplitDegree;
     std::vector<int64_t> cptr;
     try {
