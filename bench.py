@@ -168,14 +168,15 @@ def gathered_bytes(nnz, K, bf16=False):
 # DRAM bytes (read + write) per launch, per workload, phase and kernel, from one ncu
 # capture of the current kernels (two metrics, one pass, full size): the commit that
 # changes a kernel sets its entry to None until it is captured again.  480k x 18k,
-# K = 64: the movie Gram launch reads 1.11 GB (the column view's index and value stream,
-# 0.79 GB, and user rows that miss L2) and writes 32.9 MB; the user Gram launch reads
-# 0.86 GB and writes its 352,197 Gram slots (3.09 GB), which the user factorisation
-# launch reads back (3.16 GB) before writing the new rows (0.18 GB).
-TRAFFIC = {"config3_480kx18k_K64": {"rows_movie/rows_gram_kernel": None,
-                                    "rows_movie/rows_chol_kernel": None,
-                                    "rows_user/rows_gram_kernel": None,
-                                    "rows_user/rows_chol_kernel": None}}
+# K = 64, rows of 16 ratings or more on the tensor-core route: the movie Gram launch
+# reads 1.09 GB (the column view's index and value stream, 0.79 GB, and user rows that
+# miss L2) and writes 78.9 MB; the user Gram launch reads 0.91 GB and writes its 451,177
+# Gram slots (3.98 GB), which the user factorisation launch reads back (4.05 GB) before
+# writing the new rows (0.23 GB).
+TRAFFIC = {"config3_480kx18k_K64": {"rows_movie/rows_gram_kernel": 1.170e9,
+                                    "rows_movie/rows_chol_kernel": 142.6e6,
+                                    "rows_user/rows_gram_kernel": 4.889e9,
+                                    "rows_user/rows_chol_kernel": 4.271e9}}
 
 
 def l2_note(nnz):
