@@ -176,7 +176,7 @@ def test_row_launch_timing(bp):
     prob = workloads.random_small(400, 200, 64, 20000, seed=61)
     deg = np.diff(prob.csr_ptr)
     assert (deg < 48).sum() > 0 and (deg >= 48).sum() > 0
-    h = bp.create_from_problem(prob, stream=bp.torch_stream())
+    h = bp.create_from_problem(prob, stream=bp.torch_stream(), long_min_degree=48)
     try:
         assert bp.bpmf_row_launch_ms(h) == (-1.0, -1.0, -1.0)
         bp.bpmf_set_row_timing(h, True)
