@@ -169,8 +169,8 @@ int bpmf_sweep_batch(bpmf_handle* hs, int32_t n, int32_t n_sweeps);
  * sweep is captured as one CUDA graph when `cuda_stream` can be captured.
  *
  * bpmf_batch_create: hs is a host array of n >= 1 distinct handles, borrowed (they must
- * outlive the batch and keep their bins: calling bpmf_set_tuning or bpmf_set_shard on
- * one of them invalidates the batch; make a new one).  All on one device, with the
+ * outlive the batch and keep their bins: after bpmf_set_tuning or bpmf_set_shard on one
+ * of them, bpmf_batch_sweep returns BPMF_EINVAL; make a new batch).  All on one device, with the
  * same sweep order and no shard restriction, else BPMF_EINVAL.  cuda_stream: the
  * stream the batch's launches go to (NULL: the legacy default stream, not captured).
  * The tables live in one device allocation of the batch (cudaMalloc), freed by

@@ -119,6 +119,7 @@ struct bpmf_ctx {
     std::vector<size_t> alloc_bytes;
     int64_t bytes = 0;
     int64_t launches = 0;  // kernels launched by the phases
+    uint64_t bins_version = 0;  // moves whenever a side is binned again (a batch checks it)
     // bpmf_set_row_timing: events around the row kernels of phases run by bpmf_step
     bool row_timing = false;
     cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -466,6 +467,7 @@ int plan_long_bin(bpmf_ctx* h, DevSide& d, const std::vector<int32_t>& order)
 // the split of its long CUDA-core rows and the balanced plan of its tensor-core rows.
 int bin_side(bpmf_ctx* h, DevSide& d, std::vector<int32_t>& order)
 {
+    ++h->bins_version;
     // the rows of this handle's shard (every row unless restricted), as global row ids
     bin_rows(d.shard_hi - d.shard_lo, d.ptr_h.data() + d.shard_lo, h->tc ? h->long_min : INT64_MAX,
              order, &d.n_short, &d.n_long, &d.long_ratings);
@@ -1256,6 +1258,7 @@ struct BatchLaunch {
 
 struct bpmf_batch_ctx {
     std::vector<bpmf_ctx*> jobs;
+    std::vector<uint64_t> bins_version;  // each job's when its tables were made
     cudaStream_t stream = nullptr;
     cudaStream_t aux = nullptr;  // hyper steps beside the row launches
     cudaEvent_t ev[4] = {};      // sweep-level fork / join
@@ -1452,6 +1455,7 @@ int bpmf_batch_create(bpmf_handle* hs, int32_t n, void* cuda_stream, bpmf_batch*
     if (!b) return BPMF_ENOMEM;
     try {
         b->jobs.assign(hs, hs + n);
+        for (int32_t k = 0; k < n; ++k) b->bins_version.push_back(hs[k]->bins_version);
     } catch (const std::bad_alloc&) {
         delete b;
         return BPMF_ENOMEM;
@@ -1612,6 +1616,10 @@ int bpmf_batch_create(bpmf_handle* hs, int32_t n, void* cuda_stream, bpmf_batch*
 int bpmf_batch_sweep(bpmf_batch b, int32_t n_sweeps)
 {
     if (!b || n_sweeps < 0) return BPMF_EINVAL;
+    // a job binned again since (bpmf_set_tuning, bpmf_set_shard) no longer matches the
+    // tables: the batch must be made again
+    for (size_t k = 0; k < b->jobs.size(); ++k)
+        if (b->jobs[k]->bins_version != b->bins_version[k]) return BPMF_EINVAL;
     if (n_sweeps == 0) return BPMF_OK;
     const NvtxRange range("bpmf_batch_sweep");
     int rc = batch_order(b, true);

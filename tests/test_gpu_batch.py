@@ -113,6 +113,11 @@ def test_batch_object_equals_chains_alone(bp):
             assert got[3] == state[3] == 4
             rb = bp.bpmf_sweep(h, 0)
             np.testing.assert_array_equal(np.array(rb), np.array(r))  # NaN == NaN without test points
+        # a job binned again no longer matches the batch's tables
+        bp.bpmf_set_tuning(hs[1], long_min_degree=64)
+        with pytest.raises(bp.BpmfError) as ei:
+            bp.bpmf_batch_sweep(b, 1)
+        assert ei.value.code == bp.BPMF_EINVAL
     finally:
         if b is not None:
             bp.bpmf_batch_destroy(b)
