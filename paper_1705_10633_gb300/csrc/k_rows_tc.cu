@@ -563,7 +563,6 @@ __global__ void __launch_bounds__(kThreads, kGramCtasPerSm) rows_gram_kernel(Row
         const int m = 32 * (q & 1) + lane;  // row of the Gram this thread serves
         const uint32_t bar_id = 1 + grp;
         float* T = staging + grp * kStagingFloats;
-        const float alpha = a.alpha;
         const uint64_t once = l2_evict_first();
         uint32_t u = 0;  // accumulation chunks drained by this group
         for (int64_t j = grp; j < nj; j += kGroups) {
