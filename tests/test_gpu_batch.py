@@ -123,3 +123,44 @@ def test_batch_object_equals_chains_alone(bp):
             bp.bpmf_batch_destroy(b)
         for h in hs:
             bp.bpmf_destroy(h)
+
+
+def test_batch_isolates_a_job_whose_wait_times_out(bp):
+    """A job whose tensor-core Gram launch never gets its stages (BPMF_TEST_STALL: the
+    gather never arrives) times out inside the batch and reports BPMF_ETIMEOUT; the
+    other jobs of the batch finish with the results they get alone, bit for bit, and the
+    context stays usable."""
+    import torch
+    stall = workloads.random_small(300, 200, 64, 20000, seed=5)
+    others = [workloads.random_small(400, 150, 64, 15000, seed=71, n_test=50),
+              workloads.random_small(500, 120, 32, 9000, seed=72, n_test=50)]
+    alone = []
+    for prob in others:
+        h = bp.create_from_problem(prob, stream=torch.cuda.Stream().cuda_stream)
+        try:
+            r = bp.bpmf_sweep(h, 2)
+            alone.append((bp.bpmf_get_state(h, prob.M, prob.N, prob.K), r))
+        finally:
+            bp.bpmf_destroy(h)
+    p = bp.bpmf_default_params(alpha=stall.alpha, seed=stall.seed, flags=bp.BPMF_TEST_STALL,
+                               wait_timeout_ms=100)
+    hs = [bp.create_from_problem(stall, params=p, stream=torch.cuda.Stream().cuda_stream)]
+    hs += [bp.create_from_problem(prob, stream=torch.cuda.Stream().cuda_stream) for prob in others]
+    b = None
+    try:
+        assert bp.bpmf_info(hs[0], 1)["n_long"] > 0
+        b = bp.bpmf_batch_create(hs, stream=torch.cuda.Stream().cuda_stream)
+        bp.bpmf_batch_sweep(b, 2)
+        torch.cuda.synchronize()
+        assert bp.bpmf_status(hs[0]) == bp.BPMF_ETIMEOUT
+        for h, prob, (state, r) in zip(hs[1:], others, alone):
+            assert bp.bpmf_status(h) == 0
+            got = bp.bpmf_get_state(h, prob.M, prob.N, prob.K)
+            for x, y in zip(got[:3], state[:3]):
+                np.testing.assert_array_equal(x, y)
+            assert bp.bpmf_sweep(h, 0) == r
+    finally:
+        if b is not None:
+            bp.bpmf_batch_destroy(b)
+        for h in hs:
+            bp.bpmf_destroy(h)
