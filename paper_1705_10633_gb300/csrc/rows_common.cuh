@@ -469,33 +469,51 @@ __device__ __forceinline__ void factor_solve_sample_rl64(float2 (&a1)[16], float
     float n1 = b1, n2 = b2;
     // ---- back substitution x = L^{-T} t: step i broadcasts x_i and every lane
     // updates its rows r < i with L[i][r], which sits in row r of M at position
-    // i - (r & ~1); four of them (two aligned pairs) serve four steps.  Selects, not
-    // branches: the update of a row on or below i is computed and dropped.
+    // i - (r & ~1); four of them (two aligned pairs) serve four steps.  Steps i >= 32
+    // update every row r1 < 32 and, with selects, the rows r2 = 32 + lane; steps i < 32
+    // leave the rows r2 (all past i) alone and update the rows r1 with selects.
 #pragma unroll 1
-    for (int g = 15; g >= 0; --g) {
+    for (int g = 15; g >= 8; --g) {
         const float* q1 = M + r1 * kLtLd + 4 * g - (r1 & ~1);
         const float* q2 = M + r2 * kLtLd + 4 * g - (r2 & ~1);
         const float2 x1 = *reinterpret_cast<const float2*>(q1), y1 = *reinterpret_cast<const float2*>(q1 + 2);
         const float2 x2 = *reinterpret_cast<const float2*>(q2), y2 = *reinterpret_cast<const float2*>(q2 + 2);
-        const float4 A1 = make_float4(x1.x, x1.y, y1.x, y1.y);
-        const float4 A2 = make_float4(x2.x, x2.y, y2.x, y2.y);
         const float4 D = *reinterpret_cast<const float4*>(dinv + 4 * g);
-        const float l1v[4] = {A1.x, A1.y, A1.z, A1.w};
-        const float l2v[4] = {A2.x, A2.y, A2.z, A2.w};
+        const float l1v[4] = {x1.x, x1.y, y1.x, y1.y};
+        const float l2v[4] = {x2.x, x2.y, y2.x, y2.y};
         const float dv[4] = {D.x, D.y, D.z, D.w};
 #pragma unroll
         for (int u = 3; u >= 0; --u) {
             const int i = 4 * g + u;
-            const int owner = i & 31;
-            const float ui = __shfl_sync(kFullMask, i < 32 ? t1 : t2, owner) * dv[u];
-            const float f1 = fmaf(-l1v[u], ui, t1), f2 = fmaf(-l2v[u], ui, t2);
-            t1 = r1 == i ? ui : (r1 < i ? f1 : t1);
+            const float ui = __shfl_sync(kFullMask, t2, i & 31) * dv[u];
+            const float f2 = fmaf(-l2v[u], ui, t2);
+            t1 = fmaf(-l1v[u], ui, t1);
             t2 = r2 == i ? ui : (r2 < i ? f2 : t2);
             if (want_means) {
-                const float mi = __shfl_sync(kFullMask, i < 32 ? n1 : n2, owner) * dv[u];
-                const float g1 = fmaf(-l1v[u], mi, n1), g2 = fmaf(-l2v[u], mi, n2);
-                n1 = r1 == i ? mi : (r1 < i ? g1 : n1);
+                const float mi = __shfl_sync(kFullMask, n2, i & 31) * dv[u];
+                const float g2 = fmaf(-l2v[u], mi, n2);
+                n1 = fmaf(-l1v[u], mi, n1);
                 n2 = r2 == i ? mi : (r2 < i ? g2 : n2);
+            }
+        }
+    }
+#pragma unroll 1
+    for (int g = 7; g >= 0; --g) {
+        const float* q1 = M + r1 * kLtLd + 4 * g - (r1 & ~1);
+        const float2 x1 = *reinterpret_cast<const float2*>(q1), y1 = *reinterpret_cast<const float2*>(q1 + 2);
+        const float4 D = *reinterpret_cast<const float4*>(dinv + 4 * g);
+        const float l1v[4] = {x1.x, x1.y, y1.x, y1.y};
+        const float dv[4] = {D.x, D.y, D.z, D.w};
+#pragma unroll
+        for (int u = 3; u >= 0; --u) {
+            const int i = 4 * g + u;
+            const float ui = __shfl_sync(kFullMask, t1, i) * dv[u];
+            const float f1 = fmaf(-l1v[u], ui, t1);
+            t1 = r1 == i ? ui : (r1 < i ? f1 : t1);
+            if (want_means) {
+                const float mi = __shfl_sync(kFullMask, n1, i) * dv[u];
+                const float g1 = fmaf(-l1v[u], mi, n1);
+                n1 = r1 == i ? mi : (r1 < i ? g1 : n1);
             }
         }
     }
