@@ -174,9 +174,9 @@ def gathered_bytes(nnz, K, bf16=False):
 # Gram slots (3.98 GB), which the user factorisation launch reads back (4.05 GB) before
 # writing the new rows (0.23 GB).
 TRAFFIC = {"config3_480kx18k_K64": {"rows_movie/rows_gram_kernel": 1.170e9,
-                                    "rows_movie/rows_chol_kernel": None,
+                                    "rows_movie/rows_chol_kernel": 142.6e6,
                                     "rows_user/rows_gram_kernel": 4.889e9,
-                                    "rows_user/rows_chol_kernel": None}}
+                                    "rows_user/rows_chol_kernel": 4.271e9}}
 
 
 def l2_note(nnz):
